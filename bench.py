@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the KDE-on-grid hot path on GB300.
+
+Workload: 20M AIS-like points (40,000 synthetic trajectories: 70% lane traffic,
+20% port clusters, 10% uniform) over a 100 km box, 4096 x 4096 grid of
+24.4140625 m cells, Gaussian kernel, h = 100 m.  One step = Mercator
+projection of the (lon, lat) inputs (FP64) -> centring / hi-lo split ->
+density on the tensor cores (split-FP16 by default) -> split-K reduce.
+
+Metric: point.cell evaluations per second (N * nx * ny per step), in
+Gpoint.cell/s, for the whole job.  Inputs are resident in HBM when the timed
+region starts (they exceed the 129 MB L2: 320 MB of lon/lat), and `e2e`
+repeats the step through the public API with pinned host buffers, the
+host->device copy of the inputs and the device->host copy of the grid inside
+the timed region.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at ≤1e-5 err"
+UNIT = "Gpoint·cell/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", default="tc_split16",
+                    choices=["tc_split16", "tc_fp16", "simt"])
+    ap.add_argument("--grid", type=int, default=4096, help="grid side (default: the 4096^2 workload)")
+    ap.add_argument("--points", type=int, default=40_000, help="trajectories of 500 fixes")
+    ap.add_argument("--simt-grid", type=int, default=512,
+                    help="grid side for the FP32 SIMT comparison (same points)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-cells", type=int, default=320)
+    ap.add_argument("--split-k", type=int, default=0)
+    ap.add_argument("--k-chunk", type=int, default=0)
+    ap.add_argument("--tile-n", type=int, default=0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(args):
+    import workloads
+    wl = workloads.config3(n_traj=args.points, grid=args.grid)
+    ll, corner, lat0 = wl.lonlat()
+    return wl, ll, corner, lat0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2004_13653_gb300 as kde
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", local)
+    kde.load(build_if_stale=True)
+    peaks, peak_kind = load_peaks()
+
+    wl, ll, corner, lat0 = make_workload(args)
+    n, nx, ny = wl.n, wl.nx, wl.ny
+    lonlat_dev = torch.as_tensor(ll, dtype=torch.float64, device=dev)
+    w_dev = torch.as_tensor(wl.w, dtype=torch.float32, device=dev)
+    xy_dev = torch.empty_like(lonlat_dev)
+    out_dev = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    corner_dev = torch.tensor([corner], dtype=torch.float64, device=dev)
+    origin = kde.project_mercator(corner_dev, lat0).cpu().numpy()[0]
+    stream = torch.cuda.current_stream(dev)
+    tiling = dict(split_k=args.split_k, k_chunk=args.k_chunk, tile_n=args.tile_n)
+
+    def step(events=None, path=args.path, out=out_dev, gx=nx, gy=ny):
+        kde.project_mercator(lonlat_dev, lat0, out=xy_dev, stream=stream)
+        kde.grid(xy_dev, w_dev, origin, wl.cell, gx, gy, wl.h, "gaussian", out=out, path=path,
+                 stream=stream, timing_events=events, **tiling)
+
+    def new_pair():
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.record(stream)
+        return a, b
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs = [new_pair() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = kde.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(kde.event_pair(*pairs[k]))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = kde.launch_count() - launches0
+    barrier(world)
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(world, ms)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+    evals = float(n) * nx * ny
+    value = world * evals / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel
+    if args.path == "simt":
+        # per point and thread: 16 factor evaluations (4 FP32 ops + 1 MUFU each),
+        # 8 weight products, 64 FMAs for 64 cells -> 2.125 FP32 ops per pair
+        clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_pairs = sms * clk_hz * min(128 / 2.125, 16 / 0.25)
+        achieved = evals / (kernel_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_pairs / 1e12,
+                "unit": "Tpair/s", "frac": achieved / peak_pairs, "traffic": None,
+                "peak_source": f"FP32 issue 128/clk/SM at {clk_hz/1e6:.0f} MHz"}
+    else:
+        products = 3 if args.path == "tc_split16" else 1
+        flops = 2.0 * products * evals
+        peak = peaks["bf16_tflops_sustained"]
+        achieved = flops / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} bf16 sustained (FP16 dense rate taken equal)"}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"tc_split16": "f16x2(hi/lo)->f32", "tc_fp16": "f16->f32",
+                  "simt": "f32"}[args.path] + ", f64 projection/centring",
+        "data": "synthetic",
+        "config": {"workload": f"{n} AIS-like pts, {nx}x{ny} grid, cell {wl.cell} m, "
+                               f"h={wl.h} m, gaussian",
+                   "path": args.path, "points": n, "grid": [nx, ny], "h_m": wl.h,
+                   "l2": "inputs (320 MB lon/lat + 80 MB weights) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "kernel_ms": kernel_ms,
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+
+    if rank == 0 and args.path != "simt" and args.simt_grid > 0:
+        sg = args.simt_grid
+        out_s = torch.empty((sg, sg), dtype=torch.float32, device=dev)
+        step(path="simt", out=out_s, gx=sg, gy=sg)
+        torch.cuda.synchronize()
+        a, b = new_pair()
+        a.record(stream)
+        step(path="simt", out=out_s, gx=sg, gy=sg)
+        b.record(stream)
+        torch.cuda.synchronize()
+        simt = float(n) * sg * sg / (a.elapsed_time(b) * 1e-3) / 1e9
+        result["simt_fp32"] = {"value": simt, "unit": UNIT, "grid": [sg, sg],
+                               "note": "FP32 SIMT path, same points, smaller grid (the path is "
+                                       "compute-bound, its rate does not depend on grid size)"}
+        result["tensor_vs_simt"] = value / world / simt
+
+    if not args.no_e2e:
+        lonlat_host = torch.empty_like(lonlat_dev, device="cpu").pin_memory()
+        lonlat_host.copy_(torch.as_tensor(ll))
+        w_host = torch.as_tensor(wl.w).pin_memory()
+        out_host = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            lonlat_dev.copy_(lonlat_host, non_blocking=True)
+            w_dev.copy_(w_host, non_blocking=True)
+            step()
+            out_host.copy_(out_dev, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+        result["e2e"] = {"value": world * evals / (ems * 1e-3) / 1e9, "unit": UNIT,
+                         "ms_per_step": ems,
+                         "h2d_bytes_per_step": int(lonlat_host.numel() * 8 + w_host.numel() * 4),
+                         "d2h_bytes_per_step": int(out_host.numel() * 4)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, wl, origin, ll, lat0, out_dev)
+
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def cpu_baseline(args, wl, origin, ll, lat0, out_dev):
+    """The FP64 oracle on a bounded sample of cells of the same workload, on all
+    host cores; also reports the GPU result's error on those cells."""
+    import numpy as np
+
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from kde_testutil import sample_cells
+
+    cores = os.cpu_count() or 1
+    F = out_dev.cpu().numpy()
+    cells = sample_cells(F, args.cpu_cells, seed=3)
+    xy = oracle.mercator(ll, lat0)
+    t = time.perf_counter()
+    ref = oracle.kde_cells(xy, wl.w, origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN, cells,
+                           threads=cores)
+    dt = time.perf_counter() - t
+    err = float(np.max(np.abs(F.reshape(-1)[cells] - ref)) / np.max(np.abs(ref)))
+    return {"value": len(cells) * wl.n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(cells)} cells (GPU argmax 8x8 neighbourhood, corners, random) x "
+                      f"all {wl.n} points, FP64, {dt:.1f} s",
+            "gpu_err_rel_linf_on_sample": err}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step is a bounded sample
+    (cells x all points) of the same workload, rank 0 only."""
+    import numpy as np
+
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    wl, ll, corner, lat0 = make_workload(args)
+    xy = oracle.mercator(ll, lat0)
+    origin = oracle.mercator([corner], lat0)[0]
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    per_step = 24
+    times = []
+    for k in range(args.warmup + args.steps):
+        cells = rng.choice(wl.nx * wl.ny, per_step, replace=False)
+        t = time.perf_counter()
+        oracle.kde_cells(xy, wl.w, origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN, cells,
+                         threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    step_s = sum(times) / len(times)
+    value = per_step * wl.n / step_s / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{wl.n} AIS-like pts, {wl.nx}x{wl.ny} grid, cell {wl.cell} m, "
+                               f"h={wl.h} m, gaussian", "path": "oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random cells x all {wl.n} points per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * kde.h — C ABI of the GB300 (sm_103a) kernel-density-on-a-grid library.
+ *
+ * The library computes the vessel-density surface of arXiv 2004.13653,
+ * Sec. III-C (Eq. 7, Table 1), read as the direct sum over points
+ *
+ *     F[j*nx + i] = 1/(N h^2) * sum_p w_p * k((gx_i - x_p)/h) * k((gy_j - y_p)/h)
+ *
+ * at the cell centres gx_i = ox + (i + 1/2) cell, gy_j = oy + (j + 1/2) cell,
+ * where k is one factor of a Table 1 product kernel f(s,t) = k(s) k(t) with
+ * support |s| <= 1 (Eq. 8, s measured in bandwidths h), N is the number of
+ * points (not the weight sum) and (x_p, y_p) are projected metres (Sec. III-A).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: KDE_OK (0) or a negative KDE_E* code; kde_last_error()
+ *     then holds a message for the calling thread.
+ *   - Ownership: the caller owns every buffer it passes.  The library owns one
+ *     internal device workspace per device (grown on demand with cudaMalloc,
+ *     freed by kde_release()) unless the caller passes its own in kde_opts.
+ *   - Memory spaces: "device" pointers must be CUDA device (or managed)
+ *     memory; kde_grid / kde_grid_ex also accept host pointers for points,
+ *     weights and out, which are then copied through the workspace.
+ *   - Streams: kde_grid_ex and friends enqueue on opts->stream (a
+ *     cudaStream_t; NULL = the legacy default stream) and return without
+ *     waiting unless KDE_FLAG_SYNC is set.  kde_grid() always waits.
+ *   - Layout: points are interleaved (x0, y0, x1, y1, ...) FP64 metres;
+ *     weights are FP32 (NULL = all ones); out is FP32 row-major [ny][nx]
+ *     with out[j*nx + i] and is overwritten.
+ */
+#ifndef KDE_GB300_KDE_H
+#define KDE_GB300_KDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define KDE_OK 0
+#define KDE_EINVAL (-1)   /* bad argument (null, size, h, kernel id, ...)   */
+#define KDE_ENOMEM (-2)   /* workspace allocation failed or too small       */
+#define KDE_ECUDA (-3)    /* CUDA runtime / launch error                    */
+#define KDE_ETIMEOUT (-4) /* a bounded device-side wait gave up             */
+#define KDE_ENOTSUP (-5)  /* combination not supported (e.g. TC + compact)  */
+#define KDE_EDATA (-6)    /* non-finite coordinate or weight (sync calls)   */
+
+/* ---- kernels: Table 1 of the paper, in its row order -------------------- */
+typedef enum {
+  KDE_UNIFORM = 0,      /* k(s) = 1/2                       I(s)            */
+  KDE_TRIANGULAR = 1,   /* k(s) = 1 - |s|                   I(s)            */
+  KDE_EPANECHNIKOV = 2, /* k(s) = 3/4 (1 - s^2)             I(s)            */
+  KDE_QUARTIC = 3,      /* k(s) = 15/16 (1 - s^2)^2         I(s)            */
+  KDE_TRIWEIGHT = 4,    /* k(s) = 35/32 (1 - s^2)^3         I(s)            */
+  KDE_TRICUBE = 5,      /* k(s) = 70/81 (1 - |s|^3)^3       I(s)            */
+  KDE_GAUSSIAN = 6,     /* k(s) = exp(-s^2/2) / sqrt(2 pi)                  */
+  KDE_COSINE = 7        /* k(s) = pi/4 cos(pi s / 2)        I(s)            */
+} kde_kernel;
+
+/* ---- evaluation paths --------------------------------------------------- */
+typedef enum {
+  KDE_PATH_AUTO = 0,       /* Gaussian -> TC_SPLIT16, compact -> CUTOFF       */
+  KDE_PATH_SIMT_FP32 = 1,  /* FP32 direct sum on the CUDA cores (any kernel)  */
+  KDE_PATH_TC_FP16 = 2,    /* Gaussian as F = A B^T on tcgen05, FP16 operands */
+  KDE_PATH_TC_SPLIT16 = 3, /* same, hi/lo FP16 operands, three products       */
+  KDE_PATH_CUTOFF = 4      /* binned gather over the compact support          */
+} kde_path;
+
+#define KDE_FLAG_SYNC 1u         /* wait for completion and check device flags */
+#define KDE_FLAG_SKIP_ZERO 2u    /* TC paths: skip (tile, chunk) pairs whose    */
+                                 /* operands are exactly zero in FP16           */
+
+typedef struct kde_args {
+  const double* points; /* [2n] interleaved x,y metres (device or host)      */
+  const float* weights; /* [n] or NULL for unit weights (device or host)     */
+  int64_t n;            /* number of points N, >= 0                          */
+  double origin_x;      /* lower-left corner of cell (0,0), metres           */
+  double origin_y;
+  double cell;          /* cell side, metres, > 0                            */
+  int32_t nx, ny;       /* grid size, > 0, nx*ny < 2^31                      */
+  double h;             /* bandwidth, metres, > 0 and finite                 */
+  int32_t kernel_id;    /* kde_kernel                                        */
+  float* out;           /* [ny*nx] result (device or host)                   */
+} kde_args;
+
+typedef struct kde_opts {
+  int32_t path;           /* kde_path                                        */
+  uint32_t flags;         /* KDE_FLAG_*                                      */
+  void* stream;           /* cudaStream_t, NULL = legacy default stream      */
+  void* workspace;        /* optional caller-owned device scratch ...        */
+  size_t workspace_bytes; /* ... of at least kde_workspace_size() bytes      */
+  int32_t split_k;        /* point-range splits, 0 = automatic               */
+  int32_t k_chunk;        /* TC paths: points per accumulator drain, 0=auto  */
+  int32_t tile_n;         /* TC paths: 128 or 256 grid rows per tile, 0=auto */
+  int32_t max_ctas;       /* cap on resident CTAs (0 = one per SM)           */
+  void* timing_events;    /* optional cudaEvent_t[2]: recorded on the stream */
+                          /* right before / after the dominant kernel       */
+} kde_opts;
+
+/* Fill *o with the defaults (AUTO path, legacy stream, library workspace). */
+void kde_default_opts(kde_opts* o);
+
+/*
+ * kde_grid — the density of Sec. III-C (Eq. 7 read as a direct sum over
+ * points, Table 1 kernels, Eq. 8 indicator) at the nx*ny cell centres.
+ * points/weights/out may be device or host memory.  Runs on the legacy
+ * default stream with the AUTO path and returns after completion.
+ * Errors: KDE_EINVAL (null points with n > 0, null out, n < 0, nx/ny <= 0,
+ * nx*ny >= 2^31, cell or h not positive and finite, unknown kernel_id,
+ * non-finite origin), KDE_EDATA (a non-finite coordinate or weight),
+ * KDE_ENOMEM, KDE_ECUDA, KDE_ETIMEOUT.  n = 0 writes zeros.
+ */
+int kde_grid(const double* points, const float* weights, int64_t n,
+             const double grid_origin[2], double cell, int nx, int ny,
+             double h, int kernel_id, float* out);
+
+/* kde_grid with explicit path, stream, workspace and tiling (Sec. III-C,
+ * Eq. 7 / Table 1).  Asynchronous on opts->stream unless KDE_FLAG_SYNC.
+ * opts may be NULL (defaults).  KDE_ENOTSUP for a TC path with a
+ * non-Gaussian kernel (only the Gaussian row of Table 1 is separable into
+ * exponential factors that a matrix product can sum). */
+int kde_grid_ex(const kde_args* a, const kde_opts* opts);
+
+/* Bytes of device workspace kde_grid_ex needs for these arguments/options
+ * (for callers that pass their own workspace). */
+int kde_workspace_size(const kde_args* a, const kde_opts* opts, size_t* bytes);
+
+/*
+ * kde_project_mercator — Sec. III-A, Eq. 1-4: (lon, lat) in degrees to
+ * Mercator metres with r0 = a cos(phi0)/sqrt(1 - e^2 sin^2 phi0),
+ * q = ln tan(pi/4 + phi/2) + (e/2) ln((1 - e sin phi)/(1 + e sin phi)),
+ * x = lambda r0, y = q r0 (lambda in radians), WGS84 a = 6378137 m,
+ * e^2 = 0.00669437999014.  lonlat_deg and xy_out: device, [2n] interleaved
+ * FP64 (may alias).  FP64 throughout.  Asynchronous on stream.
+ * Errors: KDE_EINVAL (n < 0, null or host pointers, |lat0| >= 90).
+ */
+int kde_project_mercator(const double* lonlat_deg, int64_t n, double lat0_deg,
+                         double* xy_out, void* stream);
+
+/*
+ * kde_grid_batched — many independent densities (each one Sec. III-C, Eq. 7
+ * with its own points, grid, h and kernel) in one persistent launch whose
+ * work list spans all instances; the merged-buffer idea of Sec. IV-C-1
+ * (all trajectories in one allocation with a length table) applied to
+ * instances.  All pointers in inst[] must be device memory.  Each instance
+ * runs the path AUTO would choose (Gaussian: split-FP16 tensor path,
+ * compact kernels: binned cutoff path) unless opts->path forces
+ * KDE_PATH_SIMT_FP32.  Asynchronous on opts->stream unless KDE_FLAG_SYNC;
+ * graph-capturable when the workspace is already large enough (call once
+ * outside capture, or pass opts->workspace).
+ */
+int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts);
+
+/*
+ * kde_grid_backward — adjoint of the Gaussian density (Sec. III-C, Eq. 7
+ * with the Gaussian row of Table 1).  Given G = dL/dF (device, [ny*nx]
+ * FP32), writes dL/dpoints (device, [2n] FP32, interleaved), dL/dweights
+ * (device [n] FP32, or NULL) and dL/dh (host double, or NULL):
+ *   dL/dw_p = c sum_ij G_ij A_ip B_jp,
+ *   dL/dx_p = c w_p sum_ij G_ij (gx_i - x_p)/h^2 A_ip B_jp (same for y),
+ *   dL/dh   = -(2/h) sum_ij G_ij F_ij + c sum_p w_p sum_ij G_ij r^2/h^3 A B,
+ * c = 1/(2 pi N h^2), A, B the 1-D Gaussian factors, recomputed on the fly.
+ * Requires a->points on the device and kernel_id == KDE_GAUSSIAN.  dL/dh
+ * makes the call synchronous.
+ */
+int kde_grid_backward(const kde_args* a, const float* grad_out,
+                      float* grad_points, float* grad_weights, double* grad_h,
+                      const kde_opts* opts);
+
+/*
+ * kde_lscv_grid — least-squares cross-validation loss of the Gaussian
+ * density on the grid (the paper chooses the bandwidth by eye, Sec. V-D;
+ * this is its quantitative counterpart):
+ *   L = cell^2 sum F^2 - (2/N) sum_p w_p [bilerp(F, x_p) - w_p K(0)/(N h^2)],
+ * K(0) = 1/(2 pi), bilerp = bilinear interpolation of F between cell
+ * centres with zero outside the grid.  F: device [ny*nx] (as computed by
+ * kde_grid_ex for the same arguments).  Writes the loss to *loss (host),
+ * dL/dF to grad_F (device [ny*nx], FP32), and the loss's direct partial
+ * derivatives w.r.t. w_p and x_p (not through F) to grad_w_direct (device
+ * [n]) and grad_points_direct (device [2n]); either may be NULL.  The
+ * direct partial w.r.t. h is added to *grad_h_direct (host) when non-NULL.
+ * Synchronous.
+ */
+int kde_lscv_grid(const kde_args* a, const float* F, double* loss,
+                  float* grad_F, float* grad_w_direct,
+                  float* grad_points_direct, double* grad_h_direct,
+                  const kde_opts* opts);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* kde_last_error(void);
+
+/* Free the library's workspaces on every device (safe to call any time no
+ * call is in flight). */
+int kde_release(void);
+
+/* Number of kernels the library has launched in this process (all
+ * devices, all entry points); a diagnostic for counting launches. */
+int64_t kde_launch_count(void);
+
+/* Library version string. */
+const char* kde_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDE_GB300_KDE_H */
