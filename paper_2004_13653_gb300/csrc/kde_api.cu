@@ -124,7 +124,8 @@ int validate(const kde_args* a, const kde_opts* o) {
         a->kernel_id != KDE_GAUSSIAN)
       return fail(KDE_ENOTSUP, "tensor-core paths need the Gaussian kernel");
     if (o->split_k < 0 || o->split_k > 1024) return fail(KDE_EINVAL, "split_k out of range");
-    if (o->k_chunk < 0 || (o->k_chunk % 64) != 0) return fail(KDE_EINVAL, "k_chunk must be a multiple of 64");
+    if (o->k_chunk < 0 || (o->k_chunk % 64) != 0 || o->k_chunk == 64)
+      return fail(KDE_EINVAL, "k_chunk must be 0 or a multiple of 64 of at least 128");
     if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256)
       return fail(KDE_EINVAL, "tile_n must be 0, 128 or 256");
     if (o->workspace && o->workspace_bytes == 0)
@@ -135,8 +136,28 @@ int validate(const kde_args* a, const kde_opts* o) {
 
 int resolve_path(const kde_args* a, const kde_opts* o) {
   int path = o ? o->path : KDE_PATH_AUTO;
-  if (path == KDE_PATH_AUTO) path = KDE_PATH_SIMT_FP32;
+  if (path == KDE_PATH_AUTO)
+    path = a->kernel_id == KDE_GAUSSIAN ? KDE_PATH_TC_SPLIT16 : KDE_PATH_SIMT_FP32;
   return path;
+}
+
+// Point-range splits for the persistent tensor-core kernel: the fewest
+// splits whose work items fill the CTAs' waves within ~3%, keeping at least
+// 256 points per split.
+int choose_tc_splits(int64_t tiles, int ctas, int64_t n_pad) {
+  const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(64, n_pad / 256));
+  int best = 1;
+  double best_waste = 1e30;
+  for (int64_t s = 1; s <= max_s; ++s) {
+    const int64_t items = tiles * s;
+    const int64_t waves = (items + ctas - 1) / ctas;
+    const double waste = (double)(waves * ctas) / (double)items;
+    if (waste < best_waste - 0.03) {
+      best_waste = waste;
+      best = (int)s;
+    }
+  }
+  return best;
 }
 
 int sm_count() {
@@ -167,6 +188,18 @@ int make_plan(const kde_args* a, const kde_opts* o, bool probe_memory, Plan* p) 
       const int64_t maxs = std::max<int64_t>(1, p->n_pad / 4096);
       splits = (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 64}));
     }
+  } else if (p->path == KDE_PATH_TC_FP16 || p->path == KDE_PATH_TC_SPLIT16) {
+    TcPlan& t = p->tc;
+    t.tile_n = (o && o->tile_n) ? o->tile_n : (a->ny <= 128 ? 128 : 256);
+    t.split16 = p->path == KDE_PATH_TC_SPLIT16;
+    // the tensor core's FP32 accumulation loses accuracy with every MMA step it
+    // adds into a large sum, so split-FP16 drains its accumulators often
+    t.k_chunk = (o && o->k_chunk) ? o->k_chunk : (t.split16 ? 256 : 1024);
+    t.ctas = (o && o->max_ctas > 0) ? std::min(o->max_ctas, sms) : sms;
+    t.skip_zero = (o && (o->flags & KDE_FLAG_SKIP_ZERO)) ? 1 : 0;
+    const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + t.tile_n - 1) / t.tile_n);
+    if (splits == 0) splits = choose_tc_splits(tiles, t.ctas, p->n_pad);
+    t.splits = splits;
   } else {
     splits = std::max(splits, 1);
   }
@@ -251,6 +284,15 @@ int run_grid(const kde_args* a, const kde_opts* o, bool force_sync) {
                              scale, part, s),
                  "SIMT direct sum");
         break;
+      case KDE_PATH_TC_FP16:
+      case KDE_PATH_TC_SPLIT16: {
+        // c = 2^-30 / (2 pi N h^2); the kernel multiplies by max |w|
+        const double base = 0x1p-30 / (2.0 * 3.14159265358979323846 * (double)a->n * a->h * a->h);
+        KDE_CUDA(launch_tc(pl.tc, pts, wts, pl.n_pad, gxt, gyt, a->nx, a->ny, (float)base, scal,
+                           part, scal, s),
+                 "tensor-core contraction");
+        break;
+      }
       default:
         return fail(KDE_ENOTSUP, "path %d is not available in this build", pl.path);
     }
@@ -268,6 +310,8 @@ int run_grid(const kde_args* a, const kde_opts* o, bool force_sync) {
     if (hs.err & kErrTimeout)
       return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs.timeout_where);
     if (hs.err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
+    if (hs.err & kErrNegWeight)
+      return fail(KDE_EDATA, "the tensor-core paths need non-negative weights");
     if (hs.err) return fail(KDE_ECUDA, "device error word 0x%x", hs.err);
   }
   g_err[0] = 0;

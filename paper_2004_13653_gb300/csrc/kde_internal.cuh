@@ -21,6 +21,7 @@ namespace kde {
 constexpr int kErrTimeout = 1;    // a bounded device-side wait gave up
 constexpr int kErrNonFinite = 2;  // non-finite coordinate or weight
 constexpr int kErrBadArg = 4;     // a kernel saw an impossible argument
+constexpr int kErrNegWeight = 8;  // negative weight on a tensor-core path
 
 struct CallScalars {
   int err;            // OR of kErr* bits

@@ -1,0 +1,439 @@
+// Path (b): the Gaussian density as a tensor-core contraction.
+//
+// The Gaussian row of Table 1 factorises, exp(-(s^2+t^2)/2) = exp(-s^2/2)
+// exp(-t^2/2), so the direct sum of Eq. 7 over points is a matrix product
+//     F[i,j] = c * sum_p A[i,p] B[j,p],
+//     A[i,p] = 2^(15 - u_ip^2),   B[j,p] = (w_p / w_max) 2^(15 - v_jp^2),
+// u, v = offsets in units of h sqrt(2 ln 2), c = w_max 2^-30 / (2 pi N h^2)
+// (the 2^15 factors keep the FP16 operands in the normal range).
+//
+// One persistent CTA per SM computes 128 x BN output tiles (x index i along
+// TMEM lanes, y index j along TMEM columns) for a range of points:
+//   warp 0      one thread issues tcgen05.mma (FP16 x FP16 -> FP32 in TMEM)
+//   warp 1      loads 64 points per stage and re-centres them on the tile
+//   warps 2-5   epilogue: TMEM -> registers -> partial grid in global memory
+//   warps 6..   producers: one operand row each, 64 exponentials per stage,
+//               written as FP16 (or hi + lo FP16 pairs) into shared memory in
+//               the 128-byte-swizzled K-major layout the MMA reads directly.
+// A and B never exist in global memory.  The FP32 accumulator is drained
+// every k_chunk points into the partial grid (double-buffered in TMEM) so the
+// tensor core never adds more than k_chunk/16 products into one FP32 value.
+// In split mode each operand is hi + lo with hi = fp16(v), lo = fp16(v - hi)
+// and the MMA sums A_hi B_hi + A_hi B_lo + A_lo B_hi (about 22 bits).
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "kde_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace kde {
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128;    // grid x-cells per tile (TMEM lanes)
+constexpr int kKS = 64;     // points per pipeline stage (one 128-byte row)
+constexpr int kPS = 8;      // depth of the point-parameter ring
+constexpr int kGroup = 4;   // stages the loader fetches at once
+
+enum Role : int { kRoleMma = 1, kRoleLoader = 2, kRoleEpilogue = 3, kRoleProducer = 4 };
+
+template <int BN, bool SPLIT>
+struct Cfg {
+  static constexpr int kHN = BN / 2;  // N of one accumulator half
+  static constexpr int kABytes = kBM * kKS * 2;
+  static constexpr int kBBytes = BN * kKS * 2;
+  static constexpr int kParts = SPLIT ? 2 : 1;
+  static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
+  static constexpr int kStages = (192 * 1024) / kStageBytes;
+  static constexpr int kProducers = kBM + BN;
+  static constexpr int kProducerWarps = kProducers / 32;
+  static constexpr int kThreads = 32 * (6 + kProducerWarps);
+  // TMEM: accumulator halves in columns [0, BN), running sums in [BN, 2 BN)
+  static constexpr uint32_t kTmemCols = 2 * BN;
+  static constexpr uint32_t kIdesc = idesc_f16_f32(kBM, kHN);
+  // shared-memory map (offsets from a 1024-byte aligned base)
+  static constexpr int kOffA = 0;                               // A_hi [, A_lo]
+  static constexpr int kOffB = kParts * kABytes;                // B_hi [, B_lo]
+  static constexpr int kOffParams = kStages * kStageBytes;      // float[kPS][3][kKS]
+  static constexpr int kOffBars = kOffParams + kPS * 3 * kKS * 4;
+  static constexpr int kNumBars = 2 * kStages + 2 * kPS + 4 + 1;
+  static constexpr int kOffMisc = kOffBars + kNumBars * 8;      // tmem slot, abort flag
+  static constexpr int kSmemBytes = kOffMisc + 64 + 1024;       // + alignment slack
+  static_assert(kStages >= 2, "pipeline needs two stages");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+};
+
+struct Item {
+  int tm, tn, s;
+  int64_t k_begin;
+  int nst;  // stages of 64 points
+};
+
+__device__ __forceinline__ Item item_of(int it, int tiles_m, int tiles_n, int64_t per_split,
+                                        int64_t n_pad) {
+  Item r;
+  r.tm = it % tiles_m;
+  const int rest = it / tiles_m;
+  r.tn = rest % tiles_n;
+  r.s = rest / tiles_n;
+  r.k_begin = (int64_t)r.s * per_split;
+  int64_t k_end = r.k_begin + per_split;
+  if (k_end > n_pad) k_end = n_pad;
+  r.nst = k_end > r.k_begin ? (int)((k_end - r.k_begin) / kKS) : 0;
+  return r;
+}
+
+// Accumulator half h restarts every C stages, half 1 offset by C/2, so the
+// two halves are never drained at the same time (except at an item's end)
+// and the tensor core keeps working on one half while the other drains.
+__device__ __forceinline__ bool chunk_starts(int h, int st, int C) {
+  if (st == 0) return true;
+  const int off = h ? C / 2 : 0;
+  return st >= off && (st - off) % C == 0;
+}
+__device__ __forceinline__ int next_boundary(int h, int cs, int C) {
+  if (h == 0) return (cs / C + 1) * C;
+  return cs < C / 2 ? C / 2 : cs + C;
+}
+
+template <int BN, bool SPLIT>
+__global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
+    k_tc(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n_pad,
+         const float2* __restrict__ gxt, const float2* __restrict__ gyt, int nx, int ny,
+         int tiles_m, int tiles_n, int splits, int64_t per_split, int chunk_stages,
+         float base_scale, CallScalars* __restrict__ scal, float* __restrict__ part) {
+  using C = Cfg<BN, SPLIT>;
+  constexpr int HN = C::kHN;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  float* params = reinterpret_cast<float*>(smem + C::kOffParams);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBars);
+  uint64_t* full = bars;                       // [kStages] producers -> MMA
+  uint64_t* empty = bars + C::kStages;         // [kStages] MMA -> producers
+  uint64_t* pfull = bars + 2 * C::kStages;     // [kPS] loader -> producers
+  uint64_t* pempty = pfull + kPS;              // [kPS] producers -> loader
+  uint64_t* accfull = pempty + kPS;            // [2] MMA -> epilogue, per half
+  uint64_t* accempty = accfull + 2;            // [2] epilogue -> MMA, per half
+  uint64_t* mmadone = accempty + 2;            // [1] final drain of the MMA pipe
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kOffMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kOffMisc + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n_items = tiles_m * tiles_n * splits;
+  const int CS = chunk_stages;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], C::kProducers);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < kPS; ++s) {
+      mbar_init(&pfull[s], 32);
+      mbar_init(&pempty[s], C::kProducers);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&accfull[h], 1);
+      mbar_init(&accempty[h], 128);
+    }
+    mbar_init(mmadone, 1);
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, C::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      uint32_t g = 0;
+      uint32_t mc[2] = {0, 0};
+      bool ok = true;
+      const uint32_t smem_base = smem_u32(smem);
+      for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+        const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+        for (int st = 0; ok && st < itm.nst; ++st, ++g) {
+          const uint32_t s = g % C::kStages;
+          if (!(ok = mbar_wait(&full[s], (g / C::kStages) & 1, abort_flag, scal, kRoleMma))) break;
+          tc_fence_after();
+          const uint32_t a0 = smem_base + s * C::kStageBytes + C::kOffA;
+          const uint32_t b0 = smem_base + s * C::kStageBytes + C::kOffB;
+          const uint64_t ahi = desc_sw128(a0), alo = desc_sw128(a0 + C::kABytes);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const bool fresh = chunk_starts(h, st, CS);
+            if (fresh) {
+              if (!(ok = mbar_wait(&accempty[h], (mc[h] & 1) ^ 1, abort_flag, scal, kRoleMma))) break;
+              ++mc[h];
+              tc_fence_after();
+            }
+            const uint32_t d_tmem = tmem_base + h * HN;
+            const uint32_t bh = b0 + h * HN * 128;  // rows [h HN, (h+1) HN) of B
+            const uint64_t bhi = desc_sw128(bh), blo = desc_sw128(bh + C::kBBytes);
+#pragma unroll
+            for (int k = 0; k < kKS / 16; ++k) {
+              const uint32_t acc = (fresh && k == 0) ? 0u : 1u;
+              const uint64_t dk = (uint64_t)(2 * k);  // +32 bytes in the start-address field
+              mma_f16(d_tmem, ahi + dk, bhi + dk, C::kIdesc, acc);
+              if (SPLIT) {
+                mma_f16(d_tmem, ahi + dk, blo + dk, C::kIdesc, 1u);
+                mma_f16(d_tmem, alo + dk, bhi + dk, C::kIdesc, 1u);
+              }
+            }
+            if (st + 1 == itm.nst || chunk_starts(h, st + 1, CS)) mma_commit(&accfull[h]);
+          }
+          if (!ok) break;
+          mma_commit(&empty[s]);
+        }
+      }
+      // every issued MMA must finish before TMEM is released
+      mma_commit(mmadone);
+      mbar_wait(mmadone, 0, abort_flag, scal, kRoleMma, /*honour_abort=*/false);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // --------------------------------------------------------- point loader
+    const float wmax = __uint_as_float(scal->wmax_bits);
+    const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
+    uint32_t g = 0;
+    bool ok = true, negative = false;
+    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      const float2 cx = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
+      const float2 cy = gyt[min(itm.tn * BN + BN / 2, ny - 1)];
+      for (int st = 0; ok && st < itm.nst; st += kGroup) {
+        const int ng = min(kGroup, itm.nst - st);
+        float4 P[kGroup][2];
+        float W[kGroup][2];
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u)
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh)
+            if (u < ng) {
+              const int64_t p = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
+              P[u][hh] = __ldg(pts + p);
+              W[u][hh] = __ldg(wts + p);
+            }
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+          if (u >= ng) break;
+          const uint32_t ps = g % kPS;
+          if (!(ok = mbar_wait(&pempty[ps], ((g / kPS) & 1) ^ 1, abort_flag, scal, kRoleLoader)))
+            break;
+          float* prm = params + ps * 3 * kKS;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int e = lane + 32 * hh;
+            const float4 q = P[u][hh];
+            prm[e] = (q.x - cx.x) + (q.y - cx.y);
+            prm[kKS + e] = (q.z - cy.x) + (q.w - cy.y);
+            const float w = W[u][hh];
+            negative |= w < 0.f;
+            // B = (w / w_max) 2^(15 - v^2) = 2^(cb - v^2); w = 0 gives cb = -inf, B = 0
+            prm[2 * kKS + e] = w > 0.f ? 15.0f + log2f(w * inv_wmax) : -INFINITY;
+          }
+          mbar_arrive(&pfull[ps]);
+          ++g;
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, negative) && lane == 0) atomicOr(&scal->err, kErrNegWeight);
+  } else if (warp < 6) {
+    // ------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const float wmax = __uint_as_float(scal->wmax_bits);
+    const float scale = base_scale * (wmax > 0.f ? wmax : 1.0f);
+    const int64_t cells = (int64_t)nx * ny;
+    uint32_t dc[2] = {0, 0};
+    bool ok = true;
+    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      const int i = itm.tm * kBM + q * 32 + lane;
+      const int j0 = itm.tn * BN;
+      float* slot = part + (int64_t)itm.s * cells;
+      if (itm.nst == 0) {
+        if (i < nx)
+          for (int c = 0; c < BN && j0 + c < ny; ++c) slot[(int64_t)(j0 + c) * nx + i] = 0.f;
+        continue;
+      }
+      int cs[2] = {0, 0};
+      bool done[2] = {false, false}, first[2] = {true, true};
+      while (ok && !(done[0] && done[1])) {
+        // next drain in commit order: earliest chunk end, half 0 first on ties
+        int e[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          e[h] = done[h] ? 0x7fffffff : min(next_boundary(h, cs[h], CS), itm.nst) - 1;
+        const int h = e[0] <= e[1] ? 0 : 1;
+        const bool final = e[h] == itm.nst - 1;
+        if (!(ok = mbar_wait(&accfull[h], dc[h] & 1, abort_flag, scal, kRoleEpilogue))) break;
+        ++dc[h];
+        tc_fence_after();
+        const uint32_t acc_col = tmem_base + lane_off + h * HN;
+        const uint32_t run_col = tmem_base + lane_off + BN + h * HN;
+#pragma unroll 1
+        for (int cb = 0; cb < HN / 32; ++cb) {
+          float a[32];
+          tmem_ld32(acc_col + cb * 32, a);
+          if (!first[h]) {
+            float r[32];
+            tmem_ld32(run_col + cb * 32, r);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) a[c] += r[c];
+          }
+          if (final) {
+            if (i < nx) {
+#pragma unroll
+              for (int c = 0; c < 32; ++c) {
+                const int j = j0 + h * HN + cb * 32 + c;
+                if (j < ny) slot[(int64_t)j * nx + i] = a[c] * scale;
+              }
+            }
+          } else {
+            tmem_st32(run_col + cb * 32, a);
+          }
+        }
+        if (!final) tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&accempty[h]);
+        if (final) {
+          done[h] = true;
+        } else {
+          cs[h] = e[h] + 1;
+          first[h] = false;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ producers
+    const int t = threadIdx.x - 6 * 32;
+    const bool isA = t < kBM;  // warp-uniform
+    const int r = isA ? t : t - kBM;
+    const int lo_off = isA ? C::kABytes : C::kBBytes;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      float gv;
+      if (isA) {
+        const float2 c = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
+        const float2 v = gxt[min(itm.tm * kBM + r, nx - 1)];
+        gv = (v.x - c.x) + (v.y - c.y);
+      } else {
+        const float2 c = gyt[min(itm.tn * BN + BN / 2, ny - 1)];
+        const float2 v = gyt[min(itm.tn * BN + r, ny - 1)];
+        gv = (v.x - c.x) + (v.y - c.y);
+      }
+      for (int st = 0; st < itm.nst; ++st, ++g) {
+        const uint32_t s = g % C::kStages, ps = g % kPS;
+        if (!(ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer))) break;
+        if (!(ok = mbar_wait(&empty[s], ((g / C::kStages) & 1) ^ 1, abort_flag, scal, kRoleProducer)))
+          break;
+        unsigned char* hi_row = smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * 128;
+        const float4* crd = reinterpret_cast<const float4*>(params + ps * 3 * kKS + (isA ? 0 : kKS));
+        const float4* cbv = reinterpret_cast<const float4*>(params + ps * 3 * kKS + 2 * kKS);
+#pragma unroll 2
+        for (int c = 0; c < 8; ++c) {
+          const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
+          float4 c0 = make_float4(15.f, 15.f, 15.f, 15.f), c1 = c0;
+          if (!isA) {
+            c0 = cbv[2 * c];
+            c1 = cbv[2 * c + 1];
+          }
+          const float pc[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+          const float ce[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+          float v[8];
+#pragma unroll
+          for (int e2 = 0; e2 < 8; ++e2) {
+            const float u = gv - pc[e2];
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
+          }
+          const int off = ((c ^ (r & 7)) << 4);
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            if (SPLIT) {
+              // hi keeps 11 significant bits (exact in FP16), lo = v - hi exactly
+              const float h0 = __uint_as_float(__float_as_uint(v[2 * e2]) & 0xFFFFE000u);
+              const float h1 = __uint_as_float(__float_as_uint(v[2 * e2 + 1]) & 0xFFFFE000u);
+              const __half2 hh = __floats2half2_rn(h0, h1);
+              const __half2 ll = __floats2half2_rn(v[2 * e2] - h0, v[2 * e2 + 1] - h1);
+              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+              lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
+            } else {
+              const __half2 hh = __floats2half2_rn(v[2 * e2], v[2 * e2 + 1]);
+              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+            }
+          }
+          *reinterpret_cast<uint4*>(hi_row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          if (SPLIT)
+            *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&full[s]);
+        mbar_arrive(&pempty[ps]);
+      }
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::kTmemCols);
+  }
+}
+
+template <int BN, bool SPLIT>
+cudaError_t launch_cfg(const TcPlan& p, const float4* pts, const float* wts, int64_t n_pad,
+                       const float2* gxt, const float2* gyt, int nx, int ny, float base_scale,
+                       float* part, CallScalars* scal, cudaStream_t s) {
+  using C = Cfg<BN, SPLIT>;
+  cudaError_t e = cudaFuncSetAttribute(k_tc<BN, SPLIT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int tiles_m = (nx + kBM - 1) / kBM;
+  const int tiles_n = (ny + BN - 1) / BN;
+  int64_t per = (n_pad + p.splits - 1) / p.splits;
+  per = (per + kKS - 1) / kKS * kKS;
+  const int items = tiles_m * tiles_n * p.splits;
+  const int grid = std::min(items, p.ctas);
+  k_tc<BN, SPLIT><<<grid, C::kThreads, C::kSmemBytes, s>>>(
+      pts, wts, n_pad, gxt, gyt, nx, ny, tiles_m, tiles_n, p.splits, per, p.k_chunk / kKS,
+      base_scale, scal, part);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(const TcPlan& p) {
+  if (p.tile_n == 256) return p.split16 ? Cfg<256, true>::kSmemBytes : Cfg<256, false>::kSmemBytes;
+  return p.split16 ? Cfg<128, true>::kSmemBytes : Cfg<128, false>::kSmemBytes;
+}
+
+cudaError_t launch_tc(const TcPlan& plan, const float4* pts, const float* wts, int64_t n_pad,
+                      const float2* gxt, const float2* gyt, int nx, int ny, float scale,
+                      const CallScalars* /*scal_in*/, float* part, CallScalars* scal,
+                      cudaStream_t s) {
+  // two accumulator halves drained half a chunk apart: at least two stages
+  if (plan.k_chunk < 2 * kKS || plan.k_chunk % kKS || plan.splits < 1 || plan.ctas < 1)
+    return cudaErrorInvalidValue;
+  if (plan.tile_n == 256)
+    return plan.split16 ? launch_cfg<256, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
+                        : launch_cfg<256, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+  if (plan.tile_n == 128)
+    return plan.split16 ? launch_cfg<128, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
+                        : launch_cfg<128, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace kde

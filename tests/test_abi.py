@@ -92,7 +92,7 @@ def test_tensor_path_needs_gaussian(lib):
 
 
 @pytest.mark.parametrize("field,value", [("path", 9), ("split_k", -1), ("k_chunk", 100),
-                                         ("tile_n", 96)])
+                                         ("k_chunk", 64), ("tile_n", 96)])
 def test_invalid_options_rejected(lib, field, value):
     a = _args(out=8)
     o = kde.make_opts()
