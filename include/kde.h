@@ -96,6 +96,8 @@ typedef struct kde_opts {
   int32_t max_ctas;       /* cap on resident CTAs (0 = one per SM)           */
   void* timing_events;    /* optional cudaEvent_t[2]: recorded on the stream */
                           /* right before / after the dominant kernel       */
+  int32_t stage_points;   /* TC paths: 32 or 64 points per pipeline stage,  */
+                          /* 0 = automatic                                  */
 } kde_opts;
 
 /* Fill *o with the defaults (AUTO path, legacy stream, library workspace). */

@@ -40,7 +40,7 @@ class KdeOpts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("split_k", ctypes.c_int32), ("k_chunk", ctypes.c_int32),
                 ("tile_n", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("timing_events", ctypes.c_void_p)]
+                ("timing_events", ctypes.c_void_p), ("stage_points", ctypes.c_int32)]
 
 
 EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
@@ -146,7 +146,7 @@ def make_args(points, weights, origin, cell, nx, ny, h, kernel, out) -> KdeArgs:
 
 
 def make_opts(path="auto", flags=0, stream=None, workspace=None, split_k=0, k_chunk=0,
-              tile_n=0, max_ctas=0, timing_events=None) -> KdeOpts:
+              tile_n=0, max_ctas=0, timing_events=None, stage_points=0) -> KdeOpts:
     o = KdeOpts()
     load().kde_default_opts(ctypes.byref(o))
     o.path = PATHS[path] if isinstance(path, str) else int(path)
@@ -157,6 +157,7 @@ def make_opts(path="auto", flags=0, stream=None, workspace=None, split_k=0, k_ch
         o.workspace = _ptr(workspace)
         o.workspace_bytes = _count(workspace) * workspace.element_size()
     o.split_k, o.k_chunk, o.tile_n, o.max_ctas = int(split_k), int(k_chunk), int(tile_n), int(max_ctas)
+    o.stage_points = int(stage_points)
     if timing_events is not None:
         # keep the array alive as long as the options object
         o._events = timing_events

@@ -124,10 +124,12 @@ int validate(const kde_args* a, const kde_opts* o) {
         a->kernel_id != KDE_GAUSSIAN)
       return fail(KDE_ENOTSUP, "tensor-core paths need the Gaussian kernel");
     if (o->split_k < 0 || o->split_k > 1024) return fail(KDE_EINVAL, "split_k out of range");
-    if (o->k_chunk < 0 || (o->k_chunk % 64) != 0 || o->k_chunk == 64)
-      return fail(KDE_EINVAL, "k_chunk must be 0 or a multiple of 64 of at least 128");
+    if (o->k_chunk < 0 || (o->k_chunk % 32) != 0 || (o->k_chunk > 0 && o->k_chunk < 64))
+      return fail(KDE_EINVAL, "k_chunk must be 0 or a multiple of 32 of at least 64");
     if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256)
       return fail(KDE_EINVAL, "tile_n must be 0, 128 or 256");
+    if (o->stage_points != 0 && o->stage_points != 32 && o->stage_points != 64)
+      return fail(KDE_EINVAL, "stage_points must be 0, 32 or 64");
     if (o->workspace && o->workspace_bytes == 0)
       return fail(KDE_EINVAL, "workspace given with zero size");
   }
@@ -197,6 +199,13 @@ int make_plan(const kde_args* a, const kde_opts* o, bool probe_memory, Plan* p) 
     t.k_chunk = (o && o->k_chunk) ? o->k_chunk : (t.split16 ? 256 : 1024);
     t.ctas = (o && o->max_ctas > 0) ? std::min(o->max_ctas, sms) : sms;
     t.skip_zero = (o && (o->flags & KDE_FLAG_SKIP_ZERO)) ? 1 : 0;
+    // 64-point stages (128-byte rows): fewer barrier round trips per point
+    // outweigh the deeper pipeline 32-point stages would allow
+    t.stage_points = (o && o->stage_points) ? o->stage_points : 64;
+    // two accumulator halves drained half a chunk apart need two stages per chunk
+    if (t.k_chunk % t.stage_points || t.k_chunk < 2 * t.stage_points)
+      return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
+                  t.k_chunk, t.stage_points);
     const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + t.tile_n - 1) / t.tile_n);
     if (splits == 0) splits = choose_tc_splits(tiles, t.ctas, p->n_pad);
     t.splits = splits;

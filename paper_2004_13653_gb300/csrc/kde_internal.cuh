@@ -85,6 +85,7 @@ struct TcPlan {
   int k_chunk;     // points per TMEM accumulator drain (multiple of 64)
   int ctas;        // persistent CTAs
   int skip_zero;   // skip (tile, stage) pairs whose operands are all zero
+  int stage_points;  // 32 or 64 points per pipeline stage
 };
 size_t tc_smem_bytes(const TcPlan& p);
 cudaError_t launch_tc(const TcPlan& plan, const float4* pts, const float* wts, int64_t n_pad,

@@ -33,17 +33,24 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128;    // grid x-cells per tile (TMEM lanes)
-constexpr int kKS = 64;     // points per pipeline stage (one 128-byte row)
 constexpr int kPS = 8;      // depth of the point-parameter ring
 constexpr int kGroup = 4;   // stages the loader fetches at once
 
 enum Role : int { kRoleMma = 1, kRoleLoader = 2, kRoleEpilogue = 3, kRoleProducer = 4 };
 
-template <int BN, bool SPLIT>
+// KS points per pipeline stage: one operand row of KS FP16 values, stored
+// K-major with the 128-byte (KS = 64) or 64-byte (KS = 32) swizzle.
+template <int BN, bool SPLIT, int KS>
 struct Cfg {
+  static constexpr int kKS = KS;
+  static constexpr int kRowBytes = 2 * KS;
+  static constexpr int kChunks = KS / 8;                  // 16-byte chunks per row
+  static constexpr int kSwzShift = KS == 64 ? 0 : 1;      // row bits that permute chunks
+  static constexpr uint32_t kLayout = KS == 64 ? 2u : 4u; // 128B / 64B swizzle
+  static constexpr uint32_t kSbo = 8 * kRowBytes;         // 8-row atom stride
   static constexpr int kHN = BN / 2;  // N of one accumulator half
-  static constexpr int kABytes = kBM * kKS * 2;
-  static constexpr int kBBytes = BN * kKS * 2;
+  static constexpr int kABytes = kBM * kRowBytes;
+  static constexpr int kBBytes = BN * kRowBytes;
   static constexpr int kParts = SPLIT ? 2 : 1;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kStages = (192 * 1024) / kStageBytes;
@@ -52,7 +59,8 @@ struct Cfg {
   static constexpr int kThreads = 32 * (6 + kProducerWarps);
   // TMEM: accumulator halves in columns [0, BN), running sums in [BN, 2 BN)
   static constexpr uint32_t kTmemCols = 2 * BN;
-  static constexpr uint32_t kIdesc = idesc_f16_f32(kBM, kHN);
+  static constexpr uint32_t kIdescHalf = idesc_f16_f32(kBM, kHN);
+  static constexpr uint32_t kIdescFull = idesc_f16_f32(kBM, BN);
   // shared-memory map (offsets from a 1024-byte aligned base)
   static constexpr int kOffA = 0;                               // A_hi [, A_lo]
   static constexpr int kOffB = kParts * kABytes;                // B_hi [, B_lo]
@@ -72,7 +80,7 @@ struct Item {
 };
 
 __device__ __forceinline__ Item item_of(int it, int tiles_m, int tiles_n, int64_t per_split,
-                                        int64_t n_pad) {
+                                        int64_t n_pad, int ks) {
   Item r;
   r.tm = it % tiles_m;
   const int rest = it / tiles_m;
@@ -81,7 +89,7 @@ __device__ __forceinline__ Item item_of(int it, int tiles_m, int tiles_n, int64_
   r.k_begin = (int64_t)r.s * per_split;
   int64_t k_end = r.k_begin + per_split;
   if (k_end > n_pad) k_end = n_pad;
-  r.nst = k_end > r.k_begin ? (int)((k_end - r.k_begin) / kKS) : 0;
+  r.nst = k_end > r.k_begin ? (int)((k_end - r.k_begin) / ks) : 0;
   return r;
 }
 
@@ -98,17 +106,19 @@ __device__ __forceinline__ int next_boundary(int h, int cs, int C) {
   return cs < C / 2 ? C / 2 : cs + C;
 }
 
-template <int BN, bool SPLIT>
-__global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
+template <int BN, bool SPLIT, int KS>
+__global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     k_tc(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n_pad,
          const float2* __restrict__ gxt, const float2* __restrict__ gyt, int nx, int ny,
          int tiles_m, int tiles_n, int splits, int64_t per_split, int chunk_stages,
          float base_scale, CallScalars* __restrict__ scal, float* __restrict__ part) {
-  using C = Cfg<BN, SPLIT>;
+  using C = Cfg<BN, SPLIT, KS>;
   constexpr int HN = C::kHN;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  constexpr int kKS = KS;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // align in the shared window by pointer arithmetic on the shared array, so
+  // the compiler keeps the shared address space (LDS/STS, not generic LD/ST)
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* params = reinterpret_cast<float*>(smem + C::kOffParams);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBars);
   uint64_t* full = bars;                       // [kStages] producers -> MMA
@@ -128,12 +138,12 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
-      mbar_init(&full[s], C::kProducers);
+      mbar_init(&full[s], C::kProducerWarps);
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < kPS; ++s) {
       mbar_init(&pfull[s], 32);
-      mbar_init(&pempty[s], C::kProducers);
+      mbar_init(&pempty[s], C::kProducerWarps);
     }
     for (int h = 0; h < 2; ++h) {
       mbar_init(&accfull[h], 1);
@@ -157,37 +167,72 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
       bool ok = true;
       const uint32_t smem_base = smem_u32(smem);
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-        const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+        const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
         for (int st = 0; ok && st < itm.nst; ++st, ++g) {
           const uint32_t s = g % C::kStages;
           if (!(ok = mbar_wait(&full[s], (g / C::kStages) & 1, abort_flag, scal, kRoleMma))) break;
           tc_fence_after();
           const uint32_t a0 = smem_base + s * C::kStageBytes + C::kOffA;
           const uint32_t b0 = smem_base + s * C::kStageBytes + C::kOffB;
-          const uint64_t ahi = desc_sw128(a0), alo = desc_sw128(a0 + C::kABytes);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const bool fresh = chunk_starts(h, st, CS);
-            if (fresh) {
+          const uint64_t ahi = desc_swz(a0, C::kLayout, C::kSbo);
+          const uint64_t alo = desc_swz(a0 + C::kABytes, C::kLayout, C::kSbo);
+          const bool f0 = chunk_starts(0, st, CS), f1 = chunk_starts(1, st, CS);
+          if (f0 && f1) {
+            // first stage of an item: both halves start fresh, one N = BN MMA
+            for (int h = 0; ok && h < 2; ++h) {
               if (!(ok = mbar_wait(&accempty[h], (mc[h] & 1) ^ 1, abort_flag, scal, kRoleMma))) break;
               ++mc[h];
-              tc_fence_after();
             }
-            const uint32_t d_tmem = tmem_base + h * HN;
-            const uint32_t bh = b0 + h * HN * 128;  // rows [h HN, (h+1) HN) of B
-            const uint64_t bhi = desc_sw128(bh), blo = desc_sw128(bh + C::kBBytes);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          if (f0 != f1) {
+            // one half restarts: issue the other half's whole stage first so the
+            // tensor core works while the epilogue drains the restarting half
 #pragma unroll
-            for (int k = 0; k < kKS / 16; ++k) {
-              const uint32_t acc = (fresh && k == 0) ? 0u : 1u;
-              const uint64_t dk = (uint64_t)(2 * k);  // +32 bytes in the start-address field
-              mma_f16(d_tmem, ahi + dk, bhi + dk, C::kIdesc, acc);
-              if (SPLIT) {
-                mma_f16(d_tmem, ahi + dk, blo + dk, C::kIdesc, 1u);
-                mma_f16(d_tmem, alo + dk, bhi + dk, C::kIdesc, 1u);
+            for (int o = 0; o < 2; ++o) {
+              const int h = (o == 0) ? (f0 ? 1 : 0) : (f0 ? 0 : 1);
+              const bool fresh = o == 1;
+              if (fresh) {
+                if (!(ok = mbar_wait(&accempty[h], (mc[h] & 1) ^ 1, abort_flag, scal, kRoleMma))) break;
+                ++mc[h];
+                tc_fence_after();
+              }
+              const uint32_t d_tmem = tmem_base + h * HN;
+              const uint32_t bh = b0 + h * HN * C::kRowBytes;  // rows [h HN, (h+1) HN) of B
+              const uint64_t bhi = desc_swz(bh, C::kLayout, C::kSbo);
+              const uint64_t blo = desc_swz(bh + C::kBBytes, C::kLayout, C::kSbo);
+#pragma unroll
+              for (int k = 0; k < kKS / 16; ++k) {
+                const uint32_t acc = (fresh && k == 0) ? 0u : 1u;
+                const uint64_t dk = (uint64_t)(2 * k);  // +32 bytes in the start-address field
+                mma_f16(d_tmem, ahi + dk, bhi + dk, C::kIdescHalf, acc);
+                if (SPLIT) {
+                  mma_f16(d_tmem, ahi + dk, blo + dk, C::kIdescHalf, 1u);
+                  mma_f16(d_tmem, alo + dk, bhi + dk, C::kIdescHalf, 1u);
+                }
               }
             }
-            if (st + 1 == itm.nst || chunk_starts(h, st + 1, CS)) mma_commit(&accfull[h]);
+          } else {
+            // both halves continue (or both start): the halves are adjacent TMEM
+            // columns, so one N = BN MMA covers them
+            const uint64_t bhi = desc_swz(b0, C::kLayout, C::kSbo);
+            const uint64_t blo = desc_swz(b0 + C::kBBytes, C::kLayout, C::kSbo);
+#pragma unroll
+            for (int k = 0; k < kKS / 16; ++k) {
+              const uint32_t acc = (f0 && k == 0) ? 0u : 1u;
+              const uint64_t dk = (uint64_t)(2 * k);
+              mma_f16(tmem_base, ahi + dk, bhi + dk, C::kIdescFull, acc);
+              if (SPLIT) {
+                mma_f16(tmem_base, ahi + dk, blo + dk, C::kIdescFull, 1u);
+                mma_f16(tmem_base, alo + dk, bhi + dk, C::kIdescFull, 1u);
+              }
+            }
           }
+          if (!ok) break;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (st + 1 == itm.nst || chunk_starts(h, st + 1, CS)) mma_commit(&accfull[h]);
           if (!ok) break;
           mma_commit(&empty[s]);
         }
@@ -204,17 +249,18 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
     uint32_t g = 0;
     bool ok = true, negative = false;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
       const float2 cx = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
       const float2 cy = gyt[min(itm.tn * BN + BN / 2, ny - 1)];
       for (int st = 0; ok && st < itm.nst; st += kGroup) {
         const int ng = min(kGroup, itm.nst - st);
-        float4 P[kGroup][2];
-        float W[kGroup][2];
+        constexpr int kPer = kKS / 32;  // points per lane per stage
+        float4 P[kGroup][kPer];
+        float W[kGroup][kPer];
 #pragma unroll
         for (int u = 0; u < kGroup; ++u)
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh)
+          for (int hh = 0; hh < kPer; ++hh)
             if (u < ng) {
               const int64_t p = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
               P[u][hh] = __ldg(pts + p);
@@ -228,7 +274,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
             break;
           float* prm = params + ps * 3 * kKS;
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
+          for (int hh = 0; hh < kPer; ++hh) {
             const int e = lane + 32 * hh;
             const float4 q = P[u][hh];
             prm[e] = (q.x - cx.x) + (q.y - cx.y);
@@ -251,10 +297,10 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
     const float wmax = __uint_as_float(scal->wmax_bits);
     const float scale = base_scale * (wmax > 0.f ? wmax : 1.0f);
     const int64_t cells = (int64_t)nx * ny;
-    uint32_t dc[2] = {0, 0};
+    uint32_t dc0 = 0, dc1 = 0;
     bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
       const int i = itm.tm * kBM + q * 32 + lane;
       const int j0 = itm.tn * BN;
       float* slot = part + (int64_t)itm.s * cells;
@@ -263,18 +309,19 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
           for (int c = 0; c < BN && j0 + c < ny; ++c) slot[(int64_t)(j0 + c) * nx + i] = 0.f;
         continue;
       }
-      int cs[2] = {0, 0};
-      bool done[2] = {false, false}, first[2] = {true, true};
-      while (ok && !(done[0] && done[1])) {
+      int cs0 = 0, cs1 = 0;
+      bool done0 = false, done1 = false, first0 = true, first1 = true;
+      while (ok && !(done0 && done1)) {
         // next drain in commit order: earliest chunk end, half 0 first on ties
-        int e[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-          e[h] = done[h] ? 0x7fffffff : min(next_boundary(h, cs[h], CS), itm.nst) - 1;
-        const int h = e[0] <= e[1] ? 0 : 1;
-        const bool final = e[h] == itm.nst - 1;
-        if (!(ok = mbar_wait(&accfull[h], dc[h] & 1, abort_flag, scal, kRoleEpilogue))) break;
-        ++dc[h];
+        const int e0 = done0 ? 0x7fffffff : min(next_boundary(0, cs0, CS), itm.nst) - 1;
+        const int e1 = done1 ? 0x7fffffff : min(next_boundary(1, cs1, CS), itm.nst) - 1;
+        const int h = e0 <= e1 ? 0 : 1;
+        const int eh = h ? e1 : e0;
+        const bool first = h ? first1 : first0;
+        const bool final = eh == itm.nst - 1;
+        const uint32_t parity = (h ? dc1 : dc0) & 1;
+        if (!(ok = mbar_wait(&accfull[h], parity, abort_flag, scal, kRoleEpilogue))) break;
+        if (h) ++dc1; else ++dc0;
         tc_fence_after();
         const uint32_t acc_col = tmem_base + lane_off + h * HN;
         const uint32_t run_col = tmem_base + lane_off + BN + h * HN;
@@ -282,7 +329,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
         for (int cb = 0; cb < HN / 32; ++cb) {
           float a[32];
           tmem_ld32(acc_col + cb * 32, a);
-          if (!first[h]) {
+          if (!first) {
             float r[32];
             tmem_ld32(run_col + cb * 32, r);
 #pragma unroll
@@ -303,11 +350,10 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
         if (!final) tmem_wait_st();
         tc_fence_before();
         mbar_arrive(&accempty[h]);
-        if (final) {
-          done[h] = true;
+        if (h) {
+          if (final) done1 = true; else { cs1 = eh + 1; first1 = false; }
         } else {
-          cs[h] = e[h] + 1;
-          first[h] = false;
+          if (final) done0 = true; else { cs0 = eh + 1; first0 = false; }
         }
       }
     }
@@ -320,7 +366,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
     uint32_t g = 0;
     bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad);
+      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
       float gv;
       if (isA) {
         const float2 c = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
@@ -336,11 +382,12 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
         if (!(ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer))) break;
         if (!(ok = mbar_wait(&empty[s], ((g / C::kStages) & 1) ^ 1, abort_flag, scal, kRoleProducer)))
           break;
-        unsigned char* hi_row = smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * 128;
+        unsigned char* hi_row =
+            smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
         const float4* crd = reinterpret_cast<const float4*>(params + ps * 3 * kKS + (isA ? 0 : kKS));
         const float4* cbv = reinterpret_cast<const float4*>(params + ps * 3 * kKS + 2 * kKS);
-#pragma unroll 2
-        for (int c = 0; c < 8; ++c) {
+#pragma unroll 4
+        for (int c = 0; c < C::kChunks; ++c) {
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
           float4 c0 = make_float4(15.f, 15.f, 15.f, 15.f), c1 = c0;
           if (!isA) {
@@ -355,7 +402,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
             const float u = gv - pc[e2];
             asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
           }
-          const int off = ((c ^ (r & 7)) << 4);
+          const int off = (c ^ ((r >> C::kSwzShift) & (C::kChunks - 1))) << 4;
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int e2 = 0; e2 < 4; ++e2) {
@@ -376,9 +423,14 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
           if (SPLIT)
             *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
+        // each writer makes its stores visible to the tensor core's proxy; the
+        // warp then signals once (__syncwarp orders the lanes' writes first)
         fence_proxy_async_smem();
-        mbar_arrive(&full[s]);
-        mbar_arrive(&pempty[ps]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&full[s]);
+          mbar_arrive(&pempty[ps]);
+        }
       }
     }
   }
@@ -392,47 +444,53 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT>::kThreads, 1)
   }
 }
 
-template <int BN, bool SPLIT>
+template <int BN, bool SPLIT, int KS>
 cudaError_t launch_cfg(const TcPlan& p, const float4* pts, const float* wts, int64_t n_pad,
                        const float2* gxt, const float2* gyt, int nx, int ny, float base_scale,
                        float* part, CallScalars* scal, cudaStream_t s) {
-  using C = Cfg<BN, SPLIT>;
-  cudaError_t e = cudaFuncSetAttribute(k_tc<BN, SPLIT>,
+  using C = Cfg<BN, SPLIT, KS>;
+  // two accumulator halves drained half a chunk apart: at least two stages
+  if (p.k_chunk < 2 * KS || p.k_chunk % KS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc<BN, SPLIT, KS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
   const int tiles_m = (nx + kBM - 1) / kBM;
   const int tiles_n = (ny + BN - 1) / BN;
   int64_t per = (n_pad + p.splits - 1) / p.splits;
-  per = (per + kKS - 1) / kKS * kKS;
+  per = (per + KS - 1) / KS * KS;
   const int items = tiles_m * tiles_n * p.splits;
   const int grid = std::min(items, p.ctas);
-  k_tc<BN, SPLIT><<<grid, C::kThreads, C::kSmemBytes, s>>>(
-      pts, wts, n_pad, gxt, gyt, nx, ny, tiles_m, tiles_n, p.splits, per, p.k_chunk / kKS,
+  k_tc<BN, SPLIT, KS><<<grid, C::kThreads, C::kSmemBytes, s>>>(
+      pts, wts, n_pad, gxt, gyt, nx, ny, tiles_m, tiles_n, p.splits, per, p.k_chunk / KS,
       base_scale, scal, part);
   note_launches(1);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t tc_smem_bytes(const TcPlan& p) {
-  if (p.tile_n == 256) return p.split16 ? Cfg<256, true>::kSmemBytes : Cfg<256, false>::kSmemBytes;
-  return p.split16 ? Cfg<128, true>::kSmemBytes : Cfg<128, false>::kSmemBytes;
+template <int BN, bool SPLIT>
+cudaError_t launch_ks(const TcPlan& p, const float4* pts, const float* wts, int64_t n_pad,
+                      const float2* gxt, const float2* gyt, int nx, int ny, float base_scale,
+                      float* part, CallScalars* scal, cudaStream_t s) {
+  if (p.stage_points == 32)
+    return launch_cfg<BN, SPLIT, 32>(p, pts, wts, n_pad, gxt, gyt, nx, ny, base_scale, part, scal, s);
+  if (p.stage_points == 64)
+    return launch_cfg<BN, SPLIT, 64>(p, pts, wts, n_pad, gxt, gyt, nx, ny, base_scale, part, scal, s);
+  return cudaErrorInvalidValue;
 }
+
+}  // namespace
 
 cudaError_t launch_tc(const TcPlan& plan, const float4* pts, const float* wts, int64_t n_pad,
                       const float2* gxt, const float2* gyt, int nx, int ny, float scale,
                       const CallScalars* /*scal_in*/, float* part, CallScalars* scal,
                       cudaStream_t s) {
-  // two accumulator halves drained half a chunk apart: at least two stages
-  if (plan.k_chunk < 2 * kKS || plan.k_chunk % kKS || plan.splits < 1 || plan.ctas < 1)
-    return cudaErrorInvalidValue;
+  if (plan.splits < 1 || plan.ctas < 1) return cudaErrorInvalidValue;
   if (plan.tile_n == 256)
-    return plan.split16 ? launch_cfg<256, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
-                        : launch_cfg<256, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+    return plan.split16 ? launch_ks<256, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
+                        : launch_ks<256, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
   if (plan.tile_n == 128)
-    return plan.split16 ? launch_cfg<128, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
-                        : launch_cfg<128, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+    return plan.split16 ? launch_ks<128, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
+                        : launch_ks<128, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
   return cudaErrorInvalidValue;
 }
 

@@ -157,17 +157,18 @@ __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor, K-major operand with 128-byte swizzling:
-// rows of 64 FP16 (128 bytes) stored consecutively, 8-row atoms 1024 bytes
-// apart (stride byte offset), the atom base 1024-byte aligned.  Advancing K by
-// 16 elements adds 32 bytes to the start address.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_addr) {
+// Shared-memory matrix descriptor, K-major operand with 128-byte (layout 2)
+// or 64-byte (layout 4) swizzling: rows of 64 or 32 FP16 stored
+// consecutively, 8-row atoms `sbo` bytes apart (stride byte offset), atoms
+// aligned to their size.  Advancing K by 16 elements adds 32 bytes to the
+// start address.
+__device__ __forceinline__ uint64_t desc_swz(uint32_t smem_addr, uint32_t layout, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);  // start address, bits 0-13
   d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset, bits 32-45
+  d |= (uint64_t)(sbo >> 4) << 32;                // stride byte offset, bits 32-45
   d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                         // layout: 128-byte swizzle
+  d |= (uint64_t)layout << 61;                    // swizzle mode
   return d;
 }
 

@@ -42,11 +42,13 @@ def test_config1_full_grid(path, tile_n):
 
 @pytest.mark.parametrize("path", ["tc_split16", "tc_fp16"])
 @pytest.mark.parametrize("tile_n", [128, 256])
-def test_ragged_tiles_weighted(path, tile_n):
+@pytest.mark.parametrize("stage_points", [32, 64])
+def test_ragged_tiles_weighted(path, tile_n, stage_points):
     """3x3 tiles with ragged edges on both axes, n not a multiple of 64,
-    weights U(0.5, 2), points partly outside the grid."""
+    weights U(0.5, 2), points partly outside the grid; both stage depths
+    (128-byte and 64-byte swizzled operand rows)."""
     wl = workloads.random_points(400, 3001, 5000.0, 12.5, 300, 520, 40.0, oracle.GAUSSIAN)
-    F = run_gpu(wl, path, tile_n=tile_n)
+    F = run_gpu(wl, path, tile_n=tile_n, stage_points=stage_points)
     ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
     assert rel_linf(F, ref) <= TOL[path]
 
@@ -60,12 +62,13 @@ def _dense_cluster():
     return wl
 
 
-@pytest.mark.parametrize("path,k_chunk,split_k", [
-    ("tc_split16", 128, 1), ("tc_split16", 256, 3), ("tc_split16", 0, 0), ("tc_split16", 384, 7),
-    ("tc_fp16", 0, 0), ("tc_fp16", 4096, 2), ("tc_fp16", 192, 5)])
-def test_dense_cluster_chunk_and_split_variants(path, k_chunk, split_k):
+@pytest.mark.parametrize("path,k_chunk,split_k,stage_points", [
+    ("tc_split16", 128, 1, 64), ("tc_split16", 256, 3, 32), ("tc_split16", 0, 0, 0),
+    ("tc_split16", 384, 7, 64), ("tc_split16", 96, 2, 32),
+    ("tc_fp16", 0, 0, 0), ("tc_fp16", 4096, 2, 64), ("tc_fp16", 192, 5, 32)])
+def test_dense_cluster_chunk_and_split_variants(path, k_chunk, split_k, stage_points):
     wl = _dense_cluster()
-    F = run_gpu(wl, path, k_chunk=k_chunk, split_k=split_k)
+    F = run_gpu(wl, path, k_chunk=k_chunk, split_k=split_k, stage_points=stage_points)
     ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
     assert rel_linf(F, ref) <= TOL[path]
 
