@@ -1,0 +1,31 @@
+/*
+ * kde_diag.h — diagnostic entry points of the KDE library (building blocks
+ * exposed so they can be checked against the paper on their own).
+ */
+#ifndef KDE_GB300_KDE_DIAG_H
+#define KDE_GB300_KDE_DIAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * kde_diag_exclusive_scan — the multi-block exclusive prefix sum of
+ * arXiv 2004.13653, Sec. IV-A ("Scan Algorithm"): each block of `per_block`
+ * elements is scanned, the block totals are scanned in turn (recursively) and
+ * propagated to the following blocks.  The binned cutoff path uses it for
+ * its radix-sort bucket offsets.  in, out: device, [n] uint32 (must not
+ * alias); per_block in [1, 2048] (small values reproduce the paper's worked
+ * example with four-element blocks).  Synchronous; uses the library
+ * workspace.  Errors: KDE_EINVAL (n < 0, per_block out of range, null or host
+ * pointers), KDE_ENOMEM, KDE_ECUDA.
+ */
+int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int per_block,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDE_GB300_KDE_DIAG_H */

@@ -45,7 +45,8 @@ class KdeOpts(ctypes.Structure):
 
 EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_project_mercator", "kde_grid_batched", "kde_grid_backward", "kde_lscv_grid",
-           "kde_last_error", "kde_release", "kde_version", "kde_launch_count")
+           "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
+           "kde_diag_exclusive_scan")
 
 _lib = None
 
@@ -90,6 +91,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_release.restype = i32
     lib.kde_launch_count.argtypes = []
     lib.kde_launch_count.restype = ctypes.c_int64
+    lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
+    lib.kde_diag_exclusive_scan.restype = i32
     lib.kde_version.argtypes = []
     lib.kde_version.restype = ctypes.c_char_p
     _lib = lib
@@ -232,6 +235,16 @@ def project_mercator(lonlat, lat0_deg, out=None, stream=None):
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     check(load().kde_project_mercator(_ptr(lonlat), _count(lonlat) // 2, float(lat0_deg),
                                       _ptr(out), s))
+    return out
+
+
+def exclusive_scan(values, per_block=2048, out=None):
+    """kde_diag_exclusive_scan on a uint32-compatible int32 cuda tensor."""
+    import torch
+    if out is None:
+        out = torch.empty_like(values)
+    check(load().kde_diag_exclusive_scan(_ptr(values), _ptr(out), _count(values), int(per_block),
+                                         None))
     return out
 
 

@@ -93,8 +93,11 @@ struct Plan {
   int64_t n_pad;
   bool host_pts, host_w, host_out;
   TcPlan tc;
+  CutoffPlan co;
   // byte offsets into the workspace
   size_t off_scal, off_pts, off_wts, off_gxt, off_gyt, off_part, off_hxy, off_hw, off_hout, total;
+  size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
+      off_co_spts, off_co_sw;
 };
 
 int validate(const kde_args* a, const kde_opts* o) {
@@ -123,6 +126,8 @@ int validate(const kde_args* a, const kde_opts* o) {
     if ((o->path == KDE_PATH_TC_FP16 || o->path == KDE_PATH_TC_SPLIT16) &&
         a->kernel_id != KDE_GAUSSIAN)
       return fail(KDE_ENOTSUP, "tensor-core paths need the Gaussian kernel");
+    if (o->path == KDE_PATH_CUTOFF && a->kernel_id == KDE_GAUSSIAN)
+      return fail(KDE_ENOTSUP, "the cutoff path needs a compact-support kernel");
     if (o->split_k < 0 || o->split_k > 1024) return fail(KDE_EINVAL, "split_k out of range");
     if (o->k_chunk < 0 || (o->k_chunk % 32) != 0 || (o->k_chunk > 0 && o->k_chunk < 64))
       return fail(KDE_EINVAL, "k_chunk must be 0 or a multiple of 32 of at least 64");
@@ -139,7 +144,7 @@ int validate(const kde_args* a, const kde_opts* o) {
 int resolve_path(const kde_args* a, const kde_opts* o) {
   int path = o ? o->path : KDE_PATH_AUTO;
   if (path == KDE_PATH_AUTO)
-    path = a->kernel_id == KDE_GAUSSIAN ? KDE_PATH_TC_SPLIT16 : KDE_PATH_SIMT_FP32;
+    path = a->kernel_id == KDE_GAUSSIAN ? KDE_PATH_TC_SPLIT16 : KDE_PATH_CUTOFF;
   return path;
 }
 
@@ -224,6 +229,20 @@ int make_plan(const kde_args* a, const kde_opts* o, bool probe_memory, Plan* p) 
   p->off_hxy = take(p->host_pts ? sizeof(double) * 2 * (size_t)n : 0);
   p->off_hw = take(p->host_w ? sizeof(float) * (size_t)n : 0);
   p->off_hout = take(p->host_out ? sizeof(float) * (size_t)cells : 0);
+  if (p->path == KDE_PATH_CUTOFF) {
+    p->co = plan_cutoff(a->nx, a->ny, a->cell, a->h, p->n_pad);
+    const size_t u = sizeof(uint32_t);
+    for (int k = 0; k < 2; ++k) {
+      p->off_co_keys[k] = take(u * (size_t)p->n_pad);
+      p->off_co_vals[k] = take(u * (size_t)p->n_pad);
+    }
+    p->off_co_hist = take(u * p->co.hist_words);
+    p->off_co_hscan = take(u * p->co.hist_words);
+    p->off_co_stemp = take(u * (p->co.scan_words + 64));
+    p->off_co_start = take(u * ((size_t)p->co.nbins + 1));
+    p->off_co_spts = take(sizeof(float4) * (size_t)p->n_pad);
+    p->off_co_sw = take(sizeof(float) * (size_t)p->n_pad);
+  }
   p->total = off;
   return KDE_OK;
 }
@@ -300,6 +319,23 @@ int run_grid(const kde_args* a, const kde_opts* o, bool force_sync) {
         KDE_CUDA(launch_tc(pl.tc, pts, wts, pl.n_pad, gxt, gyt, a->nx, a->ny, (float)base, scal,
                            part, scal, s),
                  "tensor-core contraction");
+        break;
+      }
+      case KDE_PATH_CUTOFF: {
+        CutoffScratch cs;
+        for (int k = 0; k < 2; ++k) {
+          cs.keys[k] = reinterpret_cast<uint32_t*>(base + pl.off_co_keys[k]);
+          cs.vals[k] = reinterpret_cast<uint32_t*>(base + pl.off_co_vals[k]);
+        }
+        cs.hist = reinterpret_cast<uint32_t*>(base + pl.off_co_hist);
+        cs.hist_scan = reinterpret_cast<uint32_t*>(base + pl.off_co_hscan);
+        cs.scan_temp = reinterpret_cast<uint32_t*>(base + pl.off_co_stemp);
+        cs.start = reinterpret_cast<uint32_t*>(base + pl.off_co_start);
+        cs.spts = reinterpret_cast<float4*>(base + pl.off_co_spts);
+        cs.sw = reinterpret_cast<float*>(base + pl.off_co_sw);
+        KDE_CUDA(launch_cutoff(a->kernel_id, pl.co, pts, wts, a->n, pl.n_pad, a->cell, a->h, gxt,
+                               gyt, a->nx, a->ny, scale, cs, part, s),
+                 "cutoff evaluation");
         break;
       }
       default:
@@ -441,6 +477,25 @@ int kde_release(void) {
 }
 
 int64_t kde_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int per_block,
+                            void* stream) {
+  if (n < 0 || per_block < 1 || per_block > 2048)
+    return fail(KDE_EINVAL, "n must be >= 0 and per_block in [1, 2048]");
+  if (n == 0) return KDE_OK;
+  if (!in || !out) return fail(KDE_EINVAL, "null pointer");
+  if (memory_kind(in) != 0 || memory_kind(out) != 0)
+    return fail(KDE_EINVAL, "kde_diag_exclusive_scan needs device pointers");
+  void* ws = nullptr;
+  int rc = library_workspace(sizeof(uint32_t) * (scan_temp_words(n, per_block) + 64), &ws);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KDE_CUDA(launch_exclusive_scan(in, out, n, per_block, static_cast<uint32_t*>(ws), s),
+           "exclusive scan");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  g_err[0] = 0;
+  return KDE_OK;
+}
 
 const char* kde_version(void) { return "kde-gb300 0.1 (sm_103a)"; }
 

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "kde.h"
+#include "kde_diag.h"
 
 namespace kde {
 
@@ -76,6 +77,36 @@ cudaError_t launch_simt(int kid, const float4* pts, const float* wts, int64_t n_
 // Sum S partial grids in fixed order (s = 0, 1, ...) into out.
 cudaError_t launch_reduce_splits(const float* part, int splits, int64_t cells, float* out,
                                  cudaStream_t s);
+
+// Exclusive scan of m counts, `per_block` (<= 2048) per block, multi-block
+// with propagation; temp needs scan_temp_words(m, per_block) words.
+size_t scan_temp_words(int64_t m, int per_block);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t m, int per_block,
+                                  uint32_t* temp, cudaStream_t s);
+
+// Path (c): binned cutoff evaluation of the compact kernels.
+struct CutoffPlan {
+  int nbx, nby, nbins;  // 32x32-cell bins
+  int R;                // bins within reach of a point, per direction
+  int nchunks;          // radix-sort blocks of 2048 keys
+  int passes;           // 8-bit radix passes
+  size_t hist_words, scan_words;
+};
+struct CutoffScratch {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;
+  uint32_t* hist_scan;
+  uint32_t* scan_temp;
+  uint32_t* start;  // [nbins + 1]
+  float4* spts;     // points in bin order
+  float* sw;
+};
+CutoffPlan plan_cutoff(int nx, int ny, double cell, double h, int64_t n_pad);
+cudaError_t launch_cutoff(int kid, const CutoffPlan& c, const float4* pts, const float* wts,
+                          int64_t n, int64_t n_pad, double cell, double h, const float2* gxt,
+                          const float2* gyt, int nx, int ny, float scale, CutoffScratch ws,
+                          float* out, cudaStream_t s);
 
 // Path (b): Gaussian as a tcgen05 contraction.
 struct TcPlan {

@@ -1,0 +1,82 @@
+"""Parity of the binned cutoff path (path c, compact kernels) with the FP64
+oracle, through the C ABI, on the GPU (FP32: 1e-6 relative L-inf)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from kde_testutil import TOL_FP32, rel_linf, sample_cells
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2004_13653_gb300 as kde  # noqa: E402
+
+COMPACT = [k for k in range(8) if k != oracle.GAUSSIAN]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kde.load(build_if_stale=True)
+
+
+def run_gpu(wl, kid, path="cutoff", weights=True):
+    pts = torch.as_tensor(np.ascontiguousarray(wl.xy), dtype=torch.float64, device="cuda")
+    w = torch.as_tensor(wl.w, dtype=torch.float32, device="cuda") if weights else None
+    out = kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, path=path,
+                   flags=kde.FLAG_SYNC)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("kid", COMPACT, ids=[oracle.KERNEL_NAMES[k] for k in COMPACT])
+def test_all_compact_kernels_ragged(kid):
+    """Ragged 32x32 bins on both axes, weights U(0.5, 2), points partly
+    outside the grid (some beyond reach, some within a bandwidth)."""
+    wl = workloads.random_points(500 + kid, 2500, 3000.0, 10.0, 300, 150, 35.0, kid)
+    F = run_gpu(wl, kid)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("kid", [oracle.EPANECHNIKOV, oracle.TRICUBE])
+def test_wide_bandwidth_many_bins_in_reach(kid):
+    """h = 70 cells: each point reaches three bins in every direction."""
+    wl = workloads.random_points(510 + kid, 3000, 700.0, 5.0, 128, 96, 350.0, kid)
+    F = run_gpu(wl, kid)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+def test_config2_epanechnikov_sampled_and_vs_simt():
+    wl = workloads.config2(kernel=oracle.EPANECHNIKOV)
+    F = run_gpu(wl, oracle.EPANECHNIKOV)
+    cells = sample_cells(F, 256, seed=21)
+    ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                           oracle.EPANECHNIKOV, cells)
+    assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
+    S = run_gpu(wl, oracle.EPANECHNIKOV, path="simt")
+    assert rel_linf(F, S) <= 2 * TOL_FP32
+
+
+def test_bitwise_reproducible():
+    wl = workloads.config2(kernel=oracle.QUARTIC, n_traj=400)
+    a = run_gpu(wl, oracle.QUARTIC)
+    b = run_gpu(wl, oracle.QUARTIC)
+    assert np.array_equal(a, b)
+
+
+def test_all_points_out_of_reach_give_zeros():
+    wl = workloads.random_points(520, 100, 1000.0, 10.0, 50, 50, 20.0, oracle.EPANECHNIKOV)
+    wl.local[:] += 1e6
+    F = run_gpu(wl, oracle.EPANECHNIKOV)
+    assert not F.any()
+
+
+def test_single_point_and_auto_path():
+    wl = workloads.random_points(521, 1, 200.0, 10.0, 20, 20, 30.0, oracle.TRIWEIGHT)
+    wl.local[:] = [[101.0, 99.0]]
+    F = run_gpu(wl, oracle.TRIWEIGHT, path="auto")
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.TRIWEIGHT)
+    assert rel_linf(F, ref) <= TOL_FP32
