@@ -225,6 +225,30 @@ def workspace_size(points, weights, origin, cell, nx, ny, h, kernel, out, **opts
     return int(b.value)
 
 
+def grid_batched(instances, path="auto", flags=0, stream=None, **tiling):
+    """kde_grid_batched: many densities, one persistent launch per path family.
+
+    instances: sequence of dicts with keys points, weights, origin, cell, nx,
+    ny, h, kernel and optionally out (device tensors).  Returns the outputs.
+    """
+    import torch
+    args = (KdeArgs * max(len(instances), 1))()
+    outs = []
+    for k, d in enumerate(instances):
+        out = d.get("out")
+        if out is None:
+            out = torch.empty((int(d["ny"]), int(d["nx"])), dtype=torch.float32,
+                              device=d["points"].device)
+        outs.append(out)
+        args[k] = make_args(d["points"], d.get("weights"), d["origin"], d["cell"], d["nx"],
+                            d["ny"], d["h"], d.get("kernel", "gaussian"), out)
+    if stream is None and outs:
+        stream = _current_stream(outs[0].device)
+    o = make_opts(path, flags, stream, **tiling)
+    check(load().kde_grid_batched(args, len(instances), ctypes.byref(o)))
+    return outs
+
+
 def project_mercator(lonlat, lat0_deg, out=None, stream=None):
     """Eq. 1-4 on the device: [n,2] (lon, lat) degrees float64 -> metres."""
     import torch

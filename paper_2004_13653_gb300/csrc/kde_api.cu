@@ -8,7 +8,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "kde_internal.cuh"
 
@@ -87,19 +89,6 @@ int memory_kind(const void* p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-struct Plan {
-  int path;
-  int splits;
-  int64_t n_pad;
-  bool host_pts, host_w, host_out;
-  TcPlan tc;
-  CutoffPlan co;
-  // byte offsets into the workspace
-  size_t off_scal, off_pts, off_wts, off_gxt, off_gyt, off_part, off_hxy, off_hw, off_hout, total;
-  size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
-      off_co_spts, off_co_sw;
-};
-
 int validate(const kde_args* a, const kde_opts* o) {
   if (!a) return fail(KDE_EINVAL, "args is NULL");
   if (a->n < 0) return fail(KDE_EINVAL, "n = %lld is negative", (long long)a->n);
@@ -114,6 +103,8 @@ int validate(const kde_args* a, const kde_opts* o) {
     return fail(KDE_EINVAL, "grid origin must be finite");
   if (a->kernel_id < 0 || a->kernel_id > 7)
     return fail(KDE_EINVAL, "kernel_id %d is not a Table 1 kernel (0..7)", a->kernel_id);
+  if (a->n > ((int64_t)1 << 31))
+    return fail(KDE_EINVAL, "n = %lld exceeds 2^31 points per instance", (long long)a->n);
   // the kernels read points as double2 and write out as float
   if (a->points && (reinterpret_cast<uintptr_t>(a->points) & 15))
     return fail(KDE_EINVAL, "points must be 16-byte aligned");
@@ -135,6 +126,7 @@ int validate(const kde_args* a, const kde_opts* o) {
       return fail(KDE_EINVAL, "tile_n must be 0, 128 or 256");
     if (o->stage_points != 0 && o->stage_points != 32 && o->stage_points != 64)
       return fail(KDE_EINVAL, "stage_points must be 0, 32 or 64");
+    if (o->max_ctas < 0) return fail(KDE_EINVAL, "max_ctas must be >= 0");
     if (o->workspace && o->workspace_bytes == 0)
       return fail(KDE_EINVAL, "workspace given with zero size");
   }
@@ -148,7 +140,9 @@ int resolve_path(const kde_args* a, const kde_opts* o) {
   return path;
 }
 
-// Point-range splits for the persistent tensor-core kernel: the fewest
+bool is_tc(int path) { return path == KDE_PATH_TC_FP16 || path == KDE_PATH_TC_SPLIT16; }
+
+// Point-range splits for one persistent tensor-core density: the fewest
 // splits whose work items fill the CTAs' waves within ~3%, keeping at least
 // 256 points per split.
 int choose_tc_splits(int64_t tiles, int ctas, int64_t n_pad) {
@@ -175,75 +169,180 @@ int sm_count() {
   return sms > 0 ? sms : 152;
 }
 
-int make_plan(const kde_args* a, const kde_opts* o, bool probe_memory, Plan* p) {
-  memset(p, 0, sizeof(*p));
-  p->path = resolve_path(a, o);
-  const int64_t n = a->n;
-  p->n_pad = std::max<int64_t>(512, (n + 511) / 512 * 512);
-  const int64_t cells = (int64_t)a->nx * a->ny;
-  if (probe_memory) {
-    p->host_pts = n > 0 && memory_kind(a->points) == 1;
-    p->host_w = n > 0 && a->weights && memory_kind(a->weights) == 1;
-    p->host_out = memory_kind(a->out) == 1;
-  }
+struct InstPlan {
+  int path;
+  int splits;
+  int64_t n_pad, prep_begin;
+  size_t off_gxt, off_gyt, off_part;
+  // tensor-core path
+  int tiles_m, tiles_n, items;
+  int64_t per_split;
+  // cutoff path
+  CutoffGeom geo;
+  int bin_begin;
+  int64_t cut_begin;
+};
+
+struct BatchPlan {
+  int count;
+  std::vector<InstPlan> in;
+  TcPlan tc;
+  std::vector<int> tc_order;  // TC instances, most expensive items first
+  int n_tc = 0, n_cut = 0, n_simt = 0, n_reduce = 0, tc_items = 0, max_side = 1;
+  int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0;
+  CutoffSizes cz;
+  bool host_pts = false, host_w = false, host_out = false;
+  size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
+  size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
+      off_co_spts, off_co_sw, off_hxy, off_hw, off_hout, total;
+};
+
+int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory, BatchPlan* P) {
+  P->count = count;
+  P->in.assign(count, InstPlan());
   const int sms = sm_count();
-  int splits = o ? o->split_k : 0;
-  if (p->path == KDE_PATH_SIMT_FP32) {
-    if (splits == 0) {
-      const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + 63) / 64);
-      const int64_t want = (6 * (int64_t)sms + tiles - 1) / tiles;
-      const int64_t maxs = std::max<int64_t>(1, p->n_pad / 4096);
-      splits = (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 64}));
+  const int ctas = (o && o->max_ctas > 0) ? std::min(o->max_ctas, sms) : sms;
+  int tc_split16 = -1;
+  for (int k = 0; k < count; ++k) {
+    const kde_args* a = &A[k];
+    InstPlan& I = P->in[k];
+    I.path = resolve_path(a, o);
+    if (is_tc(I.path)) {
+      const int s16 = I.path == KDE_PATH_TC_SPLIT16;
+      if (tc_split16 >= 0 && tc_split16 != s16)
+        return fail(KDE_ENOTSUP, "one batch cannot mix FP16 and split-FP16 tensor paths");
+      tc_split16 = s16;
     }
-  } else if (p->path == KDE_PATH_TC_FP16 || p->path == KDE_PATH_TC_SPLIT16) {
-    TcPlan& t = p->tc;
-    t.tile_n = (o && o->tile_n) ? o->tile_n : (a->ny <= 128 ? 128 : 256);
-    t.split16 = p->path == KDE_PATH_TC_SPLIT16;
-    // the tensor core's FP32 accumulation loses accuracy with every MMA step it
-    // adds into a large sum, so split-FP16 drains its accumulators often
-    t.k_chunk = (o && o->k_chunk) ? o->k_chunk : (t.split16 ? 256 : 1024);
-    t.ctas = (o && o->max_ctas > 0) ? std::min(o->max_ctas, sms) : sms;
-    t.skip_zero = (o && (o->flags & KDE_FLAG_SKIP_ZERO)) ? 1 : 0;
-    // 64-point stages (128-byte rows): fewer barrier round trips per point
-    // outweigh the deeper pipeline 32-point stages would allow
-    t.stage_points = (o && o->stage_points) ? o->stage_points : 64;
-    // two accumulator halves drained half a chunk apart need two stages per chunk
-    if (t.k_chunk % t.stage_points || t.k_chunk < 2 * t.stage_points)
-      return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
-                  t.k_chunk, t.stage_points);
-    const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + t.tile_n - 1) / t.tile_n);
-    if (splits == 0) splits = choose_tc_splits(tiles, t.ctas, p->n_pad);
-    t.splits = splits;
-  } else {
-    splits = std::max(splits, 1);
+    I.n_pad = std::max<int64_t>(512, (a->n + 511) / 512 * 512);
+    I.prep_begin = P->total_pad;
+    P->total_pad += I.n_pad;
+    P->max_side = std::max({P->max_side, a->nx, a->ny});
   }
-  p->splits = splits;
+  if (count == 1 && probe_memory) {
+    const kde_args* a = &A[0];
+    P->host_pts = a->n > 0 && memory_kind(a->points) == 1;
+    P->host_w = a->n > 0 && a->weights && memory_kind(a->weights) == 1;
+    P->host_out = memory_kind(a->out) == 1;
+  } else if (probe_memory) {
+    for (int k = 0; k < count; ++k)
+      if ((A[k].n > 0 && memory_kind(A[k].points) != 0) ||
+          (A[k].weights && memory_kind(A[k].weights) != 0) || memory_kind(A[k].out) != 0)
+        return fail(KDE_EINVAL, "instance %d: batched calls need device pointers", k);
+  }
+
+  // tensor-core plan shared by every TC instance of the batch
+  TcPlan& t = P->tc;
+  t.split16 = tc_split16 == 1;
+  t.tile_n = (o && o->tile_n) ? o->tile_n : 256;
+  if (count == 1 && !(o && o->tile_n)) t.tile_n = A[0].ny <= 128 ? 128 : 256;
+  // the tensor core's FP32 accumulation loses accuracy with every MMA step it
+  // adds into a large sum, so split-FP16 drains its accumulators often
+  t.k_chunk = (o && o->k_chunk) ? o->k_chunk : (t.split16 ? 256 : 1024);
+  // 64-point stages (128-byte rows): fewer barrier round trips per point
+  // outweigh the deeper pipeline 32-point stages would allow
+  t.stage_points = (o && o->stage_points) ? o->stage_points : 64;
+  t.ctas = ctas;
+  t.skip_zero = (o && (o->flags & KDE_FLAG_SKIP_ZERO)) ? 1 : 0;
+  t.splits = 1;
+  if (tc_split16 >= 0 && (t.k_chunk % t.stage_points || t.k_chunk < 2 * t.stage_points))
+    return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
+                t.k_chunk, t.stage_points);
+
+  // per-path work decomposition
+  double tc_cost = 0.0;
+  for (int k = 0; k < count; ++k) {
+    const kde_args* a = &A[k];
+    InstPlan& I = P->in[k];
+    if (is_tc(I.path)) {
+      I.tiles_m = (a->nx + 127) / 128;
+      I.tiles_n = (a->ny + t.tile_n - 1) / t.tile_n;
+      tc_cost += (double)I.tiles_m * I.tiles_n * (double)I.n_pad;
+    }
+  }
+  const double target_item = tc_cost / (double)ctas / 6.0;
+  for (int k = 0; k < count; ++k) {
+    const kde_args* a = &A[k];
+    InstPlan& I = P->in[k];
+    int splits = o ? o->split_k : 0;
+    if (I.path == KDE_PATH_SIMT_FP32) {
+      if (splits == 0) {
+        const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + 63) / 64);
+        const int64_t want = (6 * (int64_t)sms + tiles - 1) / tiles;
+        const int64_t maxs = std::max<int64_t>(1, I.n_pad / 4096);
+        splits = (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 64}));
+      }
+      ++P->n_simt;
+    } else if (is_tc(I.path)) {
+      const int64_t tiles = (int64_t)I.tiles_m * I.tiles_n;
+      if (splits == 0) {
+        if (count == 1) {
+          splits = choose_tc_splits(tiles, ctas, I.n_pad);
+        } else {
+          const double want = std::ceil((double)I.n_pad / std::max(target_item, 1.0));
+          splits = (int)std::max(1.0, std::min({want, 64.0, (double)(I.n_pad / 256)}));
+        }
+      }
+      const int64_t ks = t.stage_points;
+      I.per_split = ((I.n_pad + splits - 1) / splits + ks - 1) / ks * ks;
+      I.items = (int)(tiles * splits);
+      P->tc_order.push_back(k);
+      ++P->n_tc;
+    } else {  // cutoff
+      splits = 1;
+      I.geo = cutoff_geometry(a->nx, a->ny, a->cell, a->h);
+      I.bin_begin = (int)P->total_bins;
+      P->total_bins += I.geo.nbins;
+      I.cut_begin = P->cut_m;
+      P->cut_m += I.n_pad;
+      ++P->n_cut;
+    }
+    I.splits = std::max(splits, 1);
+    if (I.splits > 1) {
+      ++P->n_reduce;
+      P->reduce_cells += (int64_t)a->nx * a->ny;
+    }
+  }
+  if (P->total_bins >= ((int64_t)1 << 31)) return fail(KDE_EINVAL, "too many bins in one batch");
+  // most expensive work items first, so round-robin CTAs balance
+  std::stable_sort(P->tc_order.begin(), P->tc_order.end(), [&](int x, int y) {
+    return P->in[x].per_split > P->in[y].per_split;
+  });
+  for (int k : P->tc_order) P->tc_items += P->in[k].items;
+  if ((int64_t)P->tc_items > 0x7fffffff) return fail(KDE_EINVAL, "too many work items");
+  P->cz = cutoff_sizes(P->cut_m, P->total_bins);
+
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
-  p->off_scal = take(sizeof(CallScalars));
-  p->off_pts = take(sizeof(float4) * (size_t)p->n_pad);
-  p->off_wts = take(sizeof(float) * (size_t)p->n_pad);
-  p->off_gxt = take(sizeof(float2) * (size_t)a->nx);
-  p->off_gyt = take(sizeof(float2) * (size_t)a->ny);
-  p->off_part = take(p->splits > 1 ? sizeof(float) * (size_t)cells * p->splits : 0);
-  p->off_hxy = take(p->host_pts ? sizeof(double) * 2 * (size_t)n : 0);
-  p->off_hw = take(p->host_w ? sizeof(float) * (size_t)n : 0);
-  p->off_hout = take(p->host_out ? sizeof(float) * (size_t)cells : 0);
-  if (p->path == KDE_PATH_CUTOFF) {
-    p->co = plan_cutoff(a->nx, a->ny, a->cell, a->h, p->n_pad);
+  P->off_scal = take(sizeof(CallScalars) * (size_t)(count + 1));
+  P->off_pts = take(sizeof(float4) * (size_t)P->total_pad);
+  P->off_wts = take(sizeof(float) * (size_t)P->total_pad);
+  P->off_tab_prep = take(sizeof(PrepInst) * (size_t)count);
+  P->off_tab_tc = take(sizeof(TcInst) * (size_t)std::max(P->n_tc, 1));
+  P->off_tab_cut = take(sizeof(CutInst) * (size_t)std::max(P->n_cut, 1));
+  P->off_tab_red = take(sizeof(ReduceInst) * (size_t)std::max(P->n_reduce, 1));
+  for (int k = 0; k < count; ++k) {
+    InstPlan& I = P->in[k];
+    I.off_gxt = take(sizeof(float2) * (size_t)A[k].nx);
+    I.off_gyt = take(sizeof(float2) * (size_t)A[k].ny);
+    I.off_part = I.splits > 1 ? take(sizeof(float) * (size_t)A[k].nx * A[k].ny * I.splits) : 0;
+  }
+  if (P->n_cut) {
     const size_t u = sizeof(uint32_t);
     for (int k = 0; k < 2; ++k) {
-      p->off_co_keys[k] = take(u * (size_t)p->n_pad);
-      p->off_co_vals[k] = take(u * (size_t)p->n_pad);
+      P->off_co_keys[k] = take(u * (size_t)P->cut_m);
+      P->off_co_vals[k] = take(u * (size_t)P->cut_m);
     }
-    p->off_co_hist = take(u * p->co.hist_words);
-    p->off_co_hscan = take(u * p->co.hist_words);
-    p->off_co_stemp = take(u * (p->co.scan_words + 64));
-    p->off_co_start = take(u * ((size_t)p->co.nbins + 1));
-    p->off_co_spts = take(sizeof(float4) * (size_t)p->n_pad);
-    p->off_co_sw = take(sizeof(float) * (size_t)p->n_pad);
+    P->off_co_hist = take(u * P->cz.hist_words);
+    P->off_co_hscan = take(u * P->cz.hist_words);
+    P->off_co_stemp = take(u * (P->cz.scan_words + 64));
+    P->off_co_start = take(u * ((size_t)P->total_bins + 1));
+    P->off_co_spts = take(sizeof(float4) * (size_t)P->cut_m);
+    P->off_co_sw = take(sizeof(float) * (size_t)P->cut_m);
   }
-  p->total = off;
+  P->off_hxy = take(P->host_pts ? sizeof(double) * 2 * (size_t)A[0].n : 0);
+  P->off_hw = take(P->host_w ? sizeof(float) * (size_t)A[0].n : 0);
+  P->off_hout = take(P->host_out ? sizeof(float) * (size_t)A[0].nx * A[0].ny : 0);
+  P->total = off;
   return KDE_OK;
 }
 
@@ -251,113 +350,222 @@ cudaStream_t stream_of(const kde_opts* o) {
   return o ? reinterpret_cast<cudaStream_t>(o->stream) : (cudaStream_t)0;
 }
 
-int run_grid(const kde_args* a, const kde_opts* o, bool force_sync) {
-  int rc = validate(a, o);
-  if (rc) return rc;
-  Plan pl;
-  rc = make_plan(a, o, true, &pl);
-  if (rc) return rc;
-  cudaStream_t s = stream_of(o);
-  const bool sync = force_sync || (o && (o->flags & KDE_FLAG_SYNC)) || pl.host_out;
-  const int64_t cells = (int64_t)a->nx * a->ny;
-
-  void* ws = nullptr;
+int acquire_workspace(const kde_opts* o, size_t need, cudaStream_t s, void** ws) {
   if (o && o->workspace) {
-    if (o->workspace_bytes < pl.total)
-      return fail(KDE_ENOMEM, "caller workspace has %zu bytes, %zu needed", o->workspace_bytes,
-                  pl.total);
-    ws = o->workspace;
-  } else {
-    rc = library_workspace(pl.total, &ws);
+    if (o->workspace_bytes < need)
+      return fail(KDE_ENOMEM, "caller workspace has %zu bytes, %zu needed", o->workspace_bytes, need);
+    *ws = o->workspace;
+    return KDE_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    if (dev < 0 || dev >= kMaxDevices || g_ws_bytes[dev] < need)
+      return fail(KDE_ENOMEM, "the workspace must hold %zu bytes before stream capture "
+                  "(make the same call once outside capture, or pass opts->workspace)", need);
+    *ws = g_ws_ptr[dev];
+    return KDE_OK;
+  }
+  cudaGetLastError();
+  return library_workspace(need, ws);
+}
+
+// Plan, lay out, upload and launch every instance of a batch on one stream.
+int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) {
+  for (int k = 0; k < count; ++k) {
+    int rc = validate(&A[k], o);
     if (rc) return rc;
   }
-  char* base = static_cast<char*>(ws);
-  CallScalars* scal = reinterpret_cast<CallScalars*>(base + pl.off_scal);
-  float* out_dev = pl.host_out ? reinterpret_cast<float*>(base + pl.off_hout) : a->out;
+  BatchPlan P;
+  int rc = make_plan(A, count, o, true, &P);
+  if (rc) return rc;
+  cudaStream_t s = stream_of(o);
+  const bool sync = force_sync || (o && (o->flags & KDE_FLAG_SYNC)) || P.host_out;
+  void* wsv = nullptr;
+  rc = acquire_workspace(o, P.total, s, &wsv);
+  if (rc) return rc;
+  char* base = static_cast<char*>(wsv);
+  CallScalars* scal = reinterpret_cast<CallScalars*>(base + P.off_scal);
+  CallScalars* batch_scal = scal + count;
+  float4* pts = reinterpret_cast<float4*>(base + P.off_pts);
+  float* wts = reinterpret_cast<float*>(base + P.off_wts);
 
-  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars), s), "clear scalars");
-  if (a->n == 0) {
-    KDE_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(float) * cells, s), "zero output");
-  } else {
-    const double* xy = a->points;
-    const float* w = a->weights;
-    if (pl.host_pts) {
-      double* d = reinterpret_cast<double*>(base + pl.off_hxy);
-      KDE_CUDA(cudaMemcpyAsync(d, xy, sizeof(double) * 2 * a->n, cudaMemcpyHostToDevice, s),
-               "copy points to device");
-      xy = d;
-    }
-    if (pl.host_w) {
-      float* d = reinterpret_cast<float*>(base + pl.off_hw);
-      KDE_CUDA(cudaMemcpyAsync(d, w, sizeof(float) * a->n, cudaMemcpyHostToDevice, s),
-               "copy weights to device");
-      w = d;
-    }
-    float4* pts = reinterpret_cast<float4*>(base + pl.off_pts);
-    float* wts = reinterpret_cast<float*>(base + pl.off_wts);
-    float2* gxt = reinterpret_cast<float2*>(base + pl.off_gxt);
-    float2* gyt = reinterpret_cast<float2*>(base + pl.off_gyt);
-    const double sigma = kernel_sigma(a->kernel_id, a->h);
-    KDE_CUDA(launch_prepare(xy, w, a->n, pl.n_pad, a->origin_x, a->origin_y, sigma, pts, wts, scal, s),
-             "prepare points");
-    KDE_CUDA(launch_grid_tables(a->nx, a->ny, a->cell, sigma, gxt, gyt, s), "grid tables");
-    const double c1 = kernel_const_1d(a->kernel_id);
-    const float scale = (float)(c1 * c1 / ((double)a->n * a->h * a->h));
-    float* part = pl.splits > 1 ? reinterpret_cast<float*>(base + pl.off_part) : out_dev;
-    cudaEvent_t* ev = o ? static_cast<cudaEvent_t*>(o->timing_events) : nullptr;
-    if (ev) KDE_CUDA(cudaEventRecord(ev[0], s), "record start event");
-    switch (pl.path) {
-      case KDE_PATH_SIMT_FP32:
-        KDE_CUDA(launch_simt(a->kernel_id, pts, wts, pl.n_pad, gxt, gyt, a->nx, a->ny, pl.splits,
-                             scale, part, s),
-                 "SIMT direct sum");
-        break;
-      case KDE_PATH_TC_FP16:
-      case KDE_PATH_TC_SPLIT16: {
-        // c = 2^-30 / (2 pi N h^2); the kernel multiplies by max |w|
-        const double base = 0x1p-30 / (2.0 * 3.14159265358979323846 * (double)a->n * a->h * a->h);
-        KDE_CUDA(launch_tc(pl.tc, pts, wts, pl.n_pad, gxt, gyt, a->nx, a->ny, (float)base, scal,
-                           part, scal, s),
-                 "tensor-core contraction");
-        break;
-      }
-      case KDE_PATH_CUTOFF: {
-        CutoffScratch cs;
-        for (int k = 0; k < 2; ++k) {
-          cs.keys[k] = reinterpret_cast<uint32_t*>(base + pl.off_co_keys[k]);
-          cs.vals[k] = reinterpret_cast<uint32_t*>(base + pl.off_co_vals[k]);
-        }
-        cs.hist = reinterpret_cast<uint32_t*>(base + pl.off_co_hist);
-        cs.hist_scan = reinterpret_cast<uint32_t*>(base + pl.off_co_hscan);
-        cs.scan_temp = reinterpret_cast<uint32_t*>(base + pl.off_co_stemp);
-        cs.start = reinterpret_cast<uint32_t*>(base + pl.off_co_start);
-        cs.spts = reinterpret_cast<float4*>(base + pl.off_co_spts);
-        cs.sw = reinterpret_cast<float*>(base + pl.off_co_sw);
-        KDE_CUDA(launch_cutoff(a->kernel_id, pl.co, pts, wts, a->n, pl.n_pad, a->cell, a->h, gxt,
-                               gyt, a->nx, a->ny, scale, cs, part, s),
-                 "cutoff evaluation");
-        break;
-      }
-      default:
-        return fail(KDE_ENOTSUP, "path %d is not available in this build", pl.path);
-    }
-    if (ev) KDE_CUDA(cudaEventRecord(ev[1], s), "record end event");
-    if (pl.splits > 1)
-      KDE_CUDA(launch_reduce_splits(part, pl.splits, cells, out_dev, s), "split-K reduce");
+  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars) * (size_t)(count + 1), s), "clear scalars");
+  const double* xy0 = A[0].points;
+  const float* w0 = A[0].weights;
+  if (P.host_pts) {
+    double* d = reinterpret_cast<double*>(base + P.off_hxy);
+    KDE_CUDA(cudaMemcpyAsync(d, xy0, sizeof(double) * 2 * A[0].n, cudaMemcpyHostToDevice, s),
+             "copy points to device");
+    xy0 = d;
   }
-  if (pl.host_out)
-    KDE_CUDA(cudaMemcpyAsync(a->out, out_dev, sizeof(float) * cells, cudaMemcpyDeviceToHost, s),
+  if (P.host_w) {
+    float* d = reinterpret_cast<float*>(base + P.off_hw);
+    KDE_CUDA(cudaMemcpyAsync(d, w0, sizeof(float) * A[0].n, cudaMemcpyHostToDevice, s),
+             "copy weights to device");
+    w0 = d;
+  }
+
+  // ---- tables
+  std::vector<PrepInst> prep(count);
+  std::vector<TcInst> tct;
+  std::vector<CutInst> cut;
+  std::vector<ReduceInst> red;
+  std::vector<float*> out_dev(count);
+  for (int k = 0; k < count; ++k) {
+    const kde_args* a = &A[k];
+    const InstPlan& I = P.in[k];
+    out_dev[k] = (k == 0 && P.host_out) ? reinterpret_cast<float*>(base + P.off_hout) : a->out;
+    PrepInst& q = prep[k];
+    q.xy = k == 0 ? xy0 : a->points;
+    q.w = k == 0 ? w0 : a->weights;
+    q.pts = pts + I.prep_begin;
+    q.wts = wts + I.prep_begin;
+    q.gxt = reinterpret_cast<float2*>(base + I.off_gxt);
+    q.gyt = reinterpret_cast<float2*>(base + I.off_gyt);
+    q.scal = scal + k;
+    q.n = a->n;
+    q.n_pad = I.n_pad;
+    q.begin = I.prep_begin;
+    q.ox = a->origin_x;
+    q.oy = a->origin_y;
+    q.sigma = kernel_sigma(a->kernel_id, a->h);
+    q.cell_sigma = a->cell * q.sigma;
+    q.nx = a->nx;
+    q.ny = a->ny;
+  }
+  auto part_of = [&](int k) {
+    return P.in[k].splits > 1 ? reinterpret_cast<float*>(base + P.in[k].off_part) : out_dev[k];
+  };
+  auto compact_scale = [&](int k) {
+    const double c1 = kernel_const_1d(A[k].kernel_id);
+    return A[k].n > 0 ? (float)(c1 * c1 / ((double)A[k].n * A[k].h * A[k].h)) : 0.0f;
+  };
+  int item_begin = 0;
+  for (int k : P.tc_order) {
+    const kde_args* a = &A[k];
+    const InstPlan& I = P.in[k];
+    TcInst q;
+    q.pts = prep[k].pts;
+    q.wts = prep[k].wts;
+    q.gxt = prep[k].gxt;
+    q.gyt = prep[k].gyt;
+    q.scal = scal + k;
+    q.part = part_of(k);
+    q.n_pad = I.n_pad;
+    q.per_split = I.per_split;
+    q.nx = a->nx;
+    q.ny = a->ny;
+    q.tiles_m = I.tiles_m;
+    q.tiles_n = I.tiles_n;
+    q.splits = I.splits;
+    q.item_begin = item_begin;
+    q.chunk_stages = P.tc.k_chunk / P.tc.stage_points;
+    // c = 2^-30 / (2 pi N h^2); the kernel multiplies by max |w|
+    q.base_scale = a->n > 0 ? (float)(0x1p-30 / (2.0 * 3.14159265358979323846 * (double)a->n *
+                                                 a->h * a->h))
+                            : 0.0f;
+    item_begin += I.items;
+    tct.push_back(q);
+  }
+  for (int k = 0; k < count; ++k) {
+    const InstPlan& I = P.in[k];
+    if (I.path == KDE_PATH_CUTOFF) {
+      CutInst q;
+      q.gxt = prep[k].gxt;
+      q.gyt = prep[k].gyt;
+      q.out = out_dev[k];
+      q.n = A[k].n;
+      q.n_pad = I.n_pad;
+      q.prep_begin = I.prep_begin;
+      q.cut_begin = I.cut_begin;
+      q.inv_binw = I.geo.inv_binw;
+      q.ext_x = I.geo.ext_x;
+      q.ext_y = I.geo.ext_y;
+      q.nbx = I.geo.nbx;
+      q.nby = I.geo.nby;
+      q.R = I.geo.R;
+      q.bin_begin = I.bin_begin;
+      q.nx = A[k].nx;
+      q.ny = A[k].ny;
+      q.kid = A[k].kernel_id;
+      q.scale = compact_scale(k);
+      cut.push_back(q);
+    }
+    if (I.splits > 1) {
+      ReduceInst q;
+      q.part = part_of(k);
+      q.out = out_dev[k];
+      q.cells = (int64_t)A[k].nx * A[k].ny;
+      q.begin = red.empty() ? 0 : red.back().begin + red.back().cells;
+      q.splits = I.splits;
+      red.push_back(q);
+    }
+  }
+  PrepInst* d_prep = reinterpret_cast<PrepInst*>(base + P.off_tab_prep);
+  TcInst* d_tc = reinterpret_cast<TcInst*>(base + P.off_tab_tc);
+  CutInst* d_cut = reinterpret_cast<CutInst*>(base + P.off_tab_cut);
+  ReduceInst* d_red = reinterpret_cast<ReduceInst*>(base + P.off_tab_red);
+  KDE_CUDA(launch_upload(prep.data(), sizeof(PrepInst) * prep.size(), d_prep, s), "upload tables");
+  if (!tct.empty())
+    KDE_CUDA(launch_upload(tct.data(), sizeof(TcInst) * tct.size(), d_tc, s), "upload tables");
+  if (!cut.empty())
+    KDE_CUDA(launch_upload(cut.data(), sizeof(CutInst) * cut.size(), d_cut, s), "upload tables");
+  if (!red.empty())
+    KDE_CUDA(launch_upload(red.data(), sizeof(ReduceInst) * red.size(), d_red, s), "upload tables");
+
+  // ---- launches
+  KDE_CUDA(launch_prepare(d_prep, count, P.total_pad, P.max_side, s), "prepare points");
+  cudaEvent_t* ev = o ? static_cast<cudaEvent_t*>(o->timing_events) : nullptr;
+  if (ev) KDE_CUDA(cudaEventRecord(ev[0], s), "record start event");
+  if (P.n_tc)
+    KDE_CUDA(launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s), "tensor-core contraction");
+  for (int k = 0; k < count; ++k) {
+    const InstPlan& I = P.in[k];
+    if (I.path != KDE_PATH_SIMT_FP32) continue;
+    KDE_CUDA(launch_simt(A[k].kernel_id, prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
+                         prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k), part_of(k), s),
+             "SIMT direct sum");
+  }
+  if (P.n_cut) {
+    CutoffScratch cs;
+    for (int k = 0; k < 2; ++k) {
+      cs.keys[k] = reinterpret_cast<uint32_t*>(base + P.off_co_keys[k]);
+      cs.vals[k] = reinterpret_cast<uint32_t*>(base + P.off_co_vals[k]);
+    }
+    cs.hist = reinterpret_cast<uint32_t*>(base + P.off_co_hist);
+    cs.hist_scan = reinterpret_cast<uint32_t*>(base + P.off_co_hscan);
+    cs.scan_temp = reinterpret_cast<uint32_t*>(base + P.off_co_stemp);
+    cs.start = reinterpret_cast<uint32_t*>(base + P.off_co_start);
+    cs.spts = reinterpret_cast<float4*>(base + P.off_co_spts);
+    cs.sw = reinterpret_cast<float*>(base + P.off_co_sw);
+    KDE_CUDA(launch_cutoff(d_cut, P.n_cut, P.cut_m, P.total_bins, pts, wts, P.cz, cs, s),
+             "cutoff evaluation");
+  }
+  if (ev) KDE_CUDA(cudaEventRecord(ev[1], s), "record end event");
+  if (P.n_reduce) KDE_CUDA(launch_reduce(d_red, P.n_reduce, P.reduce_cells, s), "split-K reduce");
+  if (P.host_out)
+    KDE_CUDA(cudaMemcpyAsync(A[0].out, out_dev[0], sizeof(float) * A[0].nx * A[0].ny,
+                             cudaMemcpyDeviceToHost, s),
              "copy result to host");
   if (sync) {
-    CallScalars hs;
-    KDE_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(int) * 3, cudaMemcpyDeviceToHost, s), "read status");
+    std::vector<CallScalars> hs(count + 1);
+    KDE_CUDA(cudaMemcpyAsync(hs.data(), scal, sizeof(CallScalars) * (count + 1),
+                             cudaMemcpyDeviceToHost, s),
+             "read status");
     KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
-    if (hs.err & kErrTimeout)
-      return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs.timeout_where);
-    if (hs.err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
-    if (hs.err & kErrNegWeight)
-      return fail(KDE_EDATA, "the tensor-core paths need non-negative weights");
-    if (hs.err) return fail(KDE_ECUDA, "device error word 0x%x", hs.err);
+    for (int k = 0; k <= count; ++k) {
+      const int err = hs[k].err;
+      if (err & kErrTimeout)
+        return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs[k].timeout_where);
+      if (err & kErrNonFinite)
+        return fail(KDE_EDATA, "instance %d: non-finite coordinate or weight", k);
+      if (err & kErrNegWeight)
+        return fail(KDE_EDATA, "the tensor-core paths need non-negative weights");
+      if (err) return fail(KDE_ECUDA, "device error word 0x%x", err);
+    }
   }
   g_err[0] = 0;
   return KDE_OK;
@@ -393,17 +601,20 @@ int kde_grid(const double* points, const float* weights, int64_t n, const double
   a.out = out;
   kde_opts o;
   kde_default_opts(&o);
-  return run_grid(&a, &o, true);
+  return run_batch(&a, 1, &o, true);
 }
 
-int kde_grid_ex(const kde_args* a, const kde_opts* opts) { return run_grid(a, opts, false); }
+int kde_grid_ex(const kde_args* a, const kde_opts* opts) {
+  if (!a) return fail(KDE_EINVAL, "args is NULL");
+  return run_batch(a, 1, opts, false);
+}
 
 int kde_workspace_size(const kde_args* a, const kde_opts* opts, size_t* bytes) {
   if (!bytes) return fail(KDE_EINVAL, "bytes is NULL");
   int rc = validate(a, opts);
   if (rc) return rc;
-  Plan pl;
-  rc = make_plan(a, opts, true, &pl);
+  BatchPlan pl;
+  rc = make_plan(a, 1, opts, true, &pl);
   if (rc) return rc;
   *bytes = pl.total;
   return KDE_OK;
@@ -426,10 +637,14 @@ int kde_project_mercator(const double* lonlat_deg, int64_t n, double lat0_deg, d
 }
 
 int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts) {
-  (void)inst;
-  (void)count;
-  (void)opts;
-  return fail(KDE_ENOTSUP, "kde_grid_batched is not available in this build");
+  if (!inst || count < 0) return fail(KDE_EINVAL, "inst is NULL or count < 0");
+  for (int b = 0; b < count; b += kMaxBatch) {
+    const int c = std::min(kMaxBatch, count - b);
+    const int rc = run_batch(inst + b, c, opts, false);
+    if (rc) return rc;
+  }
+  if (opts && (opts->flags & KDE_FLAG_SYNC) && count == 0) g_err[0] = 0;
+  return KDE_OK;
 }
 
 int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_points,

@@ -22,27 +22,40 @@ constexpr int kSortRounds = 8;      // 32-element rounds per warp
 constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
 constexpr int kBatch = 64;          // points per shared-memory batch
 
-// Bin key of each point (centred, scaled by 1/h): key = by * nbx + bx, or
-// nbins for padding and for points that cannot reach the grid.
-__global__ void k_bin_keys(const float4* __restrict__ pts, int64_t n, int64_t n_pad,
-                           double inv_binw, double ext_x, double ext_y, int nbx, int nby,
+template <class T>
+__device__ __forceinline__ int find_by(const T* tab, int ninst, int64_t v, int64_t T::*field) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].*field <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bin key of each point of every instance (points centred and scaled by 1/h):
+// key = bin_begin + by * nbx + bx, or total_bins for padding and for points
+// that cannot reach their grid.  vals = the point's index in the prepared
+// arrays.
+__global__ void k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m,
+                           const float4* __restrict__ prepared, uint32_t total_bins,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const uint32_t nbins = (uint32_t)nbx * nby;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += stride) {
-    uint32_t key = nbins;
-    if (p < n) {
-      const float4 q = pts[p];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < m; g += stride) {
+    const CutInst& I = tab[find_by(tab, ninst, g, &CutInst::cut_begin)];
+    const int64_t p = g - I.cut_begin;
+    uint32_t key = total_bins;
+    if (p < I.n) {
+      const float4 q = prepared[I.prep_begin + p];
       const double X = (double)q.x + (double)q.y, Y = (double)q.z + (double)q.w;
-      // a point reaches the grid only if it lies within one bandwidth (+ a cell) of it
-      if (X >= -1.0 && Y >= -1.0 && X <= ext_x && Y <= ext_y) {
-        const int bx = min(max((int)floor(X * inv_binw), 0), nbx - 1);
-        const int by = min(max((int)floor(Y * inv_binw), 0), nby - 1);
-        key = (uint32_t)by * nbx + bx;
+      // a point reaches the grid only if it lies within one bandwidth of it
+      if (X >= -1.0 && Y >= -1.0 && X <= I.ext_x && Y <= I.ext_y) {
+        const int bx = min(max((int)floor(X * I.inv_binw), 0), I.nbx - 1);
+        const int by = min(max((int)floor(Y * I.inv_binw), 0), I.nby - 1);
+        key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
       }
     }
-    keys[p] = key;
-    vals[p] = (uint32_t)p;
+    keys[g] = key;
+    vals[g] = (uint32_t)(I.prep_begin + p);
   }
 }
 
@@ -146,33 +159,52 @@ __global__ void k_permute(const float4* __restrict__ pts, const float* __restric
   }
 }
 
-// One CTA per 32x32 output bin; thread (cx, 4 rows).
-template <int KID>
+__device__ __forceinline__ float kfactor_rt(int kid, float d) {
+  switch (kid) {
+    case KDE_UNIFORM: return kfactor<KDE_UNIFORM>(d);
+    case KDE_TRIANGULAR: return kfactor<KDE_TRIANGULAR>(d);
+    case KDE_EPANECHNIKOV: return kfactor<KDE_EPANECHNIKOV>(d);
+    case KDE_QUARTIC: return kfactor<KDE_QUARTIC>(d);
+    case KDE_TRIWEIGHT: return kfactor<KDE_TRIWEIGHT>(d);
+    case KDE_TRICUBE: return kfactor<KDE_TRICUBE>(d);
+    default: return kfactor<KDE_COSINE>(d);
+  }
+}
+
+// One CTA per 32x32 output bin of some instance (blockIdx.x = global bin);
+// thread (cx, 4 rows).
 __global__ void __launch_bounds__(256)
-    k_cutoff(const float4* __restrict__ P, const float* __restrict__ W,
-             const uint32_t* __restrict__ start, int nbx, int nby, int R,
-             const float2* __restrict__ gxt, const float2* __restrict__ gyt, int nx, int ny,
-             float scale, float* __restrict__ out) {
+    k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
+             const float* __restrict__ W, const uint32_t* __restrict__ start) {
   __shared__ float4 sP[kBatch];
   __shared__ float sW[kBatch];
   __shared__ __align__(16) float KX[kBatch][kBin];
   __shared__ __align__(16) float KY[kBatch][kBin];
   __shared__ float2 sgx[kBin], sgy[kBin];
-  const int bx = blockIdx.x, by = blockIdx.y;
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].bin_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const CutInst& I = tab[lo];
+  const int local = blockIdx.x - I.bin_begin;
+  const int bx = local % I.nbx, by = local / I.nbx;
+  const int nx = I.nx, ny = I.ny, R = I.R, kid = I.kid;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int t = threadIdx.x;
   const int cx = t & 31, cy0 = (t >> 5) * 4;
-  if (t < kBin) sgx[t] = gxt[min(x0 + t, nx - 1)];
-  else if (t < 2 * kBin) sgy[t - kBin] = gyt[min(y0 + t - kBin, ny - 1)];
+  if (t < kBin) sgx[t] = I.gxt[min(x0 + t, nx - 1)];
+  else if (t < 2 * kBin) sgy[t - kBin] = I.gyt[min(y0 + t - kBin, ny - 1)];
   float2 run[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) run[r] = make_float2(0.f, 0.f);
   // evaluation role: point c = t / 4, eight columns / rows starting at j0
   const int ec = t >> 2, ej0 = (t & 3) * 8;
 
-  for (int qy = max(by - R, 0); qy <= min(by + R, nby - 1); ++qy) {
-    const int qx0 = max(bx - R, 0), qx1 = min(bx + R, nbx - 1);
-    const uint32_t s = start[qy * nbx + qx0], e = start[qy * nbx + qx1 + 1];
+  for (int qy = max(by - R, 0); qy <= min(by + R, I.nby - 1); ++qy) {
+    const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
+    const int row = I.bin_begin + qy * I.nbx;
+    const uint32_t s = start[row + qx0], e = start[row + qx1 + 1];
     for (uint32_t b = s; b < e; b += kBatch) {
       const int cnt = (int)min((uint32_t)kBatch, e - b);
       __syncthreads();  // previous batch fully consumed
@@ -187,8 +219,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float2 gx = sgx[ej0 + j], gy = sgy[ej0 + j];
-          KX[ec][ej0 + j] = kfactor<KID>((gx.x - p.x) + (gx.y - p.y));
-          KY[ec][ej0 + j] = w * kfactor<KID>((gy.x - p.z) + (gy.y - p.w));
+          KX[ec][ej0 + j] = kfactor_rt(kid, (gx.x - p.x) + (gx.y - p.y));
+          KY[ec][ej0 + j] = w * kfactor_rt(kid, (gy.x - p.z) + (gy.y - p.w));
         }
       }
       __syncthreads();
@@ -210,7 +242,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int y = y0 + cy0 + r;
-      if (y < ny) out[(int64_t)y * nx + x] = (run[r].x + run[r].y) * scale;
+      if (y < ny) I.out[(int64_t)y * nx + x] = (run[r].x + run[r].y) * I.scale;
     }
   }
 }
@@ -222,73 +254,63 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-CutoffPlan plan_cutoff(int nx, int ny, double cell, double h, int64_t n_pad) {
-  CutoffPlan c;
-  c.nbx = (nx + kBin - 1) / kBin;
-  c.nby = (ny + kBin - 1) / kBin;
-  c.nbins = c.nbx * c.nby;
+CutoffGeom cutoff_geometry(int nx, int ny, double cell, double h) {
+  CutoffGeom g;
+  g.nbx = (nx + kBin - 1) / kBin;
+  g.nby = (ny + kBin - 1) / kBin;
+  g.nbins = g.nbx * g.nby;
   // bins a point can reach: its support (h) plus half a cell, in 32-cell bins
-  c.R = (int)ceil((h / cell + 1.0) / kBin);
-  c.nchunks = (int)((n_pad + kSortChunk - 1) / kSortChunk);
-  int bits = 1;
-  while ((1ll << bits) <= (long long)c.nbins) ++bits;  // keys 0..nbins
-  c.passes = (bits + 7) / 8;
-  c.hist_words = (size_t)256 * c.nchunks;
-  c.scan_words = scan_temp_words((int64_t)c.hist_words, 2048);
-  return c;
+  g.R = (int)ceil((h / cell + 1.0) / kBin);
+  const double cell_s = cell / h;  // cell side in bandwidths
+  g.inv_binw = 1.0 / (kBin * cell_s);
+  g.ext_x = nx * cell_s + 1.0;
+  g.ext_y = ny * cell_s + 1.0;
+  return g;
 }
 
-cudaError_t launch_cutoff(int kid, const CutoffPlan& c, const float4* pts, const float* wts,
-                          int64_t n, int64_t n_pad, double cell, double h, const float2* gxt,
-                          const float2* gyt, int nx, int ny, float scale, CutoffScratch ws,
-                          float* out, cudaStream_t s) {
-  const double cell_s = cell / h;  // cell side in bandwidths
-  k_bin_keys<<<grid_for(n_pad), 256, 0, s>>>(pts, n, n_pad, 1.0 / (kBin * cell_s),
-                                             nx * cell_s + 1.0, ny * cell_s + 1.0, c.nbx, c.nby,
-                                             ws.keys[0], ws.vals[0]);
+CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {
+  CutoffSizes z;
+  z.nchunks = (int)((m + kSortChunk - 1) / kSortChunk);
+  int bits = 1;
+  while ((1ll << bits) <= (long long)total_bins) ++bits;  // keys 0..total_bins
+  z.passes = (bits + 7) / 8;
+  z.hist_words = (size_t)256 * z.nchunks;
+  z.scan_words = scan_temp_words((int64_t)z.hist_words, 2048);
+  return z;
+}
+
+cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
+                          const float4* prepared, const float* prepared_w, const CutoffSizes& z,
+                          CutoffScratch ws, cudaStream_t s) {
+  if (ninst <= 0 || m <= 0) return cudaSuccess;
+  k_bin_keys<<<grid_for(m), 256, 0, s>>>(tab, ninst, m, prepared, (uint32_t)total_bins,
+                                         ws.keys[0], ws.vals[0]);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int cur = 0;
-  for (int pass = 0; pass < c.passes; ++pass) {
+  for (int pass = 0; pass < z.passes; ++pass) {
     const int shift = 8 * pass;
-    k_radix_count<<<c.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], n_pad, shift, c.nchunks, ws.hist);
+    k_radix_count<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], m, shift, z.nchunks, ws.hist);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_exclusive_scan(ws.hist, ws.hist_scan, (int64_t)c.hist_words, 2048, ws.scan_temp, s);
+    e = launch_exclusive_scan(ws.hist, ws.hist_scan, (int64_t)z.hist_words, 2048, ws.scan_temp, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<<<c.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], n_pad, shift,
-                                                        c.nchunks, ws.hist_scan, ws.keys[cur ^ 1],
+    k_radix_scatter<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, shift,
+                                                        z.nchunks, ws.hist_scan, ws.keys[cur ^ 1],
                                                         ws.vals[cur ^ 1]);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cur ^= 1;
   }
-  k_bin_bounds<<<(c.nbins + 1 + 255) / 256, 256, 0, s>>>(ws.keys[cur], n_pad, c.nbins, ws.start);
+  k_bin_bounds<<<(int)((total_bins + 1 + 255) / 256), 256, 0, s>>>(ws.keys[cur], m,
+                                                                   (int)total_bins, ws.start);
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // only points that reach the grid are gathered: the first start[nbins] of the order
-  k_permute<<<grid_for(n_pad), 256, 0, s>>>(pts, wts, ws.vals[cur], n_pad, ws.spts, ws.sw);
+  k_permute<<<grid_for(m), 256, 0, s>>>(prepared, prepared_w, ws.vals[cur], m, ws.spts, ws.sw);
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  dim3 grid(c.nbx, c.nby);
-  switch (kid) {
-#define KDE_CASE(K)                                                                              \
-  case K:                                                                                        \
-    k_cutoff<K><<<grid, 256, 0, s>>>(ws.spts, ws.sw, ws.start, c.nbx, c.nby, c.R, gxt, gyt, nx, \
-                                     ny, scale, out);                                            \
-    break;
-    KDE_CASE(KDE_UNIFORM)
-    KDE_CASE(KDE_TRIANGULAR)
-    KDE_CASE(KDE_EPANECHNIKOV)
-    KDE_CASE(KDE_QUARTIC)
-    KDE_CASE(KDE_TRIWEIGHT)
-    KDE_CASE(KDE_TRICUBE)
-    KDE_CASE(KDE_COSINE)
-#undef KDE_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  k_cutoff<<<(unsigned)total_bins, 256, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -53,6 +53,60 @@ inline double kernel_sigma(int kid, double h) {
   return kid == KDE_GAUSSIAN ? 1.0 / (h * 1.17741002251547469101) : 1.0 / h;
 }
 
+// ------------------------------------------------------- instance tables
+// Every launch is driven by a table of per-instance descriptors that lives in
+// the workspace; a single density is a batch of one.  Tables are written by
+// launch_upload (a kernel whose parameters carry the bytes), so a whole call
+// can be captured in a CUDA graph.
+
+constexpr int kMaxBatch = 256;  // instances per batched launch
+
+struct PrepInst {
+  const double* xy;  // caller's points (device)
+  const float* w;    // caller's weights (device) or null
+  float4* pts;       // prepared points, n_pad entries
+  float* wts;
+  float2* gxt;
+  float2* gyt;
+  CallScalars* scal;
+  int64_t n, n_pad, begin;  // begin: offset in the flattened n_pad space
+  double ox, oy, sigma, cell_sigma;
+  int nx, ny;
+};
+
+struct TcInst {
+  const float4* pts;
+  const float* wts;
+  const float2* gxt;
+  const float2* gyt;
+  const CallScalars* scal;  // holds max |w| of the instance
+  float* part;              // [splits][ny][nx]
+  int64_t n_pad, per_split;
+  int nx, ny, tiles_m, tiles_n, splits, item_begin, chunk_stages;
+  float base_scale;  // 2^-30 / (2 pi N h^2); times max |w|
+};
+
+struct CutInst {
+  const float2* gxt;
+  const float2* gyt;
+  float* out;
+  int64_t n, n_pad, prep_begin, cut_begin;  // point ranges (prepared / cutoff spaces)
+  double inv_binw, ext_x, ext_y;
+  int nbx, nby, R, bin_begin, nx, ny, kid;
+  float scale;
+};
+
+struct ReduceInst {
+  const float* part;
+  float* out;
+  int64_t cells, begin;  // begin: offset in the flattened cell space
+  int splits;
+};
+
+// Write `bytes` host bytes to device memory `dst` in stream order (kernel
+// launches carrying the bytes as parameters; capturable).
+cudaError_t launch_upload(const void* bytes, size_t nbytes, void* dst, cudaStream_t s);
+
 // -------------------------------------------------------------- launches
 // All launch helpers enqueue on `s`, add the number of kernels they launched
 // to the process-wide counter, and return the launch status.
@@ -62,21 +116,17 @@ void note_launches(int k);
 cudaError_t launch_mercator(const double* lonlat, int64_t n, double lat0_deg, double* xy,
                             cudaStream_t s);
 
-cudaError_t launch_prepare(const double* xy, const float* w, int64_t n, int64_t n_pad,
-                           double ox, double oy, double sigma, float4* pts, float* wts,
-                           CallScalars* scal, cudaStream_t s);
-
-cudaError_t launch_grid_tables(int nx, int ny, double cell, double sigma, float2* gxt,
-                               float2* gyt, cudaStream_t s);
+// Centre / scale / split every instance's points and build its grid tables.
+cudaError_t launch_prepare(const PrepInst* tab, int ninst, int64_t total_pad, int max_side,
+                           cudaStream_t s);
 
 // Path (a): FP32 SIMT direct sum into part[S][ny][nx] (scaled).
 cudaError_t launch_simt(int kid, const float4* pts, const float* wts, int64_t n_pad,
                         const float2* gxt, const float2* gyt, int nx, int ny, int splits,
                         float scale, float* part, cudaStream_t s);
 
-// Sum S partial grids in fixed order (s = 0, 1, ...) into out.
-cudaError_t launch_reduce_splits(const float* part, int splits, int64_t cells, float* out,
-                                 cudaStream_t s);
+// Sum each instance's S partial grids in fixed order (s = 0, 1, ...).
+cudaError_t launch_reduce(const ReduceInst* tab, int ninst, int64_t total_cells, cudaStream_t s);
 
 // Exclusive scan of m counts, `per_block` (<= 2048) per block, multi-block
 // with propagation; temp needs scan_temp_words(m, per_block) words.
@@ -85,43 +135,43 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t m, 
                                   uint32_t* temp, cudaStream_t s);
 
 // Path (c): binned cutoff evaluation of the compact kernels.
-struct CutoffPlan {
-  int nbx, nby, nbins;  // 32x32-cell bins
-  int R;                // bins within reach of a point, per direction
-  int nchunks;          // radix-sort blocks of 2048 keys
-  int passes;           // 8-bit radix passes
-  size_t hist_words, scan_words;
+struct CutoffGeom {
+  int nbx, nby, nbins, R;
+  double inv_binw, ext_x, ext_y;
 };
+CutoffGeom cutoff_geometry(int nx, int ny, double cell, double h);
 struct CutoffScratch {
   uint32_t* keys[2];
   uint32_t* vals[2];
   uint32_t* hist;
   uint32_t* hist_scan;
   uint32_t* scan_temp;
-  uint32_t* start;  // [nbins + 1]
+  uint32_t* start;  // [total bins + 1]
   float4* spts;     // points in bin order
   float* sw;
 };
-CutoffPlan plan_cutoff(int nx, int ny, double cell, double h, int64_t n_pad);
-cudaError_t launch_cutoff(int kid, const CutoffPlan& c, const float4* pts, const float* wts,
-                          int64_t n, int64_t n_pad, double cell, double h, const float2* gxt,
-                          const float2* gyt, int nx, int ny, float scale, CutoffScratch ws,
-                          float* out, cudaStream_t s);
+struct CutoffSizes {
+  int nchunks, passes;
+  size_t hist_words, scan_words;
+};
+CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
+cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
+                          const float4* prepared, const float* prepared_w, const CutoffSizes& z,
+                          CutoffScratch ws, cudaStream_t s);
 
 // Path (b): Gaussian as a tcgen05 contraction.
 struct TcPlan {
-  int tile_n;      // 128 or 256 grid rows (y) per tile; tile_m is 128 (x)
-  int split16;     // 0: single FP16, 1: hi/lo split (three products)
-  int splits;      // point-range splits S (partials in part[S])
-  int k_chunk;     // points per TMEM accumulator drain (multiple of 64)
-  int ctas;        // persistent CTAs
-  int skip_zero;   // skip (tile, stage) pairs whose operands are all zero
+  int tile_n;        // 128 or 256 grid rows (y) per tile; tile_m is 128 (x)
+  int split16;       // 0: single FP16, 1: hi/lo split (three products)
+  int splits;        // point-range splits S (partials in part[S])
+  int k_chunk;       // points per TMEM accumulator drain
+  int ctas;          // persistent CTAs
+  int skip_zero;     // skip (tile, stage) pairs whose operands are all zero
   int stage_points;  // 32 or 64 points per pipeline stage
 };
 size_t tc_smem_bytes(const TcPlan& p);
-cudaError_t launch_tc(const TcPlan& plan, const float4* pts, const float* wts, int64_t n_pad,
-                      const float2* gxt, const float2* gyt, int nx, int ny, float scale,
-                      const CallScalars* scal_in, float* part, CallScalars* scal,
-                      cudaStream_t s);
+// One persistent launch over the work items of every instance in `tab`.
+cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
+                      CallScalars* err, cudaStream_t s);
 
 }  // namespace kde

@@ -4,6 +4,11 @@
 // centred, scaled coordinate into two FP32 numbers hi + lo.  These are the
 // only FP64 steps of the library: the projected coordinates are ~1e7 m and
 // their differences must be resolved to millimetres.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "kde_internal.cuh"
 
 namespace kde {
@@ -33,49 +38,72 @@ __device__ __forceinline__ float2 split_hi_lo(double v) {
   return make_float2(hi, lo);
 }
 
+// Instance of flattened index p: the last entry whose begin <= p.
+template <class T>
+__device__ __forceinline__ int find_instance(const T* tab, int ninst, int64_t p) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].begin <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Centre, scale, split; weights copied (unit when w == NULL); padding zeroed;
-// max |w| reduced for the tensor path's operand scaling.
-__global__ void k_prepare(const double* __restrict__ xy, const float* __restrict__ w, int64_t n,
-                          int64_t n_pad, double ox, double oy, double sigma,
-                          float4* __restrict__ pts, float* __restrict__ wts,
-                          CallScalars* __restrict__ scal) {
+// max |w| reduced per instance for the tensor path's operand scaling.  Every
+// instance's n_pad is a multiple of 512, so a warp never straddles two.
+__global__ void k_prepare(const PrepInst* __restrict__ tab, int ninst, int64_t total) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  unsigned wbits = 0;
-  bool bad = false;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += stride) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const PrepInst& I = tab[find_instance(tab, ninst, g)];
+    const int64_t p = g - I.begin;
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     float wv = 0.f;
-    if (p < n) {
-      const double2 v = reinterpret_cast<const double2*>(xy)[p];
-      const double X = (v.x - ox) * sigma;
-      const double Y = (v.y - oy) * sigma;
-      wv = w ? w[p] : 1.0f;
+    bool bad = false;
+    unsigned wbits = 0;
+    if (p < I.n) {
+      const double2 v = reinterpret_cast<const double2*>(I.xy)[p];
+      const double X = (v.x - I.ox) * I.sigma;
+      const double Y = (v.y - I.oy) * I.sigma;
+      wv = I.w ? I.w[p] : 1.0f;
       if (isfinite(X) && isfinite(Y) && isfinite(wv)) {
         const float2 sx = split_hi_lo(X), sy = split_hi_lo(Y);
         r = make_float4(sx.x, sx.y, sy.x, sy.y);
-        wbits = max(wbits, __float_as_uint(fabsf(wv)));
+        wbits = __float_as_uint(fabsf(wv));
       } else {
         bad = true;
         wv = 0.f;
       }
     }
-    pts[p] = r;
-    wts[p] = wv;
-  }
-  // warp-level max, one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) wbits = max(wbits, __shfl_xor_sync(0xffffffffu, wbits, o));
-  const unsigned anybad = __any_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    if (wbits) atomicMax(&scal->wmax_bits, wbits);
-    if (anybad) atomicOr(&scal->err, kErrNonFinite);
+    I.pts[p] = r;
+    I.wts[p] = wv;
+    // warp-level max, one atomic per warp (all lanes share the instance)
+    for (int o = 16; o > 0; o >>= 1) wbits = max(wbits, __shfl_xor_sync(0xffffffffu, wbits, o));
+    const unsigned anybad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (wbits) atomicMax(&I.scal->wmax_bits, wbits);
+      if (anybad) atomicOr(&I.scal->err, kErrNonFinite);
+    }
   }
 }
 
-__global__ void k_grid_tables(int nx, int ny, double cell_sigma, float2* __restrict__ gxt,
-                              float2* __restrict__ gyt) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < nx) gxt[t] = split_hi_lo(((double)t + 0.5) * cell_sigma);
-  if (t < ny) gyt[t] = split_hi_lo(((double)t + 0.5) * cell_sigma);
+// Cell-centre tables: blockIdx.y = instance.
+__global__ void k_grid_tables(const PrepInst* __restrict__ tab) {
+  const PrepInst& I = tab[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < max(I.nx, I.ny);
+       t += gridDim.x * blockDim.x) {
+    if (t < I.nx) I.gxt[t] = split_hi_lo(((double)t + 0.5) * I.cell_sigma);
+    if (t < I.ny) I.gyt[t] = split_hi_lo(((double)t + 0.5) * I.cell_sigma);
+  }
+}
+
+constexpr int kBlobBytes = 31 * 1024;
+struct Blob {
+  unsigned char bytes[kBlobBytes];
+};
+
+__global__ void k_upload(const __grid_constant__ Blob blob, int nbytes, unsigned char* dst) {
+  for (int i = threadIdx.x; i < nbytes; i += blockDim.x) dst[i] = blob.bytes[i];
 }
 
 int blocks_for(int64_t n, int threads) {
@@ -97,22 +125,35 @@ cudaError_t launch_mercator(const double* lonlat, int64_t n, double lat0_deg, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_prepare(const double* xy, const float* w, int64_t n, int64_t n_pad,
-                           double ox, double oy, double sigma, float4* pts, float* wts,
-                           CallScalars* scal, cudaStream_t s) {
-  if (n_pad <= 0) return cudaSuccess;
-  k_prepare<<<blocks_for(n_pad, 256), 256, 0, s>>>(xy, w, n, n_pad, ox, oy, sigma, pts, wts,
-                                                    scal);
+cudaError_t launch_prepare(const PrepInst* tab, int ninst, int64_t total_pad, int max_side,
+                           cudaStream_t s) {
+  if (ninst <= 0) return cudaSuccess;
+  if (total_pad > 0) {
+    k_prepare<<<blocks_for(total_pad, 256), 256, 0, s>>>(tab, ninst, total_pad);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((max_side + 255) / 256, ninst);
+  k_grid_tables<<<grid, 256, 0, s>>>(tab);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_grid_tables(int nx, int ny, double cell, double sigma, float2* gxt,
-                               float2* gyt, cudaStream_t s) {
-  const int m = nx > ny ? nx : ny;
-  k_grid_tables<<<(m + 255) / 256, 256, 0, s>>>(nx, ny, cell * sigma, gxt, gyt);
-  note_launches(1);
-  return cudaGetLastError();
+cudaError_t launch_upload(const void* bytes, size_t nbytes, void* dst, cudaStream_t s) {
+  static Blob blob;  // staging for the launch parameters (copied at launch)
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  const unsigned char* src = static_cast<const unsigned char*>(bytes);
+  for (size_t off = 0; off < nbytes; off += kBlobBytes) {
+    const int len = (int)std::min<size_t>(kBlobBytes, nbytes - off);
+    memcpy(blob.bytes, src + off, len);
+    k_upload<<<1, 256, 0, s>>>(blob, len, static_cast<unsigned char*>(dst) + off);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace kde

@@ -74,21 +74,31 @@ struct Cfg {
 };
 
 struct Item {
+  const TcInst* I;  // the instance the item belongs to
   int tm, tn, s;
   int64_t k_begin;
-  int nst;  // stages of 64 points
+  int nst;  // stages of KS points
 };
 
-__device__ __forceinline__ Item item_of(int it, int tiles_m, int tiles_n, int64_t per_split,
-                                        int64_t n_pad, int ks) {
+// Work item `it` of the whole launch: instance found by binary search on the
+// table's item_begin, then (x tile, y tile, point split) within it.
+__device__ __forceinline__ Item item_of(const TcInst* __restrict__ tab, int ninst, int it,
+                                        int ks) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].item_begin <= it) lo = mid; else hi = mid - 1;
+  }
   Item r;
-  r.tm = it % tiles_m;
-  const int rest = it / tiles_m;
-  r.tn = rest % tiles_n;
-  r.s = rest / tiles_n;
-  r.k_begin = (int64_t)r.s * per_split;
-  int64_t k_end = r.k_begin + per_split;
-  if (k_end > n_pad) k_end = n_pad;
+  r.I = tab + lo;
+  const int local = it - r.I->item_begin;
+  r.tm = local % r.I->tiles_m;
+  const int rest = local / r.I->tiles_m;
+  r.tn = rest % r.I->tiles_n;
+  r.s = rest / r.I->tiles_n;
+  r.k_begin = (int64_t)r.s * r.I->per_split;
+  int64_t k_end = r.k_begin + r.I->per_split;
+  if (k_end > r.I->n_pad) k_end = r.I->n_pad;
   r.nst = k_end > r.k_begin ? (int)((k_end - r.k_begin) / ks) : 0;
   return r;
 }
@@ -108,10 +118,7 @@ __device__ __forceinline__ int next_boundary(int h, int cs, int C) {
 
 template <int BN, bool SPLIT, int KS>
 __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
-    k_tc(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n_pad,
-         const float2* __restrict__ gxt, const float2* __restrict__ gyt, int nx, int ny,
-         int tiles_m, int tiles_n, int splits, int64_t per_split, int chunk_stages,
-         float base_scale, CallScalars* __restrict__ scal, float* __restrict__ part) {
+    k_tc(const TcInst* __restrict__ tab, int ninst, int n_items, CallScalars* __restrict__ scal) {
   using C = Cfg<BN, SPLIT, KS>;
   constexpr int HN = C::kHN;
   constexpr int kKS = KS;
@@ -133,8 +140,6 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n_items = tiles_m * tiles_n * splits;
-  const int CS = chunk_stages;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -167,7 +172,8 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
       bool ok = true;
       const uint32_t smem_base = smem_u32(smem);
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-        const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
+        const Item itm = item_of(tab, ninst, it, kKS);
+        const int CS = itm.I->chunk_stages;
         for (int st = 0; ok && st < itm.nst; ++st, ++g) {
           const uint32_t s = g % C::kStages;
           if (!(ok = mbar_wait(&full[s], (g / C::kStages) & 1, abort_flag, scal, kRoleMma))) break;
@@ -244,14 +250,17 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     __syncwarp();
   } else if (warp == 1) {
     // --------------------------------------------------------- point loader
-    const float wmax = __uint_as_float(scal->wmax_bits);
-    const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
     uint32_t g = 0;
     bool ok = true, negative = false;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
-      const float2 cx = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
-      const float2 cy = gyt[min(itm.tn * BN + BN / 2, ny - 1)];
+      const Item itm = item_of(tab, ninst, it, kKS);
+      const TcInst& I = *itm.I;
+      const float wmax = __uint_as_float(I.scal->wmax_bits);
+      const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
+      const float2 cx = I.gxt[min(itm.tm * kBM + kBM / 2, I.nx - 1)];
+      const float2 cy = I.gyt[min(itm.tn * BN + BN / 2, I.ny - 1)];
+      const float4* __restrict__ pts = I.pts;
+      const float* __restrict__ wts = I.wts;
       for (int st = 0; ok && st < itm.nst; st += kGroup) {
         const int ng = min(kGroup, itm.nst - st);
         constexpr int kPer = kKS / 32;  // points per lane per stage
@@ -294,16 +303,17 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     // ------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const float wmax = __uint_as_float(scal->wmax_bits);
-    const float scale = base_scale * (wmax > 0.f ? wmax : 1.0f);
-    const int64_t cells = (int64_t)nx * ny;
     uint32_t dc0 = 0, dc1 = 0;
     bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
+      const Item itm = item_of(tab, ninst, it, kKS);
+      const TcInst& I = *itm.I;
+      const int nx = I.nx, ny = I.ny, CS = I.chunk_stages;
+      const float wmax = __uint_as_float(I.scal->wmax_bits);
+      const float scale = I.base_scale * (wmax > 0.f ? wmax : 1.0f);
       const int i = itm.tm * kBM + q * 32 + lane;
       const int j0 = itm.tn * BN;
-      float* slot = part + (int64_t)itm.s * cells;
+      float* slot = I.part + (int64_t)itm.s * nx * ny;
       if (itm.nst == 0) {
         if (i < nx)
           for (int c = 0; c < BN && j0 + c < ny; ++c) slot[(int64_t)(j0 + c) * nx + i] = 0.f;
@@ -366,15 +376,16 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     uint32_t g = 0;
     bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item itm = item_of(it, tiles_m, tiles_n, per_split, n_pad, kKS);
+      const Item itm = item_of(tab, ninst, it, kKS);
+      const TcInst& I = *itm.I;
       float gv;
       if (isA) {
-        const float2 c = gxt[min(itm.tm * kBM + kBM / 2, nx - 1)];
-        const float2 v = gxt[min(itm.tm * kBM + r, nx - 1)];
+        const float2 c = I.gxt[min(itm.tm * kBM + kBM / 2, I.nx - 1)];
+        const float2 v = I.gxt[min(itm.tm * kBM + r, I.nx - 1)];
         gv = (v.x - c.x) + (v.y - c.y);
       } else {
-        const float2 c = gyt[min(itm.tn * BN + BN / 2, ny - 1)];
-        const float2 v = gyt[min(itm.tn * BN + r, ny - 1)];
+        const float2 c = I.gyt[min(itm.tn * BN + BN / 2, I.ny - 1)];
+        const float2 v = I.gyt[min(itm.tn * BN + r, I.ny - 1)];
         gv = (v.x - c.x) + (v.y - c.y);
       }
       for (int st = 0; st < itm.nst; ++st, ++g) {
@@ -445,52 +456,43 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
 }
 
 template <int BN, bool SPLIT, int KS>
-cudaError_t launch_cfg(const TcPlan& p, const float4* pts, const float* wts, int64_t n_pad,
-                       const float2* gxt, const float2* gyt, int nx, int ny, float base_scale,
-                       float* part, CallScalars* scal, cudaStream_t s) {
+cudaError_t launch_cfg(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
+                       CallScalars* err, cudaStream_t s) {
   using C = Cfg<BN, SPLIT, KS>;
-  // two accumulator halves drained half a chunk apart: at least two stages
-  if (p.k_chunk < 2 * KS || p.k_chunk % KS) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_tc<BN, SPLIT, KS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  const int tiles_m = (nx + kBM - 1) / kBM;
-  const int tiles_n = (ny + BN - 1) / BN;
-  int64_t per = (n_pad + p.splits - 1) / p.splits;
-  per = (per + KS - 1) / KS * KS;
-  const int items = tiles_m * tiles_n * p.splits;
-  const int grid = std::min(items, p.ctas);
-  k_tc<BN, SPLIT, KS><<<grid, C::kThreads, C::kSmemBytes, s>>>(
-      pts, wts, n_pad, gxt, gyt, nx, ny, tiles_m, tiles_n, p.splits, per, p.k_chunk / KS,
-      base_scale, scal, part);
+  const int grid = std::min(n_items, p.ctas);
+  k_tc<BN, SPLIT, KS><<<grid, C::kThreads, C::kSmemBytes, s>>>(tab, ninst, n_items, err);
   note_launches(1);
   return cudaGetLastError();
 }
 
 template <int BN, bool SPLIT>
-cudaError_t launch_ks(const TcPlan& p, const float4* pts, const float* wts, int64_t n_pad,
-                      const float2* gxt, const float2* gyt, int nx, int ny, float base_scale,
-                      float* part, CallScalars* scal, cudaStream_t s) {
-  if (p.stage_points == 32)
-    return launch_cfg<BN, SPLIT, 32>(p, pts, wts, n_pad, gxt, gyt, nx, ny, base_scale, part, scal, s);
-  if (p.stage_points == 64)
-    return launch_cfg<BN, SPLIT, 64>(p, pts, wts, n_pad, gxt, gyt, nx, ny, base_scale, part, scal, s);
+cudaError_t launch_ks(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
+                      CallScalars* err, cudaStream_t s) {
+  if (p.stage_points == 32) return launch_cfg<BN, SPLIT, 32>(p, tab, ninst, n_items, err, s);
+  if (p.stage_points == 64) return launch_cfg<BN, SPLIT, 64>(p, tab, ninst, n_items, err, s);
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_tc(const TcPlan& plan, const float4* pts, const float* wts, int64_t n_pad,
-                      const float2* gxt, const float2* gyt, int nx, int ny, float scale,
-                      const CallScalars* /*scal_in*/, float* part, CallScalars* scal,
-                      cudaStream_t s) {
-  if (plan.splits < 1 || plan.ctas < 1) return cudaErrorInvalidValue;
+size_t tc_smem_bytes(const TcPlan& p) {
+  if (p.tile_n == 256)
+    return p.split16 ? Cfg<256, true, 64>::kSmemBytes : Cfg<256, false, 64>::kSmemBytes;
+  return p.split16 ? Cfg<128, true, 64>::kSmemBytes : Cfg<128, false, 64>::kSmemBytes;
+}
+
+cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
+                      CallScalars* err, cudaStream_t s) {
+  if (ninst < 1 || n_items < 1 || plan.ctas < 1) return cudaErrorInvalidValue;
   if (plan.tile_n == 256)
-    return plan.split16 ? launch_ks<256, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
-                        : launch_ks<256, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+    return plan.split16 ? launch_ks<256, true>(plan, tab, ninst, n_items, err, s)
+                        : launch_ks<256, false>(plan, tab, ninst, n_items, err, s);
   if (plan.tile_n == 128)
-    return plan.split16 ? launch_ks<128, true>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s)
-                        : launch_ks<128, false>(plan, pts, wts, n_pad, gxt, gyt, nx, ny, scale, part, scal, s);
+    return plan.split16 ? launch_ks<128, true>(plan, tab, ninst, n_items, err, s)
+                        : launch_ks<128, false>(plan, tab, ninst, n_items, err, s);
   return cudaErrorInvalidValue;
 }
 
