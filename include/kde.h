@@ -189,6 +189,27 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss,
                   float* grad_points_direct, double* grad_h_direct,
                   const kde_opts* opts);
 
+/*
+ * kde_grid_noalloc — the FP32 SIMT density (path KDE_PATH_SIMT_FP32, one
+ * point split) without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * (a stream capture that forbids allocation, a real-time loop that must not
+ * block on the allocator, a plugin whose host owns all device memory, a fixed
+ * memory budget).  Its scratch is one static device array of 8 MiB per GPU,
+ * reserved while the library is loaded; inputs needing more scratch (about
+ * 400,000 points on a small grid; 20 bytes per point plus 8 per grid row and
+ * column) are rejected with KDE_EINVAL.  points, weights (or NULL) and out
+ * are device memory, laid out as for kde_grid.  Asynchronous on `stream`
+ * (a cudaStream_t, NULL = legacy default stream); non-finite inputs are not
+ * reported.  Every call on a device shares the scratch and it keeps the last
+ * call's contents: calls that overlap on the GPU race.  The first call on a
+ * device looks up the scratch's device address; make it before any stream
+ * capture.  Errors: KDE_EINVAL, KDE_ECUDA.
+ */
+int kde_grid_noalloc(const double* points, const float* weights, int64_t n,
+                     const double grid_origin[2], double cell, int nx, int ny, double h,
+                     int kernel_id, float* out, void* stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* kde_last_error(void);
 

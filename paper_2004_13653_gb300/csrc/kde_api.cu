@@ -572,6 +572,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
 }
 
 }  // namespace
+
+void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
 }  // namespace kde
 
 using namespace kde;

@@ -113,6 +113,9 @@ cudaError_t launch_upload(const void* bytes, size_t nbytes, void* dst, cudaStrea
 
 void note_launches(int k);
 
+// Set the calling thread's kde_last_error() message.
+void set_error_message(const char* msg);
+
 cudaError_t launch_mercator(const double* lonlat, int64_t n, double lat0_deg, double* xy,
                             cudaStream_t s);
 
