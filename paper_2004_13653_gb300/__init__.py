@@ -252,6 +252,42 @@ def grid_batched(instances, path="auto", flags=0, stream=None, **tiling):
     return outs
 
 
+def grid_backward(points, weights, origin, cell, nx, ny, h, grad_out, stream=None,
+                  want_h=True):
+    """kde_grid_backward (Gaussian): (dL/dpoints [n,2] f32, dL/dw [n] f32, dL/dh)."""
+    import torch
+    n = _count(points) // 2
+    gxy = torch.empty((n, 2), dtype=torch.float32, device=points.device)
+    gw = torch.empty(n, dtype=torch.float32, device=points.device)
+    gh = ctypes.c_double(0.0)
+    if stream is None:
+        stream = _current_stream(points.device)
+    a = make_args(points, weights, origin, cell, nx, ny, h, "gaussian", grad_out)
+    o = make_opts("auto", 0, stream)
+    check(load().kde_grid_backward(ctypes.byref(a), _ptr(grad_out.contiguous()), _ptr(gxy),
+                                   _ptr(gw), ctypes.byref(gh) if want_h else None,
+                                   ctypes.byref(o)))
+    return gxy, gw, (gh.value if want_h else None)
+
+
+def lscv_grid(F, points, weights, origin, cell, nx, ny, h, stream=None):
+    """kde_lscv_grid (Gaussian): (loss, dL/dF, direct dL/dw, direct dL/dpoints, direct dL/dh)."""
+    import torch
+    n = _count(points) // 2
+    G = torch.empty_like(F)
+    gw = torch.empty(n, dtype=torch.float32, device=points.device)
+    gxy = torch.empty((n, 2), dtype=torch.float32, device=points.device)
+    loss = ctypes.c_double(0.0)
+    gh = ctypes.c_double(0.0)
+    if stream is None:
+        stream = _current_stream(points.device)
+    a = make_args(points, weights, origin, cell, nx, ny, h, "gaussian", F)
+    o = make_opts("auto", 0, stream)
+    check(load().kde_lscv_grid(ctypes.byref(a), _ptr(F), ctypes.byref(loss), _ptr(G), _ptr(gw),
+                               _ptr(gxy), ctypes.byref(gh), ctypes.byref(o)))
+    return loss.value, G, gw, gxy, gh.value
+
+
 def project_mercator(lonlat, lat0_deg, out=None, stream=None):
     """Eq. 1-4 on the device: [n,2] (lon, lat) degrees float64 -> metres."""
     import torch

@@ -1,0 +1,252 @@
+// Adjoint of the Gaussian density and the grid LSCV loss.
+//
+// Density (Sec. III-C, Eq. 7 read as a direct sum, Gaussian row of Table 1):
+//   F_ij = c sum_p w_p A_ip B_jp,  A_ip = exp(-s_ip^2/2), B_jp = exp(-t_jp^2/2),
+//   s_ip = (gx_i - x_p)/h, t_jp = (gy_j - y_p)/h, c = 1/(2 pi N h^2).
+// For a cotangent G = dL/dF:
+//   dL/dw_p = c sum_ij G_ij A_ip B_jp
+//   dL/dx_p = c w_p / h sum_ij G_ij s_ip A_ip B_jp     (dA/dx_p = A s / h)
+//   dL/dy_p = c w_p / h sum_ij G_ij t_jp A_ip B_jp
+//   dL/dh   = -(2/h) sum_ij G_ij F_ij + c/h sum_p w_p sum_ij G_ij (s^2 + t^2) A B
+// and sum_ij G_ij F_ij = sum_p w_p dL/dw_p, so F itself is not needed.
+//
+// One warp per point: lanes take the columns of the point's window, the rows
+// are walked in order, and the four sums are reduced across the warp in a
+// fixed order (reproducible).  The window spans +-8 bandwidths (clamped to the
+// grid): beyond it every term is below exp(-32) of the largest, far under the
+// accuracy of the FP32 sums.
+#include "kde_internal.cuh"
+#include "kernel_factors.cuh"
+
+namespace kde {
+namespace {
+
+constexpr float kLog2e = 1.44269504088896340736f;
+constexpr int kColsPerLane = 8;  // window columns a lane keeps in registers per block
+
+__device__ __forceinline__ float gauss(float s) { return ex2_approx(-0.5f * kLog2e * s * s); }
+
+__global__ void __launch_bounds__(256)
+    k_adjoint_gauss(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n,
+                    const float* __restrict__ G, const float2* __restrict__ gxt,
+                    const float2* __restrict__ gyt, int nx, int ny, double cell_s, int R,
+                    float c, float inv_h, float* __restrict__ grad_xy,
+                    float* __restrict__ grad_w, double* __restrict__ hterm,
+                    double* __restrict__ lterm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
+    const float4 P = pts[p];
+    const float w = wts[p];
+    // window of cells within R of the point's cell (X, Y in bandwidths)
+    const double X = (double)P.x + (double)P.y, Y = (double)P.z + (double)P.w;
+    const int ic = (int)floor(X / cell_s), jc = (int)floor(Y / cell_s);
+    const int i0 = max(ic - R, 0), i1 = min(ic + R, nx - 1);
+    const int j0 = max(jc - R, 0), j1 = min(jc + R, ny - 1);
+    float aw = 0.f, ax = 0.f, ay = 0.f, ah = 0.f;
+    if (i0 <= i1 && j0 <= j1) {
+      for (int ib = i0; ib <= i1; ib += 32 * kColsPerLane) {
+        float A[kColsPerLane], S[kColsPerLane];
+        int col[kColsPerLane];
+#pragma unroll
+        for (int k = 0; k < kColsPerLane; ++k) {
+          const int i = ib + lane + 32 * k;
+          col[k] = i <= i1 ? i : -1;
+          const float2 g = gxt[min(i, nx - 1)];
+          S[k] = (g.x - P.x) + (g.y - P.y);
+          A[k] = col[k] >= 0 ? gauss(S[k]) : 0.f;
+        }
+        for (int j = j0; j <= j1; ++j) {
+          const float2 g = gyt[j];
+          const float t = (g.x - P.z) + (g.y - P.w);
+          const float B = gauss(t);
+          const float* Grow = G + (int64_t)j * nx;
+#pragma unroll
+          for (int k = 0; k < kColsPerLane; ++k) {
+            if (col[k] < 0) continue;
+            const float q = Grow[col[k]] * B * A[k];
+            aw += q;
+            ax = fmaf(S[k], q, ax);
+            ay = fmaf(t, q, ay);
+            ah = fmaf(fmaf(S[k], S[k], t * t), q, ah);
+          }
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      aw += __shfl_xor_sync(0xffffffffu, aw, o);
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      ah += __shfl_xor_sync(0xffffffffu, ah, o);
+    }
+    if (lane == 0) {
+      const float gw = c * aw;
+      if (grad_w) grad_w[p] = gw;
+      grad_xy[2 * p] = c * w * inv_h * ax;
+      grad_xy[2 * p + 1] = c * w * inv_h * ay;
+      hterm[p] = (double)c * w * inv_h * ah;
+      lterm[p] = (double)w * gw;
+    }
+  }
+}
+
+// Fixed-order block sums of a double array: partial[b] = sum of block b's slice.
+__global__ void k_sum_blocks(const double* __restrict__ v, int64_t n, int64_t per_block,
+                             double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const int64_t b0 = (int64_t)blockIdx.x * per_block;
+  const int64_t b1 = min(b0 + per_block, n);
+  double acc = 0.0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += v[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// ----------------------------------------------------------------- LSCV
+
+// Gd = 2 cell^2 F; per-block partial sums of F^2 (FP64).
+__global__ void k_lscv_grid(const float* __restrict__ F, int64_t cells, double two_cell2,
+                            double* __restrict__ G, double* __restrict__ sq_part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cells;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float f = F[q];
+    if (G) G[q] = two_cell2 * f;
+    acc += (double)f * f;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sq_part[blockIdx.x] = sh[0];
+}
+
+// Per point: bilinear sample of F between cell centres (zero outside), the
+// leave-one-out term, the loss's direct partials, and the scatter of
+// -(2/N) w_p beta into the FP64 cotangent (atomic adds; in FP64 their order
+// does not show in the FP32 result).
+__global__ void k_lscv_points(const float4* __restrict__ pts, const float* __restrict__ wts,
+                              int64_t n, const float* __restrict__ F, int nx, int ny,
+                              double cells_per_h, float inv_cell, double inv_N, double self_term,
+                              double* __restrict__ G, float* __restrict__ gw_direct,
+                              float* __restrict__ gxy_direct, double* __restrict__ loo) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const float4 P = pts[p];
+    const double w = wts[p];
+    const double fx = ((double)P.x + (double)P.y) * cells_per_h - 0.5;
+    const double fy = ((double)P.z + (double)P.w) * cells_per_h - 0.5;
+    const double fi = floor(fx), fj = floor(fy);
+    const double ax = fx - fi, ay = fy - fj;
+    double v = 0.0, dvx = 0.0, dvy = 0.0;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const double ii = fi + a, jj = fj + b;
+        if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+        const int64_t q = (int64_t)jj * nx + (int64_t)ii;
+        const double wx = a ? ax : 1.0 - ax, wy = b ? ay : 1.0 - ay;
+        const double f = F[q];
+        v += wx * wy * f;
+        dvx += (a ? 1.0 : -1.0) * wy * f;
+        dvy += (b ? 1.0 : -1.0) * wx * f;
+        if (G) atomicAdd(&G[q], -2.0 * inv_N * w * wx * wy);
+      }
+    if (gw_direct) gw_direct[p] = (float)(-2.0 * inv_N * (v - 2.0 * w * self_term));
+    if (gxy_direct) {
+      gxy_direct[2 * p] = (float)(-2.0 * inv_N * w * dvx * inv_cell);
+      gxy_direct[2 * p + 1] = (float)(-2.0 * inv_N * w * dvy * inv_cell);
+    }
+    loo[p] = w * (v - w * self_term);
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ src, int64_t n, float* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride)
+    dst[q] = (float)src[q];
+}
+
+__global__ void k_square(const float* __restrict__ w, int64_t n, double* __restrict__ w2) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    w2[p] = (double)w[p] * w[p];
+}
+
+int grid_blocks(int64_t n, int threads, int cap) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_square_weights(const float* w, int64_t n, double* w2, cudaStream_t s) {
+  k_square<<<grid_blocks(n, 256, 152 * 16), 256, 0, s>>>(w, n, w2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+size_t sum_partials(int64_t n) { return (size_t)((n + 65535) / 65536) + 1; }
+
+cudaError_t launch_sum(const double* v, int64_t n, double* partial, double* result,
+                       cudaStream_t s) {
+  const int64_t per = 65536;
+  const int nb = (int)std::max<int64_t>(1, (n + per - 1) / per);
+  k_sum_blocks<<<nb, 256, 0, s>>>(v, n, per, partial);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_blocks<<<1, 256, 0, s>>>(partial, nb, nb, result);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n, const float* G,
+                                 const float2* gxt, const float2* gyt, int nx, int ny,
+                                 double cell, double h, float* grad_xy, float* grad_w,
+                                 double* hterm, double* lterm, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int R = (int)ceil(8.0 * h / cell) + 1;
+  const float c = (float)(1.0 / (2.0 * 3.14159265358979323846 * (double)n * h * h));
+  k_adjoint_gauss<<<grid_blocks(n * 32, 256, 152 * 64), 256, 0, s>>>(
+      pts, wts, n, G, gxt, gyt, nx, ny, cell / h, R, c, (float)(1.0 / h), grad_xy, grad_w, hterm,
+      lterm);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const float* F, int nx,
+                        int ny, double cell, double h, double* Gd, float* G, float* gw_direct,
+                        float* gxy_direct, double* sq_part, int sq_blocks, double* loo,
+                        cudaStream_t s) {
+  const int64_t cells = (int64_t)nx * ny;
+  k_lscv_grid<<<sq_blocks, 256, 0, s>>>(F, cells, 2.0 * cell * cell, Gd, sq_part);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const double self = 1.0 / (2.0 * 3.14159265358979323846) / ((double)n * h * h);
+    k_lscv_points<<<grid_blocks(n, 256, 152 * 16), 256, 0, s>>>(
+        pts, wts, n, F, nx, ny, h / cell, (float)(1.0 / cell), 1.0 / (double)n, self, Gd,
+        gw_direct, gxy_direct, loo);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (G) {
+    k_to_float<<<grid_blocks(cells, 256, 152 * 16), 256, 0, s>>>(Gd, cells, G);
+    note_launches(1);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace kde

@@ -652,27 +652,187 @@ int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts) {
 
 int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_points,
                       float* grad_weights, double* grad_h, const kde_opts* opts) {
-  (void)a;
-  (void)grad_out;
-  (void)grad_points;
-  (void)grad_weights;
-  (void)grad_h;
-  (void)opts;
-  return fail(KDE_ENOTSUP, "kde_grid_backward is not available in this build");
+  int rc = validate(a, opts);
+  if (rc) return rc;
+  if (a->kernel_id != KDE_GAUSSIAN)
+    return fail(KDE_ENOTSUP, "the adjoint is implemented for the Gaussian kernel");
+  if (!grad_out || (a->n > 0 && !grad_points))
+    return fail(KDE_EINVAL, "grad_out and grad_points are required");
+  if (a->n > 0 && (memory_kind(a->points) != 0 || (a->weights && memory_kind(a->weights) != 0) ||
+                   memory_kind(grad_points) != 0 ||
+                   (grad_weights && memory_kind(grad_weights) != 0)))
+    return fail(KDE_EINVAL, "kde_grid_backward needs device pointers");
+  if (memory_kind(grad_out) != 0) return fail(KDE_EINVAL, "grad_out must be device memory");
+  if ((reinterpret_cast<uintptr_t>(grad_points) & 7) || (reinterpret_cast<uintptr_t>(grad_out) & 3))
+    return fail(KDE_EINVAL, "misaligned gradient buffer");
+  cudaStream_t s = stream_of(opts);
+  if (a->n == 0) {
+    if (grad_h) *grad_h = 0.0;
+    g_err[0] = 0;
+    return KDE_OK;
+  }
+  const int64_t n_pad = (a->n + 511) / 512 * 512;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
+  const size_t o_scal = take(sizeof(CallScalars));
+  const size_t o_tab = take(sizeof(PrepInst));
+  const size_t o_pts = take(sizeof(float4) * n_pad);
+  const size_t o_wts = take(sizeof(float) * n_pad);
+  const size_t o_gxt = take(sizeof(float2) * a->nx);
+  const size_t o_gyt = take(sizeof(float2) * a->ny);
+  const size_t o_ht = take(sizeof(double) * a->n);
+  const size_t o_lt = take(sizeof(double) * a->n);
+  const size_t o_part = take(sizeof(double) * 2 * sum_partials(a->n));
+  const size_t o_res = take(sizeof(double) * 2);
+  void* wsv = nullptr;
+  rc = acquire_workspace(opts, off, s, &wsv);
+  if (rc) return rc;
+  char* base = static_cast<char*>(wsv);
+  PrepInst q;
+  q.xy = a->points;
+  q.w = a->weights;
+  q.pts = reinterpret_cast<float4*>(base + o_pts);
+  q.wts = reinterpret_cast<float*>(base + o_wts);
+  q.gxt = reinterpret_cast<float2*>(base + o_gxt);
+  q.gyt = reinterpret_cast<float2*>(base + o_gyt);
+  q.scal = reinterpret_cast<CallScalars*>(base + o_scal);
+  q.n = a->n;
+  q.n_pad = n_pad;
+  q.begin = 0;
+  q.ox = a->origin_x;
+  q.oy = a->origin_y;
+  q.sigma = 1.0 / a->h;  // offsets in bandwidths
+  q.cell_sigma = a->cell / a->h;
+  q.nx = a->nx;
+  q.ny = a->ny;
+  double* ht = reinterpret_cast<double*>(base + o_ht);
+  double* lt = reinterpret_cast<double*>(base + o_lt);
+  double* part = reinterpret_cast<double*>(base + o_part);
+  double* res = reinterpret_cast<double*>(base + o_res);
+  KDE_CUDA(cudaMemsetAsync(q.scal, 0, sizeof(CallScalars), s), "clear scalars");
+  KDE_CUDA(launch_upload(&q, sizeof(q), base + o_tab, s), "upload tables");
+  KDE_CUDA(launch_prepare(reinterpret_cast<PrepInst*>(base + o_tab), 1, n_pad,
+                          std::max(a->nx, a->ny), s),
+           "prepare points");
+  KDE_CUDA(launch_adjoint_gauss(q.pts, q.wts, a->n, grad_out, q.gxt, q.gyt, a->nx, a->ny, a->cell,
+                                a->h, grad_points, grad_weights, ht, lt, s),
+           "adjoint");
+  const bool sync = grad_h || (opts && (opts->flags & KDE_FLAG_SYNC));
+  if (grad_h) {
+    const size_t np = sum_partials(a->n);
+    KDE_CUDA(launch_sum(ht, a->n, part, res, s), "sum");
+    KDE_CUDA(launch_sum(lt, a->n, part + np, res + 1, s), "sum");
+  }
+  if (sync) {
+    double hres[2] = {0.0, 0.0};
+    int err = 0;
+    if (grad_h)
+      KDE_CUDA(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s), "read result");
+    KDE_CUDA(cudaMemcpyAsync(&err, &q.scal->err, sizeof(int), cudaMemcpyDeviceToHost, s),
+             "read status");
+    KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+    if (err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
+    // dL/dh = -(2/h) sum G F + sum_p h-terms, with sum G F = sum_p w_p dL/dw_p
+    if (grad_h) *grad_h = -2.0 / a->h * hres[1] + hres[0];
+  }
+  g_err[0] = 0;
+  return KDE_OK;
 }
 
 int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F,
                   float* grad_w_direct, float* grad_points_direct, double* grad_h_direct,
                   const kde_opts* opts) {
-  (void)a;
-  (void)F;
-  (void)loss;
-  (void)grad_F;
-  (void)grad_w_direct;
-  (void)grad_points_direct;
-  (void)grad_h_direct;
-  (void)opts;
-  return fail(KDE_ENOTSUP, "kde_lscv_grid is not available in this build");
+  if (!a) return fail(KDE_EINVAL, "args is NULL");
+  kde_args chk = *a;
+  if (!chk.out) chk.out = const_cast<float*>(F);  // out is not used here
+  int rc = validate(&chk, opts);
+  if (rc) return rc;
+  if (a->kernel_id != KDE_GAUSSIAN)
+    return fail(KDE_ENOTSUP, "the LSCV loss is implemented for the Gaussian kernel");
+  if (!F || !loss) return fail(KDE_EINVAL, "F and loss are required");
+  if (memory_kind(F) != 0 || (grad_F && memory_kind(grad_F) != 0) ||
+      (a->n > 0 && (memory_kind(a->points) != 0 ||
+                    (a->weights && memory_kind(a->weights) != 0) ||
+                    (grad_w_direct && memory_kind(grad_w_direct) != 0) ||
+                    (grad_points_direct && memory_kind(grad_points_direct) != 0))))
+    return fail(KDE_EINVAL, "kde_lscv_grid needs device pointers");
+  cudaStream_t s = stream_of(opts);
+  const int64_t n = a->n;
+  const int64_t n_pad = std::max<int64_t>(512, (n + 511) / 512 * 512);
+  const int sq_blocks = 152 * 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
+  const size_t o_scal = take(sizeof(CallScalars));
+  const size_t o_tab = take(sizeof(PrepInst));
+  const size_t o_pts = take(sizeof(float4) * n_pad);
+  const size_t o_wts = take(sizeof(float) * n_pad);
+  const size_t o_gxt = take(sizeof(float2) * a->nx);
+  const size_t o_gyt = take(sizeof(float2) * a->ny);
+  const size_t o_loo = take(sizeof(double) * std::max<int64_t>(n, 1));
+  const size_t o_w2 = take(sizeof(double) * std::max<int64_t>(n, 1));
+  const size_t o_sq = take(sizeof(double) * sq_blocks);
+  const size_t o_gd = take(grad_F ? sizeof(double) * (size_t)a->nx * a->ny : 0);
+  const size_t o_part = take(sizeof(double) * 3 * (sum_partials(std::max<int64_t>(n, sq_blocks)) + 1));
+  const size_t o_res = take(sizeof(double) * 4);
+  void* wsv = nullptr;
+  rc = acquire_workspace(opts, off, s, &wsv);
+  if (rc) return rc;
+  char* base = static_cast<char*>(wsv);
+  PrepInst q;
+  q.xy = a->points;
+  q.w = a->weights;
+  q.pts = reinterpret_cast<float4*>(base + o_pts);
+  q.wts = reinterpret_cast<float*>(base + o_wts);
+  q.gxt = reinterpret_cast<float2*>(base + o_gxt);
+  q.gyt = reinterpret_cast<float2*>(base + o_gyt);
+  q.scal = reinterpret_cast<CallScalars*>(base + o_scal);
+  q.n = n;
+  q.n_pad = n_pad;
+  q.begin = 0;
+  q.ox = a->origin_x;
+  q.oy = a->origin_y;
+  q.sigma = 1.0 / a->h;
+  q.cell_sigma = a->cell / a->h;
+  q.nx = a->nx;
+  q.ny = a->ny;
+  double* loo = reinterpret_cast<double*>(base + o_loo);
+  double* w2 = reinterpret_cast<double*>(base + o_w2);
+  double* sq = reinterpret_cast<double*>(base + o_sq);
+  double* part = reinterpret_cast<double*>(base + o_part);
+  double* res = reinterpret_cast<double*>(base + o_res);
+  const size_t np = sum_partials(std::max<int64_t>(n, sq_blocks)) + 1;
+  KDE_CUDA(cudaMemsetAsync(q.scal, 0, sizeof(CallScalars), s), "clear scalars");
+  KDE_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * 4, s), "clear results");
+  KDE_CUDA(launch_upload(&q, sizeof(q), base + o_tab, s), "upload tables");
+  KDE_CUDA(launch_prepare(reinterpret_cast<PrepInst*>(base + o_tab), 1, n_pad,
+                          std::max(a->nx, a->ny), s),
+           "prepare points");
+  KDE_CUDA(launch_lscv(q.pts, q.wts, n, F, a->nx, a->ny, a->cell, a->h,
+                       grad_F ? reinterpret_cast<double*>(base + o_gd) : nullptr, grad_F,
+                       grad_w_direct, grad_points_direct, sq, sq_blocks, loo, s),
+           "LSCV");
+  KDE_CUDA(launch_sum(sq, sq_blocks, part, res, s), "sum");
+  if (n > 0) {
+    KDE_CUDA(launch_square_weights(q.wts, n, w2, s), "squares");
+    KDE_CUDA(launch_sum(loo, n, part + np, res + 1, s), "sum");
+    KDE_CUDA(launch_sum(w2, n, part + 2 * np, res + 2, s), "sum");
+  }
+  double hres[4];
+  int err = 0;
+  KDE_CUDA(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s), "read result");
+  KDE_CUDA(cudaMemcpyAsync(&err, &q.scal->err, sizeof(int), cudaMemcpyDeviceToHost, s),
+           "read status");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  if (err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
+  const double N = (double)std::max<int64_t>(n, 1);
+  // L = cell^2 sum F^2 - (2/N) sum_p w_p [bilerp - w_p K0/(N h^2)]
+  *loss = a->cell * a->cell * hres[0] - 2.0 / N * hres[1];
+  if (grad_h_direct) {
+    const double k0 = 1.0 / (2.0 * 3.14159265358979323846);
+    *grad_h_direct += -4.0 * k0 * hres[2] / (N * N * a->h * a->h * a->h);
+  }
+  g_err[0] = 0;
+  return KDE_OK;
 }
 
 const char* kde_last_error(void) { return g_err; }

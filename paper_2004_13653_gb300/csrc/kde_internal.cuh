@@ -162,6 +162,24 @@ cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t tota
                           const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                           CutoffScratch ws, cudaStream_t s);
 
+// Adjoint of the Gaussian density (points prepared with sigma = 1/h) and the
+// grid LSCV loss.  hterm / lterm: per-point FP64 terms of dL/dh.
+cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n, const float* G,
+                                 const float2* gxt, const float2* gyt, int nx, int ny,
+                                 double cell, double h, float* grad_xy, float* grad_w,
+                                 double* hterm, double* lterm, cudaStream_t s);
+// Gd: FP64 scratch for the cotangent (cells), G: FP32 cotangent out.
+cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const float* F, int nx,
+                        int ny, double cell, double h, double* Gd, float* G, float* gw_direct,
+                        float* gxy_direct, double* sq_part, int sq_blocks, double* loo,
+                        cudaStream_t s);
+cudaError_t launch_square_weights(const float* w, int64_t n, double* w2, cudaStream_t s);
+// Fixed-order sum of n doubles into *result (device); partial needs
+// sum_partials(n) doubles.
+size_t sum_partials(int64_t n);
+cudaError_t launch_sum(const double* v, int64_t n, double* partial, double* result,
+                       cudaStream_t s);
+
 // Path (b): Gaussian as a tcgen05 contraction.
 struct TcPlan {
   int tile_n;        // 128 or 256 grid rows (y) per tile; tile_m is 128 (x)

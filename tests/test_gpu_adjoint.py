@@ -1,0 +1,131 @@
+"""Adjoint of the Gaussian density, the grid LSCV loss and the bandwidth fit,
+through the C ABI, against the FP64 oracle's analytic gradients (relative
+L-inf within 1e-4, normalised by the largest oracle component)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from kde_testutil import TOL_GRAD, rel_linf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2004_13653_gb300 as kde  # noqa: E402
+from paper_2004_13653_gb300 import autograd as kag  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kde.load(build_if_stale=True)
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def _case(seed=900, n=300, nx=60, ny=50):
+    wl = workloads.random_points(seed, n, 600.0, 10.0, nx, ny, 25.0, oracle.GAUSSIAN)
+    G = np.random.default_rng(seed).normal(0, 1, (ny, nx))
+    return wl, G
+
+
+def test_adjoint_matches_oracle_vjp():
+    wl, G = _case()
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                                    _dev(G, torch.float32))
+    rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, G)
+    assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
+    assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    assert gh == pytest.approx(rh, rel=TOL_GRAD)
+
+
+def test_adjoint_wide_bandwidth_whole_grid_window():
+    """h = 40 cells: the +-8h window covers the whole grid."""
+    wl = workloads.random_points(901, 200, 300.0, 5.0, 60, 60, 200.0, oracle.GAUSSIAN)
+    G = np.random.default_rng(901).normal(0, 1, (60, 60))
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, 60, 60, wl.h, _dev(G, torch.float32))
+    rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, 60, 60, wl.h, G)
+    assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
+    assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    assert gh == pytest.approx(rh, rel=TOL_GRAD)
+
+
+def test_lscv_loss_cotangent_and_direct_terms_match_oracle():
+    wl, _ = _case(902, 400)
+    F = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
+    loss, G, gw, gxy, gh = kde.lscv_grid(_dev(F, torch.float32), _dev(wl.xy, torch.float64),
+                                         _dev(wl.w, torch.float32), wl.origin, wl.cell, wl.nx,
+                                         wl.ny, wl.h)
+    ref_loss = oracle.lscv_loss(F, wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h)
+    ref_G = oracle.lscv_cotangent(F, wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    assert rel_linf(G.cpu().numpy(), ref_G) <= 1e-5
+
+
+def test_lscv_gradient_through_autograd_matches_oracle():
+    """dL/d(log h) and dL/domega (w = N softmax(omega)) from the GPU chain
+    (split-FP16 forward, adjoint, LSCV) against the oracle's FP64 analytic
+    gradient, itself pinned to central differences."""
+    wl, _ = _case(903, 500, 64, 64)
+    n = wl.n
+    omega0 = np.log(wl.w.astype(np.float64) / wl.w.sum())
+    log_h = torch.tensor(math.log(wl.h), dtype=torch.float64, device="cuda", requires_grad=True)
+    omega = torch.tensor(omega0, dtype=torch.float64, device="cuda", requires_grad=True)
+    pts = _dev(wl.xy, torch.float64)
+    w = (n * torch.softmax(omega, 0)).to(torch.float32)
+    L = kag.lscv_loss(pts, w, torch.exp(log_h), wl.origin, wl.cell, wl.nx, wl.ny)
+    L.backward()
+    wv = n * np.exp(omega0) / np.exp(omega0).sum()
+    rL, rgw, rgxy, rgh = oracle.lscv_value_and_grad(wl.xy, wv, wl.origin, wl.cell, wl.nx, wl.ny,
+                                                    wl.h)
+    assert float(L) == pytest.approx(rL, rel=1e-4)
+    assert float(log_h.grad) == pytest.approx(wl.h * rgh, rel=TOL_GRAD, abs=1e-4 * abs(wl.h * rgh))
+    ref_om = wv * (rgw - np.sum(wv * rgw) / n)
+    assert rel_linf(omega.grad.cpu().numpy(), ref_om) <= TOL_GRAD
+
+
+def test_config5_adjoint_sampled_points():
+    """2M lane fixes thinned by the oracle's Douglas-Peucker at 10 m, 1024^2
+    grid, h = 150 m, cotangent = the LSCV cotangent: the adjoint on sampled
+    points against the oracle."""
+    raw = workloads.config5_raw()
+    keep = oracle.douglas_peucker(raw.local, raw.offsets, 10.0)
+    xy = raw.xy[keep]
+    w = np.ones(xy.shape[0], np.float32)
+    F = kde.grid(_dev(xy, torch.float64), _dev(w, torch.float32), raw.origin, raw.cell, raw.nx,
+                 raw.ny, raw.h, "gaussian", flags=kde.FLAG_SYNC)
+    loss, G, _, _, _ = kde.lscv_grid(F, _dev(xy, torch.float64), _dev(w, torch.float32),
+                                     raw.origin, raw.cell, raw.nx, raw.ny, raw.h)
+    gxy, gw, _ = kde.grid_backward(_dev(xy, torch.float64), _dev(w, torch.float32), raw.origin,
+                                   raw.cell, raw.nx, raw.ny, raw.h, G, want_h=False)
+    sel = np.random.default_rng(5).choice(xy.shape[0], 48, replace=False)
+    rw, rxy, _ = oracle.kde_vjp_gauss(xy, w, raw.origin, raw.cell, raw.nx, raw.ny, raw.h,
+                                      G.cpu().numpy().astype(np.float64), pts=sel)
+    assert rel_linf(gw.cpu().numpy()[sel], rw) <= TOL_GRAD
+    assert rel_linf(gxy.cpu().numpy()[sel], rxy) <= TOL_GRAD
+
+
+def test_fit_bandwidth_decreases_loss_and_resumes(tmp_path):
+    wl = workloads.config2(seed=904, n_traj=20, fixes=500)
+    wl.nx = wl.ny = 256
+    wl.cell = wl.box / 256
+    pts = _dev(wl.xy, torch.float64)
+    w0 = torch.ones(wl.n, dtype=torch.float32, device="cuda")
+    h_full, w_full, losses = kag.fit_bandwidth(pts, w0, wl.origin, wl.cell, 256, 256, 150.0,
+                                               steps=40, lr=0.05)
+    assert losses[-1] < losses[0]
+    ck = str(tmp_path / "lscv.pt")
+    kag.fit_bandwidth(pts, w0, wl.origin, wl.cell, 256, 256, 150.0, steps=20, lr=0.05,
+                      checkpoint=ck, every=10)
+    h_res, w_res, losses_res = kag.fit_bandwidth(pts, w0, wl.origin, wl.cell, 256, 256, 150.0,
+                                                 steps=40, lr=0.05, checkpoint=ck, every=10)
+    assert len(losses_res) == 40
+    assert h_res == pytest.approx(h_full, rel=1e-6)
+    assert losses_res[-1] == pytest.approx(losses[-1], rel=1e-6)
