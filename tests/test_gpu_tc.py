@@ -120,3 +120,22 @@ def test_config3_full_size_sampled():
     ref = oracle.kde_cells(oracle.mercator(ll, lat0), wl.w, origin, wl.cell, wl.nx, wl.ny, wl.h,
                            oracle.GAUSSIAN, cells)
     assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_SPLIT
+
+
+def test_autotuned_tiling_is_valid_and_accurate(tmp_path):
+    from paper_2004_13653_gb300 import autotune
+    wl = workloads.config2(n_traj=400)
+    pts = torch.as_tensor(wl.xy, dtype=torch.float64, device="cuda")
+    w = torch.as_tensor(wl.w, dtype=torch.float32, device="cuda")
+    cache = str(tmp_path / "tune.json")
+    opts = autotune.tune(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "tc_split16",
+                         cache_path=cache)
+    assert opts in autotune.CANDIDATES["tc_split16"]
+    assert autotune.tune(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "tc_split16",
+                         cache_path=cache) == opts  # served from the cache
+    F = kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "gaussian", path="tc_split16",
+                 flags=kde.FLAG_SYNC, **opts).cpu().numpy()
+    cells = sample_cells(F, 128, seed=13)
+    ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN,
+                           cells)
+    assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_SPLIT
