@@ -70,6 +70,10 @@ typedef enum {
 #define KDE_FLAG_SYNC 1u         /* wait for completion and check device flags */
 #define KDE_FLAG_SKIP_ZERO 2u    /* TC paths: skip (tile, chunk) pairs whose    */
                                  /* operands are exactly zero in FP16           */
+#define KDE_FLAG_CTA_PAIR 4u     /* TC paths: 256x256 tiles on pairs of CTAs    */
+                                 /* (tcgen05 cta_group::2); the default for     */
+                                 /* split-FP16 with 256-wide tiles              */
+#define KDE_FLAG_ONE_CTA 8u      /* TC paths: 128xN tiles on single CTAs        */
 
 typedef struct kde_args {
   const double* points; /* [2n] interleaved x,y metres (device or host)      */

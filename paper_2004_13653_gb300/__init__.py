@@ -16,7 +16,7 @@ from . import build as _build
 KERNELS = {"uniform": 0, "triangular": 1, "epanechnikov": 2, "quartic": 3, "triweight": 4,
            "tricube": 5, "gaussian": 6, "cosine": 7}
 PATHS = {"auto": 0, "simt": 1, "tc_fp16": 2, "tc_split16": 3, "cutoff": 4}
-FLAG_SYNC, FLAG_SKIP_ZERO = 1, 2
+FLAG_SYNC, FLAG_SKIP_ZERO, FLAG_CTA_PAIR, FLAG_ONE_CTA = 1, 2, 4, 8
 
 KDE_OK, KDE_EINVAL, KDE_ENOMEM, KDE_ECUDA, KDE_ETIMEOUT, KDE_ENOTSUP, KDE_EDATA = 0, -1, -2, -3, -4, -5, -6
 _ERRNAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EDATA"}

@@ -244,6 +244,21 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   t.ctas = ctas;
   t.skip_zero = (o && (o->flags & KDE_FLAG_SKIP_ZERO)) ? 1 : 0;
   t.splits = 1;
+  // CTA pairs (256 x 256 tiles, cta_group::2) halve each SM's operand reads
+  // per MMA; they are the default for split-FP16 with 256-wide tiles
+  const bool want_pair = o && (o->flags & KDE_FLAG_CTA_PAIR);
+  const bool no_pair = o && (o->flags & KDE_FLAG_ONE_CTA);
+  if (want_pair && no_pair) return fail(KDE_EINVAL, "KDE_FLAG_CTA_PAIR and KDE_FLAG_ONE_CTA conflict");
+  if (want_pair) {
+    if ((o->tile_n && o->tile_n != 256) || (o->stage_points && o->stage_points != 64))
+      return fail(KDE_EINVAL, "CTA-pair tiles are 256 x 256 with 64-point stages");
+    t.tile_n = 256;
+    t.stage_points = 64;
+  }
+  const bool pair_ok = t.tile_n == 256 && t.stage_points == 64 && ctas >= 2;
+  if (want_pair && !pair_ok)
+    return fail(KDE_EINVAL, "CTA-pair tiles need tile_n 256, 64-point stages and two CTAs");
+  t.pair = want_pair || (!no_pair && pair_ok && tc_split16 == 1) ? 1 : 0;
   if (tc_split16 >= 0 && (t.k_chunk % t.stage_points || t.k_chunk < 2 * t.stage_points))
     return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
                 t.k_chunk, t.stage_points);
@@ -254,12 +269,13 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     const kde_args* a = &A[k];
     InstPlan& I = P->in[k];
     if (is_tc(I.path)) {
-      I.tiles_m = (a->nx + 127) / 128;
+      const int tile_m = t.pair ? 256 : 128;
+      I.tiles_m = (a->nx + tile_m - 1) / tile_m;
       I.tiles_n = (a->ny + t.tile_n - 1) / t.tile_n;
       tc_cost += (double)I.tiles_m * I.tiles_n * (double)I.n_pad;
     }
   }
-  const double target_item = tc_cost / (double)ctas / 6.0;
+  const double target_item = tc_cost / (double)(t.pair ? ctas / 2 : ctas) / 6.0;
   for (int k = 0; k < count; ++k) {
     const kde_args* a = &A[k];
     InstPlan& I = P->in[k];
@@ -276,7 +292,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       const int64_t tiles = (int64_t)I.tiles_m * I.tiles_n;
       if (splits == 0) {
         if (count == 1) {
-          splits = choose_tc_splits(tiles, ctas, I.n_pad);
+          splits = choose_tc_splits(tiles, t.pair ? ctas / 2 : ctas, I.n_pad);
         } else {
           const double want = std::ceil((double)I.n_pad / std::max(target_item, 1.0));
           splits = (int)std::max(1.0, std::min({want, 64.0, (double)(I.n_pad / 256)}));
@@ -521,7 +537,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   cudaEvent_t* ev = o ? static_cast<cudaEvent_t*>(o->timing_events) : nullptr;
   if (ev) KDE_CUDA(cudaEventRecord(ev[0], s), "record start event");
   if (P.n_tc)
-    KDE_CUDA(launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s), "tensor-core contraction");
+    KDE_CUDA(P.tc.pair ? launch_tc_pair(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s)
+                       : launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s),
+             "tensor-core contraction");
   for (int k = 0; k < count; ++k) {
     const InstPlan& I = P.in[k];
     if (I.path != KDE_PATH_SIMT_FP32) continue;

@@ -189,10 +189,14 @@ struct TcPlan {
   int ctas;          // persistent CTAs
   int skip_zero;     // skip (tile, stage) pairs whose operands are all zero
   int stage_points;  // 32 or 64 points per pipeline stage
+  int pair;          // 1: 256 x 256 tiles on CTA pairs (cta_group::2)
 };
 size_t tc_smem_bytes(const TcPlan& p);
 // One persistent launch over the work items of every instance in `tab`.
 cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
                       CallScalars* err, cudaStream_t s);
+// The same on CTA pairs (tiles_m / tiles_n of the table count 256-cell tiles).
+cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
+                           CallScalars* err, cudaStream_t s);
 
 }  // namespace kde

@@ -23,11 +23,11 @@ def _lib():
     kde.load(build_if_stale=True)
 
 
-def run_gpu(wl, path, weights=True, **kw):
+def run_gpu(wl, path, weights=True, flags_extra=0, **kw):
     pts = torch.as_tensor(np.ascontiguousarray(wl.xy), dtype=torch.float64, device="cuda")
     w = torch.as_tensor(wl.w, dtype=torch.float32, device="cuda") if weights else None
     out = kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "gaussian", path=path,
-                   flags=kde.FLAG_SYNC, **kw)
+                   flags=kde.FLAG_SYNC | flags_extra, **kw)
     return out.cpu().numpy()
 
 
@@ -139,3 +139,40 @@ def test_autotuned_tiling_is_valid_and_accurate(tmp_path):
     ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN,
                            cells)
     assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("path", ["tc_split16", "tc_fp16"])
+def test_cta_pair_config1_and_ragged(path):
+    """256 x 256 tiles on CTA pairs (cta_group::2): each CTA generates its own
+    128 rows of A and of B; ragged tiles on both axes."""
+    for wl in (workloads.config1(),
+               workloads.random_points(410, 3001, 5000.0, 12.5, 300, 520, 40.0, oracle.GAUSSIAN)):
+        F = run_gpu(wl, path, flags_extra=kde.FLAG_CTA_PAIR)
+        ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                              oracle.GAUSSIAN)
+        assert rel_linf(F, ref) <= TOL[path]
+
+
+@pytest.mark.parametrize("k_chunk,split_k", [(128, 1), (256, 3), (0, 0), (512, 5)])
+def test_cta_pair_dense_cluster(k_chunk, split_k):
+    wl = _dense_cluster()
+    F = run_gpu(wl, "tc_split16", flags_extra=kde.FLAG_CTA_PAIR, k_chunk=k_chunk, split_k=split_k)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
+    assert rel_linf(F, ref) <= TOL_SPLIT
+
+
+def test_cta_pair_batched_matches_single():
+    wls = [workloads.random_points(420 + k, 2000 + 500 * k, 4000.0, 10.0, 200 + 40 * k,
+                                   300 - 30 * k, 35.0, oracle.GAUSSIAN) for k in range(5)]
+    insts = [dict(points=torch.as_tensor(wl.xy, dtype=torch.float64, device="cuda"),
+                  weights=torch.as_tensor(wl.w, dtype=torch.float32, device="cuda"),
+                  origin=wl.origin, cell=wl.cell, nx=wl.nx, ny=wl.ny, h=wl.h, kernel="gaussian")
+             for wl in wls]
+    outs = kde.grid_batched(insts, flags=kde.FLAG_SYNC | kde.FLAG_CTA_PAIR, split_k=2)
+    for wl, d, F in zip(wls, insts, outs):
+        alone = kde.grid(d["points"], d["weights"], wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                         "gaussian", flags=kde.FLAG_SYNC | kde.FLAG_CTA_PAIR, split_k=2)
+        assert torch.equal(F, alone)
+        ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                              oracle.GAUSSIAN)
+        assert rel_linf(F.cpu().numpy(), ref) <= TOL_SPLIT
