@@ -30,6 +30,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at ≤1e-5 err"
+
+# DRAM bytes (read + write) per launch of the contraction kernel on the default workload, from
+# one ncu capture (profiles/k_tc_pair_dram_20M_4096sq.md); reported only while the kernel's
+# sources hash to the value they had when the counters were taken.
+TRAFFIC = {("tc_split16", 4096, 40_000): {
+    "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh",
+                "paper_2004_13653_gb300/csrc/kde_internal.cuh"],
+    "sha256": "f3b1f267bfd72bc17be7f832b9c1002af55c756ed2355d0a06c4a1702d541616",
+    "bytes": 1412567808 + 535942912}}
+
+
+def measured_traffic(path, grid, points):
+    import hashlib
+    t = TRAFFIC.get((path, grid, points))
+    if not t:
+        return None
+    h = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest() == t["sha256"] else None
 UNIT = "Gpoint·cell/s"
 
 
@@ -40,14 +61,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", default="tc_split16",
-                    choices=["tc_split16", "tc_fp16", "simt"])
+                    choices=["tc_split16", "tc_fp16", "simt", "cutoff"])
+    ap.add_argument("--kernel", default="gaussian",
+                    help="Table 1 kernel (the cutoff path needs a compact one)")
+    ap.add_argument("--flags", type=int, default=0, help="extra KDE_FLAG_* bits")
+    ap.add_argument("--extra", action="store_true",
+                    help="also measure the batched, cutoff and LSCV workloads (slower)")
     ap.add_argument("--grid", type=int, default=4096, help="grid side (default: the 4096^2 workload)")
     ap.add_argument("--points", type=int, default=40_000, help="trajectories of 500 fixes")
     ap.add_argument("--simt-grid", type=int, default=512,
                     help="grid side for the FP32 SIMT comparison (same points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-cells", type=int, default=320)
+    ap.add_argument("--cpu-cells", type=int, default=1200)
     ap.add_argument("--split-k", type=int, default=0)
     ap.add_argument("--k-chunk", type=int, default=0)
     ap.add_argument("--tile-n", type=int, default=0)
@@ -171,8 +197,8 @@ def run_ours(args):
 
     def step(events=None, path=args.path, out=out_dev, gx=nx, gy=ny):
         kde.project_mercator(lonlat_dev, lat0, out=xy_dev, stream=stream)
-        kde.grid(xy_dev, w_dev, origin, wl.cell, gx, gy, wl.h, "gaussian", out=out, path=path,
-                 stream=stream, timing_events=events, **tiling)
+        kde.grid(xy_dev, w_dev, origin, wl.cell, gx, gy, wl.h, args.kernel, out=out, path=path,
+                 flags=args.flags, stream=stream, timing_events=events, **tiling)
 
     def new_pair():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -209,7 +235,7 @@ def run_ours(args):
     value = world * evals / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel
-    if args.path == "simt":
+    if args.path in ("simt", "cutoff"):
         # per point and thread: 16 factor evaluations (4 FP32 ops + 1 MUFU each),
         # 8 weight products, 64 FMAs for 64 cells -> 2.125 FP32 ops per pair
         clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -225,7 +251,9 @@ def run_ours(args):
         peak = peaks["bf16_tflops_sustained"]
         achieved = flops / (kernel_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": measured_traffic(args.path, args.grid, args.points) if not args.flags
+                else None,
                 "peak_source": f"{peak_kind} bf16 sustained (FP16 dense rate taken equal)"}
 
     result = {
@@ -233,10 +261,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"tc_split16": "f16x2(hi/lo)->f32", "tc_fp16": "f16->f32",
-                  "simt": "f32"}[args.path] + ", f64 projection/centring",
+                  "simt": "f32", "cutoff": "f32"}[args.path] + ", f64 projection/centring",
         "data": "synthetic",
         "config": {"workload": f"{n} AIS-like pts, {nx}x{ny} grid, cell {wl.cell} m, "
-                               f"h={wl.h} m, gaussian",
+                               f"h={wl.h} m, {args.kernel}",
                    "path": args.path, "points": n, "grid": [nx, ny], "h_m": wl.h,
                    "l2": "inputs (320 MB lon/lat + 80 MB weights) larger than L2",
                    "parallelism": f"replicas x{world}"},
@@ -246,7 +274,7 @@ def run_ours(args):
         "clocks": clk,
     }
 
-    if rank == 0 and args.path != "simt" and args.simt_grid > 0:
+    if rank == 0 and args.path not in ("simt", "cutoff") and args.simt_grid > 0:
         sg = args.simt_grid
         out_s = torch.empty((sg, sg), dtype=torch.float32, device=dev)
         step(path="simt", out=out_s, gx=sg, gy=sg)
@@ -293,8 +321,85 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, wl, origin, ll, lat0, out_dev)
 
+    if rank == 0 and args.extra:
+        del lonlat_dev, xy_dev, out_dev
+        torch.cuda.empty_cache()
+        result["extra"] = extra_workloads(dev)
+
     if rank == 0:
         print(json.dumps(result))
+
+
+def _time(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_workloads(dev):
+    """The other rows of the hot path on their own workloads: the binned
+    cutoff path (1M lane points, 1024^2, Epanechnikov), the batched persistent
+    launch (256 instances, 1e4..2e6 points each) and the LSCV bandwidth fit
+    (1024^2, 200 Adam steps) on the 2M raw lane fixes (the Douglas-Peucker
+    thinning of that workload is an oracle-side step, so it is left out here)."""
+    import numpy as np
+    import torch
+
+    import paper_2004_13653_gb300 as kde
+    import workloads
+    from paper_2004_13653_gb300 import autograd as kag
+    out = {}
+    wl = workloads.config2(kernel=2)
+    pts = torch.as_tensor(wl.xy, dtype=torch.float64, device=dev)
+    w = torch.as_tensor(wl.w, device=dev)
+    F = torch.empty((wl.ny, wl.nx), device=dev)
+    ms = _time(lambda: kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "epanechnikov",
+                                out=F, path="cutoff"))
+    out["cutoff_epanechnikov_1M_1024sq"] = {
+        "ms": ms, "Gpoint_cell_per_s": wl.n * wl.nx * wl.ny / ms / 1e6,
+        "note": "definition-level rate (N nx ny / time); the path evaluates only the support"}
+    inst = workloads.config4_instances()
+    insts = [dict(points=torch.as_tensor(x.xy, dtype=torch.float64, device=dev),
+                  weights=torch.as_tensor(x.w, device=dev), origin=x.origin, cell=x.cell,
+                  nx=x.nx, ny=x.ny, h=x.h, kernel=x.kernel) for x in inst]
+    outs = [torch.empty((x.ny, x.nx), device=dev) for x in inst]
+    for d, o in zip(insts, outs):
+        d["out"] = o
+    ms = _time(lambda: kde.grid_batched(insts), reps=2)
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            kde.grid_batched(insts, stream=st)
+    torch.cuda.synchronize()
+    gms = _time(g.replay, reps=2)
+    pairs = float(sum(x.n * x.nx * x.ny for x in inst))
+    out["batched_256_instances"] = {
+        "points": int(sum(x.n for x in inst)), "ms": ms, "graph_replay_ms": gms,
+        "Gpoint_cell_per_s": pairs / gms / 1e6,
+        "kernels": {"gaussian": sum(x.kernel == 6 for x in inst),
+                    "epanechnikov": sum(x.kernel == 2 for x in inst)}}
+    del insts, outs, g
+    raw = workloads.config5_raw()
+    xy = torch.as_tensor(raw.xy, dtype=torch.float64, device=dev)
+    w0 = torch.ones(xy.shape[0], dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, _, losses = kag.fit_bandwidth(xy, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,
+                                     steps=200, lr=0.05)
+    torch.cuda.synchronize()
+    out["lscv_fit_200_steps"] = {"points": int(xy.shape[0]),
+                                 "seconds": time.perf_counter() - t0, "h_final_m": h,
+                                 "loss_first": losses[0], "loss_last": losses[-1]}
+    return out
 
 
 def cpu_baseline(args, wl, origin, ll, lat0, out_dev):

@@ -25,6 +25,17 @@ extern "C" {
 int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int per_block,
                             void* stream);
 
+/*
+ * kde_diag_wait_timeout — exercises the bounded device-side waits that every
+ * pipeline of the library uses between its producer, MMA and epilogue roles
+ * (no counterpart in the paper, which has no such pipelines): one kernel
+ * waits on a barrier nothing signals, gives up after limit_ns nanoseconds,
+ * records the timeout and returns, leaving the context usable.  Returns
+ * KDE_ETIMEOUT (the expected outcome), or KDE_EINVAL for a limit outside
+ * [1 us, 2 s].  Synchronous.
+ */
+int kde_diag_wait_timeout(int64_t limit_ns, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

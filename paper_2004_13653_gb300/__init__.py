@@ -46,7 +46,7 @@ class KdeOpts(ctypes.Structure):
 EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_project_mercator", "kde_grid_batched", "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
-           "kde_diag_exclusive_scan", "kde_grid_noalloc")
+           "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout")
 
 _lib = None
 
@@ -94,6 +94,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_grid_noalloc.argtypes = [vp, vp, i64, P(ctypes.c_double * 2), d, i32, i32, d, i32,
                                      vp, vp]
     lib.kde_grid_noalloc.restype = i32
+    lib.kde_diag_wait_timeout.argtypes = [i64, vp]
+    lib.kde_diag_wait_timeout.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
     lib.kde_diag_exclusive_scan.restype = i32
     lib.kde_version.argtypes = []

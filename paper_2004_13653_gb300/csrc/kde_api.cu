@@ -874,6 +874,25 @@ int kde_release(void) {
 
 int64_t kde_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int kde_diag_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 2000000000ll)
+    return fail(KDE_EINVAL, "limit_ns must be in [1 us, 2 s]");
+  void* ws = nullptr;
+  int rc = library_workspace(sizeof(CallScalars), &ws);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CallScalars* scal = static_cast<CallScalars*>(ws);
+  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars), s), "clear scalars");
+  KDE_CUDA(launch_wait_timeout(scal, (uint64_t)limit_ns, s), "timeout diagnostic");
+  CallScalars hs;
+  KDE_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s), "read status");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  if (hs.err & kErrTimeout)
+    return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs.timeout_where);
+  g_err[0] = 0;
+  return KDE_OK;
+}
+
 int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int per_block,
                             void* stream) {
   if (n < 0 || per_block < 1 || per_block > 2048)

@@ -192,6 +192,8 @@ struct TcPlan {
   int pair;          // 1: 256 x 256 tiles on CTA pairs (cta_group::2)
 };
 size_t tc_smem_bytes(const TcPlan& p);
+// Diagnostic: one wait that times out after limit_ns (sets kErrTimeout).
+cudaError_t launch_wait_timeout(CallScalars* scal, uint64_t limit_ns, cudaStream_t s);
 // One persistent launch over the work items of every instance in `tab`.
 cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
                       CallScalars* err, cudaStream_t s);

@@ -476,7 +476,27 @@ cudaError_t launch_ks(const TcPlan& p, const TcInst* tab, int ninst, int n_items
   return cudaErrorInvalidValue;
 }
 
+// A wait on an mbarrier that nothing signals, bounded by limit_ns: exercises
+// the timeout path of the pipelines' waits (records kErrTimeout, returns).
+__global__ void k_wait_timeout(CallScalars* scal, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0, &abort_flag, scal, 99, /*honour_abort=*/true, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout(CallScalars* scal, uint64_t limit_ns, cudaStream_t s) {
+  k_wait_timeout<<<1, 32, 0, s>>>(scal, limit_ns);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 size_t tc_smem_bytes(const TcPlan& p) {
   if (p.tile_n == 256)

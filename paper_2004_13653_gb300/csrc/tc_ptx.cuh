@@ -55,7 +55,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
 // when another role has aborted or after kWaitLimitNs, recording a timeout
 // (with the waiting role's id) in the call's scalars.  Returns false then.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          CallScalars* scal, int role, bool honour_abort = true) {
+                                          CallScalars* scal, int role, bool honour_abort = true,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
@@ -63,7 +64,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if (mbar_try_wait(a, parity)) return true;
     if ((it & 63) == 0) {
       if (honour_abort && *abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      // a second guard besides the clock: a cap on the iterations
+      if (globaltimer_ns() - t0 > limit_ns || it > (1u << 30)) {
         *abort_flag = 1;
         if (atomicOr(&scal->err, kErrTimeout) == 0) atomicExch(&scal->timeout_where, role);
         return false;
@@ -224,7 +226,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
     if (mbar_try_wait_cluster(a, parity)) return true;
     if ((it & 63) == 0) {
       if (honour_abort && *abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > kWaitLimitNs || it > (1u << 30)) {
         *abort_flag = 1;
         if (atomicOr(&scal->err, kErrTimeout) == 0) atomicExch(&scal->timeout_where, role);
         return false;
