@@ -72,6 +72,10 @@ def _load():
         lib.oracle_ved.restype = d
         lib.oracle_dp.argtypes = [vp, vp, i64, d, vp]
         lib.oracle_dp.restype = i32
+        lib.oracle_count_matrix.argtypes = [vp, vp, i64, d, d, d, i32, i32, i32, vp]
+        lib.oracle_count_matrix.restype = i64
+        lib.oracle_convolve.argtypes = [vp, i32, i32, d, d, i32, i32, i64, vp]
+        lib.oracle_convolve.restype = None
         _lib = lib
     return _lib
 
@@ -239,3 +243,27 @@ def douglas_peucker(xy, offsets, eps: float) -> np.ndarray:
     if rc != 0:
         raise MemoryError("oracle_dp failed")
     return keep.astype(bool)
+
+
+def count_matrix(xy, offsets, origin, cell, nx, ny, interpolate=True):
+    """Sec. IV-B / Algorithm 3: int32 count matrix [ny, nx] of the fixes, with the
+    Eq. InterX/InterY interpolation of skipped cells; returns (counts, added)."""
+    lib = _load()
+    xy = _f64(xy).reshape(-1, 2)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    counts = np.zeros(int(nx) * int(ny), dtype=np.int32)
+    added = lib.oracle_count_matrix(_ptr(xy), _ptr(off), off.shape[0] - 1, float(origin[0]),
+                                    float(origin[1]), float(cell), int(nx), int(ny),
+                                    int(bool(interpolate)), _ptr(counts))
+    return counts.reshape(int(ny), int(nx)), int(added)
+
+
+def convolve(counts, cell, h, kid, window, n_points) -> np.ndarray:
+    """Eq. 7: the window x window stencil f(s,t) = k(s cell/h) k(t cell/h)/(N h^2)."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+    ny, nx = c.shape
+    out = np.empty((ny, nx), dtype=np.float64)
+    lib.oracle_convolve(_ptr(c), int(nx), int(ny), float(cell), float(h), int(kid), int(window),
+                        int(n_points), _ptr(out))
+    return out

@@ -17,6 +17,9 @@
  *     at cell centres gx_i = ox + (i+1/2) cell, gy_j = oy + (j+1/2) cell
  *   - Douglas-Peucker with the vertical Euclidean distance of Eq. 9 and the
  *     "larger than epsilon" split rule ..... Sec. III-B, Sec. IV-A
+ *   - the paper's binned estimator: count matrix M_D of the projected fixes
+ *     with linear interpolation of skipped cells (Sec. IV-B, Eq. InterX/
+ *     InterY, Algorithm 3) and its discrete convolution (Eq. 7)
  *
  * Readings where the paper is silent (each is listed in the design doc):
  *   - s and t in Table 1 are offsets divided by the bandwidth h, with support
@@ -418,4 +421,71 @@ int oracle_dp(const double* xy, const int64_t* off, int64_t ntraj, double eps,
     free(st);
   }
   return 0;
+}
+
+/* ------------------------------------------- binned estimator (Eq. 7) */
+
+/* Cell of coordinate v on an axis with origin o, cell side d, n cells; -1 when
+ * outside [o, o + n d). */
+static int64_t cell_of(double v, double o, double d, int n) {
+  const double f = floor((v - o) / d);
+  if (!(f >= 0.0) || f >= (double)n) return -1;
+  return (int64_t)f;
+}
+
+/* Count matrix M_D (Sec. IV-B, Algorithm 3): every fix adds one to its cell;
+ * when `interpolate` is set, between consecutive fixes of one trajectory
+ * (both inside the grid) whose cells differ by c_max = max(|di|, |dj|) > 1
+ * the cells round(i0 + c/c_max di), round(j0 + c/c_max dj), c = 1..c_max-1,
+ * are added too (Eq. InterX / InterY; rounding = floor(v + 1/2)).
+ * off: trajectory boundaries [off[k], off[k+1]) (ntraj of them).  Returns the
+ * number of interpolated cells added. */
+int64_t oracle_count_matrix(const double* xy, const int64_t* off, int64_t ntraj, double ox,
+                            double oy, double cell, int nx, int ny, int interpolate,
+                            int32_t* counts) {
+  int64_t added = 0;
+  for (int64_t q = 0; q < (int64_t)nx * ny; ++q) counts[q] = 0;
+  for (int64_t k = 0; k < ntraj; ++k) {
+    for (int64_t p = off[k]; p < off[k + 1]; ++p) {
+      const int64_t i = cell_of(xy[2 * p], ox, cell, nx);
+      const int64_t j = cell_of(xy[2 * p + 1], oy, cell, ny);
+      if (i < 0 || j < 0) continue;
+      counts[j * nx + i] += 1;
+      if (!interpolate || p + 1 >= off[k + 1]) continue;
+      const int64_t i1 = cell_of(xy[2 * p + 2], ox, cell, nx);
+      const int64_t j1 = cell_of(xy[2 * p + 3], oy, cell, ny);
+      if (i1 < 0 || j1 < 0) continue;
+      const int64_t di = i1 - i, dj = j1 - j;
+      const int64_t cmax = llabs(di) > llabs(dj) ? llabs(di) : llabs(dj);
+      for (int64_t c = 1; c < cmax; ++c) {
+        const double t = (double)c / (double)cmax;
+        const int64_t ic = (int64_t)floor((double)i + t * (double)di + 0.5);
+        const int64_t jc = (int64_t)floor((double)j + t * (double)dj + 0.5);
+        counts[jc * nx + ic] += 1;
+        ++added;
+      }
+    }
+  }
+  return added;
+}
+
+/* Eq. 7: out(i,j) = sum_{s,t=-a..a} f(s,t) M_D(i-s, j-t) with the Table 1
+ * stencil f(s,t) = k(s cell/h) k(t cell/h) / (N h^2) (cells outside the grid
+ * count zero), a = (window-1)/2. */
+void oracle_convolve(const int32_t* counts, int nx, int ny, double cell, double h, int kid,
+                     int window, int64_t n_points, double* out) {
+  const int a = (window - 1) / 2;
+  const double norm = 1.0 / ((double)n_points * h * h);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double acc = 0.0;
+      for (int t = -a; t <= a; ++t)
+        for (int s = -a; s <= a; ++s) {
+          const int ii = i - s, jj = j - t;
+          if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+          acc += oracle_kernel_1d(kid, s * cell / h) * oracle_kernel_1d(kid, t * cell / h) *
+                 (double)counts[(int64_t)jj * nx + ii];
+        }
+      out[(int64_t)j * nx + i] = norm * acc;
+    }
 }
