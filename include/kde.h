@@ -194,6 +194,28 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss,
                   const kde_opts* opts);
 
 /*
+ * kde_grid_binned — the paper's own estimator (Sec. IV-B): the fixes are
+ * projected onto the count matrix M_D (Algorithm 3; cell = floor((x - o) /
+ * cell), fixes outside the grid are dropped), cells skipped between
+ * consecutive fixes of one trajectory are added by linear interpolation
+ * (Eq. InterX / InterY: round(i + c/c_max di), c = 1..c_max-1, when both
+ * fixes are inside the grid and interpolate != 0), and M_D is convolved with
+ * the window x window stencil f(s,t) = k(s cell/h) k(t cell/h) / (N h^2) of a
+ * Table 1 kernel (Eq. 7, N = n fixes).  window: odd, <= 255, or 0 for the
+ * compact support (2 floor(h/cell) + 1) or +-4 h for the Gaussian.  points:
+ * device [2n] interleaved metres; traj_offsets: device [ntraj+1] trajectory
+ * boundaries, or NULL for one trajectory; counts_out: device [ny*nx] int32
+ * (optional); out: device [ny*nx] FP32; interpolated: host (optional, makes
+ * the call synchronous) = number of interpolated cells added.  The counts are
+ * exact integers (identical to a CPU evaluation); the convolution is FP32.
+ * Errors: KDE_EINVAL (as kde_grid, plus window, offsets, host pointers).
+ */
+int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t ntraj,
+                    int64_t n, const double grid_origin[2], double cell, int nx, int ny,
+                    double h, int kernel_id, int window, int interpolate, int32_t* counts_out,
+                    float* out, int64_t* interpolated, const kde_opts* opts);
+
+/*
  * kde_grid_noalloc — the FP32 SIMT density (path KDE_PATH_SIMT_FP32, one
  * point split) without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory

@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
                  or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                                    "-pthread", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

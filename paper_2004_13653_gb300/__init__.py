@@ -46,7 +46,8 @@ class KdeOpts(ctypes.Structure):
 EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_project_mercator", "kde_grid_batched", "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
-           "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout")
+           "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
+           "kde_grid_binned")
 
 _lib = None
 
@@ -94,6 +95,9 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_grid_noalloc.argtypes = [vp, vp, i64, P(ctypes.c_double * 2), d, i32, i32, d, i32,
                                      vp, vp]
     lib.kde_grid_noalloc.restype = i32
+    lib.kde_grid_binned.argtypes = [vp, vp, i64, i64, P(ctypes.c_double * 2), d, i32, i32, d, i32,
+                                    i32, i32, vp, vp, P(ctypes.c_int64), P(KdeOpts)]
+    lib.kde_grid_binned.restype = i32
     lib.kde_diag_wait_timeout.argtypes = [i64, vp]
     lib.kde_diag_wait_timeout.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
@@ -288,6 +292,28 @@ def lscv_grid(F, points, weights, origin, cell, nx, ny, h, stream=None):
     check(load().kde_lscv_grid(ctypes.byref(a), _ptr(F), ctypes.byref(loss), _ptr(G), _ptr(gw),
                                _ptr(gxy), ctypes.byref(gh), ctypes.byref(o)))
     return loss.value, G, gw, gxy, gh.value
+
+
+def grid_binned(points, offsets, origin, cell, nx, ny, h, kernel="gaussian", window=0,
+                interpolate=True, stream=None, count=True):
+    """kde_grid_binned: (density [ny,nx] f32, counts [ny,nx] int32, interpolated cells).
+    With count=False the call stays asynchronous and the third value is None."""
+    import torch
+    dev = points.device
+    out = torch.empty((int(ny), int(nx)), dtype=torch.float32, device=dev)
+    counts = torch.empty((int(ny), int(nx)), dtype=torch.int32, device=dev)
+    n = _count(points) // 2
+    ntraj = 0 if offsets is None else _count(offsets) - 1
+    org = (ctypes.c_double * 2)(float(origin[0]), float(origin[1]))
+    added = ctypes.c_int64(0)
+    if stream is None:
+        stream = _current_stream(dev)
+    o = make_opts("auto", 0, stream)
+    check(load().kde_grid_binned(_ptr(points), _ptr(offsets), ntraj, n, ctypes.byref(org),
+                                 float(cell), int(nx), int(ny), float(h), kernel_id(kernel),
+                                 int(window), int(bool(interpolate)), _ptr(counts), _ptr(out),
+                                 ctypes.byref(added) if count else None, ctypes.byref(o)))
+    return out, counts, (int(added.value) if count else None)
 
 
 def project_mercator(lonlat, lat0_deg, out=None, stream=None):

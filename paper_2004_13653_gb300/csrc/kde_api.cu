@@ -874,6 +874,64 @@ int kde_release(void) {
 
 int64_t kde_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t ntraj, int64_t n,
+                    const double grid_origin[2], double cell, int nx, int ny, double h,
+                    int kernel_id, int window, int interpolate, int32_t* counts_out, float* out,
+                    int64_t* interpolated, const kde_opts* opts) {
+  if (!grid_origin) return fail(KDE_EINVAL, "grid_origin is NULL");
+  kde_args a;
+  a.points = points;
+  a.weights = nullptr;
+  a.n = n;
+  a.origin_x = grid_origin[0];
+  a.origin_y = grid_origin[1];
+  a.cell = cell;
+  a.nx = nx;
+  a.ny = ny;
+  a.h = h;
+  a.kernel_id = kernel_id;
+  a.out = out;
+  int rc = validate(&a, nullptr);
+  if (rc) return rc;
+  if (traj_offsets && ntraj < 1) return fail(KDE_EINVAL, "ntraj must be >= 1 with offsets");
+  if (ny > 64 * 65535) return fail(KDE_EINVAL, "ny = %d exceeds 4194240 rows", ny);
+  if (window < 0 || (window > 0 && ((window & 1) == 0 || window > 255)))
+    return fail(KDE_EINVAL, "window must be 0 (automatic) or odd and <= 255");
+  if ((n > 0 && memory_kind(points) != 0) || memory_kind(out) != 0 ||
+      (traj_offsets && memory_kind(traj_offsets) != 0) ||
+      (counts_out && memory_kind(counts_out) != 0))
+    return fail(KDE_EINVAL, "kde_grid_binned needs device pointers");
+  if ((traj_offsets && (reinterpret_cast<uintptr_t>(traj_offsets) & 7)) ||
+      (counts_out && (reinterpret_cast<uintptr_t>(counts_out) & 3)))
+    return fail(KDE_EINVAL, "misaligned offsets or counts");
+  cudaStream_t s = stream_of(opts);
+  const int64_t cells = (int64_t)nx * ny;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
+  const size_t o_added = take(sizeof(unsigned long long));
+  const size_t o_counts = take(counts_out ? 0 : sizeof(int) * (size_t)cells);
+  const size_t o_rows = take(sizeof(float) * (size_t)cells);
+  void* wsv = nullptr;
+  rc = acquire_workspace(opts, off, s, &wsv);
+  if (rc) return rc;
+  char* base = static_cast<char*>(wsv);
+  int* counts = counts_out ? reinterpret_cast<int*>(counts_out) : reinterpret_cast<int*>(base + o_counts);
+  unsigned long long* added = reinterpret_cast<unsigned long long*>(base + o_added);
+  const int win = binned_window(kernel_id, h, cell, window);
+  KDE_CUDA(launch_binned(points, n, traj_offsets, ntraj, grid_origin[0], grid_origin[1], cell, nx,
+                         ny, h, kernel_id, win, interpolate, counts,
+                         reinterpret_cast<float*>(base + o_rows), added, out, s),
+           "binned estimator");
+  if (interpolated || (opts && (opts->flags & KDE_FLAG_SYNC))) {
+    unsigned long long hv = 0;
+    KDE_CUDA(cudaMemcpyAsync(&hv, added, sizeof(hv), cudaMemcpyDeviceToHost, s), "read count");
+    KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+    if (interpolated) *interpolated = (int64_t)hv;
+  }
+  g_err[0] = 0;
+  return KDE_OK;
+}
+
 int kde_diag_wait_timeout(int64_t limit_ns, void* stream) {
   if (limit_ns < 1000 || limit_ns > 2000000000ll)
     return fail(KDE_EINVAL, "limit_ns must be in [1 us, 2 s]");

@@ -180,6 +180,14 @@ size_t sum_partials(int64_t n);
 cudaError_t launch_sum(const double* v, int64_t n, double* partial, double* result,
                        cudaStream_t s);
 
+// The paper's binned estimator: count matrix with interpolation (Algorithm 3)
+// and the separable window x window convolution of Eq. 7.
+int binned_window(int kid, double h, double cell, int window);
+cudaError_t launch_binned(const double* xy, int64_t n, const int64_t* off, int64_t ntraj,
+                          double ox, double oy, double cell, int nx, int ny, double h, int kid,
+                          int window, int interpolate, int* counts, float* rowbuf,
+                          unsigned long long* added, float* out, cudaStream_t s);
+
 // Path (b): Gaussian as a tcgen05 contraction.
 struct TcPlan {
   int tile_n;        // 128 or 256 grid rows (y) per tile; tile_m is 128 (x)
