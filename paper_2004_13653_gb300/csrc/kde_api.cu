@@ -177,11 +177,18 @@ struct InstPlan {
   // tensor-core path
   int tiles_m, tiles_n, items;
   int64_t per_split;
-  // cutoff path
+  // cutoff path, and the bin sort of block-sparse tensor-core instances
   CutoffGeom geo;
   int bin_begin;
   int64_t cut_begin;
+  int tile_begin;  // block-sparse: first tile in the batch's tile numbering
 };
+
+// Block-sparse skipping: reach of a Gaussian operand in prepared units
+// (h sqrt(2 ln 2)).  2^(15 - 6.45^2) < 2^-26.6, which rounds to zero in FP16
+// (hi and lo alike); the margin over the exact bound sqrt(41) = 6.403 covers
+// the FP32 rounding of the offsets and of ex2.approx.
+constexpr double kSparseReach = 6.45;
 
 struct BatchPlan {
   int count;
@@ -189,7 +196,10 @@ struct BatchPlan {
   TcPlan tc;
   std::vector<int> tc_order;  // TC instances, most expensive items first
   int n_tc = 0, n_cut = 0, n_simt = 0, n_reduce = 0, tc_items = 0, max_side = 1;
-  int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0;
+  int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0, cut_bins = 0;
+  bool sparse = false;  // block-sparse tensor-core instances
+  int tiles_total = 0, piece_len = 0, max_pieces = 0;
+  size_t off_sp_total = 0, off_sp_np = 0, off_sp_pb = 0, off_sp_temp = 0, off_sp_part = 0;
   CutoffSizes cz;
   bool host_pts = false, host_w = false, host_out = false;
   size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
@@ -246,8 +256,12 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   t.splits = 1;
   // CTA pairs (256 x 256 tiles, cta_group::2) halve each SM's operand reads
   // per MMA; they are the default for split-FP16 with 256-wide tiles
-  const bool want_pair = o && (o->flags & KDE_FLAG_CTA_PAIR);
+  // block-sparse skipping runs on CTA pairs
+  const bool want_sparse = t.skip_zero && tc_split16 >= 0;
+  const bool want_pair = o && ((o->flags & KDE_FLAG_CTA_PAIR) || want_sparse);
   const bool no_pair = o && (o->flags & KDE_FLAG_ONE_CTA);
+  if (want_sparse && no_pair)
+    return fail(KDE_ENOTSUP, "KDE_FLAG_SKIP_ZERO runs on CTA pairs; KDE_FLAG_ONE_CTA excludes it");
   if (want_pair && no_pair) return fail(KDE_EINVAL, "KDE_FLAG_CTA_PAIR and KDE_FLAG_ONE_CTA conflict");
   if (want_pair) {
     if ((o->tile_n && o->tile_n != 256) || (o->stage_points && o->stage_points != 64))
@@ -259,6 +273,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   if (want_pair && !pair_ok)
     return fail(KDE_EINVAL, "CTA-pair tiles need tile_n 256, 64-point stages and two CTAs");
   t.pair = want_pair || (!no_pair && pair_ok && tc_split16 == 1) ? 1 : 0;
+  P->sparse = want_sparse;
   if (tc_split16 >= 0 && (t.k_chunk % t.stage_points || t.k_chunk < 2 * t.stage_points))
     return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
                 t.k_chunk, t.stage_points);
@@ -288,6 +303,13 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
         splits = (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 64}));
       }
       ++P->n_simt;
+    } else if (is_tc(I.path) && P->sparse) {
+      // block-sparse: the work list is built on the device; no point splits
+      splits = 1;
+      I.per_split = I.n_pad;
+      I.items = 0;
+      P->tc_order.push_back(k);
+      ++P->n_tc;
     } else if (is_tc(I.path)) {
       const int64_t tiles = (int64_t)I.tiles_m * I.tiles_n;
       if (splits == 0) {
@@ -305,7 +327,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       ++P->n_tc;
     } else {  // cutoff
       splits = 1;
-      I.geo = cutoff_geometry(a->nx, a->ny, a->cell, a->h);
+      I.geo = cutoff_geometry(a->nx, a->ny, a->cell / a->h, 1.0);
       I.bin_begin = (int)P->total_bins;
       P->total_bins += I.geo.nbins;
       I.cut_begin = P->cut_m;
@@ -318,11 +340,50 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       P->reduce_cells += (int64_t)a->nx * a->ny;
     }
   }
-  if (P->total_bins >= ((int64_t)1 << 31)) return fail(KDE_EINVAL, "too many bins in one batch");
   // most expensive work items first, so round-robin CTAs balance
   std::stable_sort(P->tc_order.begin(), P->tc_order.end(), [&](int x, int y) {
     return P->in[x].per_split > P->in[y].per_split;
   });
+  P->cut_bins = P->total_bins;
+  if (P->sparse) {
+    // bins of the block-sparse instances follow the cutoff bins in the sort
+    double est = 0.0;
+    int64_t bound = 0;
+    for (int k : P->tc_order) {
+      const kde_args* a = &A[k];
+      InstPlan& I = P->in[k];
+      const double cs = a->cell * kernel_sigma(KDE_GAUSSIAN, a->h);
+      I.geo = cutoff_geometry(a->nx, a->ny, cs, kSparseReach);
+      I.bin_begin = (int)P->total_bins;
+      P->total_bins += I.geo.nbins;
+      I.cut_begin = P->cut_m;
+      P->cut_m += I.n_pad;
+      I.tile_begin = P->tiles_total;
+      P->tiles_total += I.tiles_m * I.tiles_n;
+      est += 1.5 * (double)I.n_pad;
+    }
+    // pieces of about an eighth of each CTA pair's share, in whole drain chunks
+    const int clusters = std::max(1, ctas / 2);
+    int64_t L = (int64_t)(est / (8.0 * clusters));
+    L = std::max<int64_t>(2048, std::min<int64_t>(32768, L));
+    L = (L + t.k_chunk - 1) / t.k_chunk * t.k_chunk;
+    P->piece_len = (int)L;
+    for (int k : P->tc_order) {
+      const kde_args* a = &A[k];
+      const InstPlan& I = P->in[k];
+      // a bin lies within reach of at most `per_axis` tiles along each axis
+      const double rc = kSparseReach / (a->cell * kernel_sigma(KDE_GAUSSIAN, a->h));
+      const int64_t per_axis = (int64_t)std::ceil((288.0 + 2.0 * rc) / 256.0) + 1;
+      const int64_t tiles = (int64_t)I.tiles_m * I.tiles_n;
+      const int64_t reach_tiles = std::min(per_axis * per_axis, tiles);
+      bound += (I.n_pad * reach_tiles + L - 1) / L + tiles;
+    }
+    if (bound > (1 << 24) || P->tiles_total > (1 << 26))
+      return fail(KDE_EINVAL, "block-sparse work list too large (%lld pieces)", (long long)bound);
+    P->max_pieces = (int)bound;
+  }
+  if (P->total_bins >= ((int64_t)1 << 31)) return fail(KDE_EINVAL, "too many bins in one batch");
+  if (P->cut_m >= ((int64_t)1 << 32)) return fail(KDE_EINVAL, "too many points to sort in one batch");
   for (int k : P->tc_order) P->tc_items += P->in[k].items;
   if ((int64_t)P->tc_items > 0x7fffffff) return fail(KDE_EINVAL, "too many work items");
   P->cz = cutoff_sizes(P->cut_m, P->total_bins);
@@ -334,7 +395,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   P->off_wts = take(sizeof(float) * (size_t)P->total_pad);
   P->off_tab_prep = take(sizeof(PrepInst) * (size_t)count);
   P->off_tab_tc = take(sizeof(TcInst) * (size_t)std::max(P->n_tc, 1));
-  P->off_tab_cut = take(sizeof(CutInst) * (size_t)std::max(P->n_cut, 1));
+  P->off_tab_cut = take(sizeof(CutInst) * (size_t)std::max(P->n_cut + (P->sparse ? P->n_tc : 0), 1));
   P->off_tab_red = take(sizeof(ReduceInst) * (size_t)std::max(P->n_reduce, 1));
   for (int k = 0; k < count; ++k) {
     InstPlan& I = P->in[k];
@@ -342,7 +403,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     I.off_gyt = take(sizeof(float2) * (size_t)A[k].ny);
     I.off_part = I.splits > 1 ? take(sizeof(float) * (size_t)A[k].nx * A[k].ny * I.splits) : 0;
   }
-  if (P->n_cut) {
+  if (P->n_cut || P->sparse) {
     const size_t u = sizeof(uint32_t);
     for (int k = 0; k < 2; ++k) {
       P->off_co_keys[k] = take(u * (size_t)P->cut_m);
@@ -354,6 +415,14 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     P->off_co_start = take(u * ((size_t)P->total_bins + 1));
     P->off_co_spts = take(sizeof(float4) * (size_t)P->cut_m);
     P->off_co_sw = take(sizeof(float) * (size_t)P->cut_m);
+  }
+  if (P->sparse) {
+    const size_t u = sizeof(uint32_t);
+    P->off_sp_total = take(u * (size_t)P->tiles_total);
+    P->off_sp_np = take(u * ((size_t)P->tiles_total + 1));
+    P->off_sp_pb = take(u * ((size_t)P->tiles_total + 1));
+    P->off_sp_temp = take(u * sparse_scan_words(P->tiles_total));
+    P->off_sp_part = take(sizeof(float) * 65536 * (size_t)P->max_pieces);
   }
   P->off_hxy = take(P->host_pts ? sizeof(double) * 2 * (size_t)A[0].n : 0);
   P->off_hw = take(P->host_w ? sizeof(float) * (size_t)A[0].n : 0);
@@ -483,6 +552,22 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     q.base_scale = a->n > 0 ? (float)(0x1p-30 / (2.0 * 3.14159265358979323846 * (double)a->n *
                                                  a->h * a->h))
                             : 0.0f;
+    q.start = nullptr;
+    q.cs = q.reach = q.inv_binw = 0.0;
+    q.nbx = q.nby = q.bin_begin = q.tile_begin = 0;
+    if (P.sparse) {  // points in bin order; the sparse reduce writes the output
+      q.pts = reinterpret_cast<const float4*>(base + P.off_co_spts);
+      q.wts = reinterpret_cast<const float*>(base + P.off_co_sw);
+      q.part = out_dev[k];
+      q.start = reinterpret_cast<const uint32_t*>(base + P.off_co_start);
+      q.cs = prep[k].cell_sigma;
+      q.reach = kSparseReach;
+      q.inv_binw = I.geo.inv_binw;
+      q.nbx = I.geo.nbx;
+      q.nby = I.geo.nby;
+      q.bin_begin = I.bin_begin;
+      q.tile_begin = I.tile_begin;
+    }
     item_begin += I.items;
     tct.push_back(q);
   }
@@ -500,6 +585,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.inv_binw = I.geo.inv_binw;
       q.ext_x = I.geo.ext_x;
       q.ext_y = I.geo.ext_y;
+      q.reach = 1.0;
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
       q.R = I.geo.R;
@@ -520,6 +606,35 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       red.push_back(q);
     }
   }
+  const int n_cut_only = (int)cut.size();
+  if (P.sparse) {  // bin-sort entries of the block-sparse instances, after the cutoff ones
+    for (int k : P.tc_order) {
+      const InstPlan& I = P.in[k];
+      CutInst q = {};
+      q.gxt = prep[k].gxt;
+      q.gyt = prep[k].gyt;
+      q.out = out_dev[k];
+      q.n = A[k].n;
+      q.n_pad = I.n_pad;
+      q.prep_begin = I.prep_begin;
+      q.cut_begin = I.cut_begin;
+      q.inv_binw = I.geo.inv_binw;
+      q.ext_x = I.geo.ext_x;
+      q.ext_y = I.geo.ext_y;
+      q.reach = kSparseReach;
+      q.nbx = I.geo.nbx;
+      q.nby = I.geo.nby;
+      q.R = I.geo.R;
+      q.bin_begin = I.bin_begin;
+      q.nx = A[k].nx;
+      q.ny = A[k].ny;
+      q.kid = KDE_GAUSSIAN;
+      cut.push_back(q);
+    }
+    // cut_begin must increase along the table for the key kernel's search
+    std::stable_sort(cut.begin() + n_cut_only, cut.end(),
+                     [](const CutInst& x, const CutInst& y) { return x.cut_begin < y.cut_begin; });
+  }
   PrepInst* d_prep = reinterpret_cast<PrepInst*>(base + P.off_tab_prep);
   TcInst* d_tc = reinterpret_cast<TcInst*>(base + P.off_tab_tc);
   CutInst* d_cut = reinterpret_cast<CutInst*>(base + P.off_tab_cut);
@@ -536,19 +651,8 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   KDE_CUDA(launch_prepare(d_prep, count, P.total_pad, P.max_side, s), "prepare points");
   cudaEvent_t* ev = o ? static_cast<cudaEvent_t*>(o->timing_events) : nullptr;
   if (ev) KDE_CUDA(cudaEventRecord(ev[0], s), "record start event");
-  if (P.n_tc)
-    KDE_CUDA(P.tc.pair ? launch_tc_pair(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s)
-                       : launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s),
-             "tensor-core contraction");
-  for (int k = 0; k < count; ++k) {
-    const InstPlan& I = P.in[k];
-    if (I.path != KDE_PATH_SIMT_FP32) continue;
-    KDE_CUDA(launch_simt(A[k].kernel_id, prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
-                         prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k), part_of(k), s),
-             "SIMT direct sum");
-  }
-  if (P.n_cut) {
-    CutoffScratch cs;
+  CutoffScratch cs;
+  if (P.n_cut || P.sparse) {
     for (int k = 0; k < 2; ++k) {
       cs.keys[k] = reinterpret_cast<uint32_t*>(base + P.off_co_keys[k]);
       cs.vals[k] = reinterpret_cast<uint32_t*>(base + P.off_co_vals[k]);
@@ -559,9 +663,37 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     cs.start = reinterpret_cast<uint32_t*>(base + P.off_co_start);
     cs.spts = reinterpret_cast<float4*>(base + P.off_co_spts);
     cs.sw = reinterpret_cast<float*>(base + P.off_co_sw);
-    KDE_CUDA(launch_cutoff(d_cut, P.n_cut, P.cut_m, P.total_bins, pts, wts, P.cz, cs, s),
-             "cutoff evaluation");
+    KDE_CUDA(launch_bin_sort(d_cut, (int)cut.size(), P.cut_m, P.total_bins, pts, wts, P.cz, cs, s),
+             "bin sort");
   }
+  if (P.n_tc && P.sparse) {
+    SparseCtl sp;
+    sp.piece_begin = reinterpret_cast<const uint32_t*>(base + P.off_sp_pb);
+    sp.tile_total = reinterpret_cast<const uint32_t*>(base + P.off_sp_total);
+    sp.part = reinterpret_cast<float*>(base + P.off_sp_part);
+    sp.tiles_total = P.tiles_total;
+    sp.piece_len = P.piece_len;
+    sp.max_pieces = P.max_pieces;
+    KDE_CUDA(launch_sparse_plan(d_tc, P.n_tc, sp, reinterpret_cast<uint32_t*>(base + P.off_sp_np),
+                                reinterpret_cast<uint32_t*>(base + P.off_sp_temp), batch_scal, s),
+             "block-sparse work list");
+    KDE_CUDA(launch_tc_pair(P.tc, d_tc, P.n_tc, 0, &sp, batch_scal, s),
+             "block-sparse tensor-core contraction");
+    KDE_CUDA(launch_sparse_reduce(d_tc, P.n_tc, sp, s), "block-sparse reduce");
+  } else if (P.n_tc) {
+    KDE_CUDA(P.tc.pair ? launch_tc_pair(P.tc, d_tc, P.n_tc, P.tc_items, nullptr, batch_scal, s)
+                       : launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s),
+             "tensor-core contraction");
+  }
+  for (int k = 0; k < count; ++k) {
+    const InstPlan& I = P.in[k];
+    if (I.path != KDE_PATH_SIMT_FP32) continue;
+    KDE_CUDA(launch_simt(A[k].kernel_id, prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
+                         prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k), part_of(k), s),
+             "SIMT direct sum");
+  }
+  if (P.n_cut)
+    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, cs, s), "cutoff evaluation");
   if (ev) KDE_CUDA(cudaEventRecord(ev[1], s), "record end event");
   if (P.n_reduce) KDE_CUDA(launch_reduce(d_red, P.n_reduce, P.reduce_cells, s), "split-K reduce");
   if (P.host_out)

@@ -32,7 +32,7 @@ __device__ __forceinline__ int find_by(const T* tab, int ninst, int64_t v, int64
   return lo;
 }
 
-// Bin key of each point of every instance (points centred and scaled by 1/h):
+// Bin key of each point of every instance (points centred and scaled):
 // key = bin_begin + by * nbx + bx, or total_bins for padding and for points
 // that cannot reach their grid.  vals = the point's index in the prepared
 // arrays.
@@ -47,8 +47,8 @@ __global__ void k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m
     if (p < I.n) {
       const float4 q = prepared[I.prep_begin + p];
       const double X = (double)q.x + (double)q.y, Y = (double)q.z + (double)q.w;
-      // a point reaches the grid only if it lies within one bandwidth of it
-      if (X >= -1.0 && Y >= -1.0 && X <= I.ext_x && Y <= I.ext_y) {
+      // a point reaches the grid only if it lies within the reach of it
+      if (X >= -I.reach && Y >= -I.reach && X <= I.ext_x && Y <= I.ext_y) {
         const int bx = min(max((int)floor(X * I.inv_binw), 0), I.nbx - 1);
         const int by = min(max((int)floor(Y * I.inv_binw), 0), I.nby - 1);
         key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
@@ -254,17 +254,16 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-CutoffGeom cutoff_geometry(int nx, int ny, double cell, double h) {
+CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach) {
   CutoffGeom g;
   g.nbx = (nx + kBin - 1) / kBin;
   g.nby = (ny + kBin - 1) / kBin;
   g.nbins = g.nbx * g.nby;
-  // bins a point can reach: its support (h) plus half a cell, in 32-cell bins
-  g.R = (int)ceil((h / cell + 1.0) / kBin);
-  const double cell_s = cell / h;  // cell side in bandwidths
-  g.inv_binw = 1.0 / (kBin * cell_s);
-  g.ext_x = nx * cell_s + 1.0;
-  g.ext_y = ny * cell_s + 1.0;
+  // bins a point can reach: its support plus half a cell, in 32-cell bins
+  g.R = (int)ceil((reach / cs + 1.0) / kBin);
+  g.inv_binw = 1.0 / (kBin * cs);
+  g.ext_x = nx * cs + reach;
+  g.ext_y = ny * cs + reach;
   return g;
 }
 
@@ -279,9 +278,9 @@ CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {
   return z;
 }
 
-cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
-                          const float4* prepared, const float* prepared_w, const CutoffSizes& z,
-                          CutoffScratch ws, cudaStream_t s) {
+cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
+                            const float4* prepared, const float* prepared_w, const CutoffSizes& z,
+                            CutoffScratch ws, cudaStream_t s) {
   if (ninst <= 0 || m <= 0) return cudaSuccess;
   k_bin_keys<<<grid_for(m), 256, 0, s>>>(tab, ninst, m, prepared, (uint32_t)total_bins,
                                          ws.keys[0], ws.vals[0]);
@@ -309,8 +308,13 @@ cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t tota
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_permute<<<grid_for(m), 256, 0, s>>>(prepared, prepared_w, ws.vals[cur], m, ws.spts, ws.sw);
   note_launches(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_cutoff<<<(unsigned)total_bins, 256, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
+                               const CutoffScratch& ws, cudaStream_t s) {
+  if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
+  k_cutoff<<<(unsigned)cut_bins, 256, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -80,10 +80,44 @@ struct TcInst {
   const float2* gxt;
   const float2* gyt;
   const CallScalars* scal;  // holds max |w| of the instance
-  float* part;              // [splits][ny][nx]
+  float* part;              // [splits][ny][nx]; with block-sparse skipping: the output
   int64_t n_pad, per_split;
   int nx, ny, tiles_m, tiles_n, splits, item_begin, chunk_stages;
   float base_scale;  // 2^-30 / (2 pi N h^2); times max |w|
+  // block-sparse skipping (pts / wts then hold the points in bin order)
+  const uint32_t* start;  // bin starts of the shared sort
+  double cs, reach, inv_binw;  // cell and reach in prepared units, 1 / bin width
+  int nbx, nby, bin_begin, tile_begin;
+};
+
+// Points of bin rows lo_by..hi_by, columns lo_bx..hi_bx can reach the 256 x 256
+// tile (tm, tn): every other point lies farther than `reach` (prepared units)
+// from each of the tile's cell centres along x or along y.  Used by both the
+// planning kernel and the contraction, so the two agree bit for bit.
+struct BinRange {
+  int lo_bx, hi_bx, lo_by, hi_by;
+};
+__host__ __device__ inline BinRange tile_bins(double cs, double reach, double inv_binw, int nbx,
+                                              int nby, int tm, int tn) {
+  BinRange r;
+  const double x0 = ((double)tm * 256 + 0.5) * cs - reach, x1 = ((double)tm * 256 + 255.5) * cs + reach;
+  const double y0 = ((double)tn * 256 + 0.5) * cs - reach, y1 = ((double)tn * 256 + 255.5) * cs + reach;
+  r.lo_bx = (int)fmax(0.0, floor(x0 * inv_binw));
+  r.hi_bx = (int)fmin((double)(nbx - 1), floor(x1 * inv_binw));
+  r.lo_by = (int)fmax(0.0, floor(y0 * inv_binw));
+  r.hi_by = (int)fmin((double)(nby - 1), floor(y1 * inv_binw));
+  return r;
+}
+
+// Work list of the block-sparse contraction: each tile's points (its bin
+// rows' runs, concatenated) cut into pieces of piece_len points; piece p of
+// all tiles is work item piece_begin[tile] + p and owns partial tile p of
+// `part` (256 x 256 floats, [j_local][i_local]).
+struct SparseCtl {
+  const uint32_t* piece_begin;  // [tiles_total + 1], exclusive scan of pieces per tile
+  const uint32_t* tile_total;   // [tiles_total] points that can reach each tile
+  float* part;                  // [max_pieces][256][256]
+  int tiles_total, piece_len, max_pieces;
 };
 
 struct CutInst {
@@ -91,7 +125,7 @@ struct CutInst {
   const float2* gyt;
   float* out;
   int64_t n, n_pad, prep_begin, cut_begin;  // point ranges (prepared / cutoff spaces)
-  double inv_binw, ext_x, ext_y;
+  double inv_binw, ext_x, ext_y, reach;     // reach: support radius in prepared units
   int nbx, nby, R, bin_begin, nx, ny, kid;
   float scale;
 };
@@ -142,7 +176,8 @@ struct CutoffGeom {
   int nbx, nby, nbins, R;
   double inv_binw, ext_x, ext_y;
 };
-CutoffGeom cutoff_geometry(int nx, int ny, double cell, double h);
+// cs: cell side in prepared units; reach: support radius in prepared units.
+CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach);
 struct CutoffScratch {
   uint32_t* keys[2];
   uint32_t* vals[2];
@@ -158,9 +193,14 @@ struct CutoffSizes {
   size_t hist_words, scan_words;
 };
 CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
-cudaError_t launch_cutoff(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
-                          const float4* prepared, const float* prepared_w, const CutoffSizes& z,
-                          CutoffScratch ws, cudaStream_t s);
+// Keys, stable radix sort, bin starts and the permuted points for every
+// instance of `tab` (cutoff instances and block-sparse tensor-core instances).
+cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
+                            const float4* prepared, const float* prepared_w, const CutoffSizes& z,
+                            CutoffScratch ws, cudaStream_t s);
+// The cutoff evaluation of the first ninst instances (bins 0..cut_bins-1).
+cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
+                               const CutoffScratch& ws, cudaStream_t s);
 
 // Adjoint of the Gaussian density (points prepared with sigma = 1/h) and the
 // grid LSCV loss.  hterm / lterm: per-point FP64 terms of dL/dh.
@@ -206,7 +246,17 @@ cudaError_t launch_wait_timeout(CallScalars* scal, uint64_t limit_ns, cudaStream
 cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
                       CallScalars* err, cudaStream_t s);
 // The same on CTA pairs (tiles_m / tiles_n of the table count 256-cell tiles).
+// With sp != nullptr the work items are the pieces of the block-sparse work
+// list (their count is read on the device).
 cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
-                           CallScalars* err, cudaStream_t s);
+                           const SparseCtl* sp, CallScalars* err, cudaStream_t s);
+// Block-sparse work list: tile totals, pieces per tile, their exclusive scan.
+size_t sparse_scan_words(int tiles_total);
+cudaError_t launch_sparse_plan(const TcInst* tab, int ninst, const SparseCtl& sp,
+                               uint32_t* npieces, uint32_t* scan_temp, CallScalars* err,
+                               cudaStream_t s);
+// Sum each tile's piece partials in order into the instance outputs.
+cudaError_t launch_sparse_reduce(const TcInst* tab, int ninst, const SparseCtl& sp,
+                                 cudaStream_t s);
 
 }  // namespace kde

@@ -68,8 +68,10 @@ struct PairCfg {
 struct Item {
   const TcInst* I;
   int tm, tn, s;
-  int64_t k_begin;
+  int64_t k_begin;  // dense: first point; sparse: first position in the tile's runs
   int nst;
+  int64_t slot;     // sparse: the piece's partial tile
+  int64_t vend;     // sparse: end position in the tile's runs
 };
 
 __device__ __forceinline__ Item pair_item(const TcInst* __restrict__ tab, int ninst, int it) {
@@ -89,13 +91,86 @@ __device__ __forceinline__ Item pair_item(const TcInst* __restrict__ tab, int ni
   int64_t k_end = r.k_begin + r.I->per_split;
   if (k_end > r.I->n_pad) k_end = r.I->n_pad;
   r.nst = k_end > r.k_begin ? (int)((k_end - r.k_begin) / kKS) : 0;
+  r.slot = 0;
+  r.vend = k_end;
   return r;
 }
 
-template <bool SPLIT>
+// Block-sparse work item `it`: the tile whose pieces contain it, the piece's
+// range of positions in the concatenation of the tile's bin-row runs.
+__device__ __forceinline__ Item sparse_item(const TcInst* __restrict__ tab, int ninst,
+                                            const SparseCtl& sp, int it) {
+  int lo = 0, hi = sp.tiles_total - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)__ldg(sp.piece_begin + mid) <= it) lo = mid; else hi = mid - 1;
+  }
+  const int t = lo;
+  int a = 0, b = ninst - 1;
+  while (a < b) {
+    const int mid = (a + b + 1) >> 1;
+    if (tab[mid].tile_begin <= t) a = mid; else b = mid - 1;
+  }
+  Item r;
+  r.I = tab + a;
+  const int local = t - r.I->tile_begin;
+  r.tm = local % r.I->tiles_m;
+  r.tn = local / r.I->tiles_m;
+  r.s = 0;
+  r.k_begin = (int64_t)(it - (int)__ldg(sp.piece_begin + t)) * sp.piece_len;
+  const int64_t total = __ldg(sp.tile_total + t);
+  r.vend = min(total, r.k_begin + (int64_t)sp.piece_len);
+  r.nst = r.vend > r.k_begin ? (int)((r.vend - r.k_begin + kKS - 1) / kKS) : 0;
+  r.slot = it;
+  return r;
+}
+
+template <bool SPARSE>
+__device__ __forceinline__ Item get_item(const TcInst* __restrict__ tab, int ninst,
+                                         const SparseCtl& sp, int it) {
+  if (SPARSE) return sparse_item(tab, ninst, sp, it);
+  return pair_item(tab, ninst, it);
+}
+
+// Walks the bin-row runs of one tile in increasing position order and maps a
+// position to an index of the sorted points.
+struct RunCursor {
+  const uint32_t* start;
+  int row0, nbx, lo_bx, hi_bx, by, hi_by;
+  int64_t vr;         // position of the current run's first point
+  uint32_t ra, rb;    // the current run in the sorted points
+  __device__ __forceinline__ void load_run() {
+    const int row = row0 + by * nbx;
+    ra = __ldg(start + row + lo_bx);
+    rb = __ldg(start + row + hi_bx + 1);
+  }
+  __device__ __forceinline__ void init(const TcInst& I, int tm, int tn) {
+    const BinRange br = tile_bins(I.cs, I.reach, I.inv_binw, I.nbx, I.nby, tm, tn);
+    start = I.start;
+    row0 = I.bin_begin;
+    nbx = I.nbx;
+    lo_bx = br.lo_bx;
+    hi_bx = br.hi_bx;
+    by = br.lo_by;
+    hi_by = br.hi_by;
+    vr = 0;
+    load_run();
+  }
+  // index of position v (v below the tile's total)
+  __device__ __forceinline__ int64_t map(int64_t v) {
+    while (v >= vr + (int64_t)(rb - ra) && by < hi_by) {
+      vr += rb - ra;
+      ++by;
+      load_run();
+    }
+    return (int64_t)ra + (v - vr);
+  }
+};
+
+template <bool SPLIT, bool SPARSE>
 __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
-    k_tc_pair(const TcInst* __restrict__ tab, int ninst, int n_items,
-              CallScalars* __restrict__ scal) {
+    k_tc_pair(const TcInst* __restrict__ tab, int ninst, int n_items_arg,
+              const __grid_constant__ SparseCtl sp, CallScalars* __restrict__ scal) {
   using C = PairCfg<SPLIT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -112,6 +187,13 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kOffMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int n_items = n_items_arg;
+  if (SPARSE) {  // the work list was built on the device by the preceding launches
+    const int listed = (int)__ldg(sp.piece_begin + sp.tiles_total);
+    n_items = min(listed, sp.max_pieces);
+    if (listed > sp.max_pieces && blockIdx.x == 0 && threadIdx.x == 0)
+      atomicOr(&scal->err, kErrBadArg);
+  }
   const uint32_t rank = cluster_rank();
   const uint32_t peer = rank ^ 1u;
   const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
@@ -148,7 +230,7 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
       bool ok = true;
       const uint32_t smem_base = smem_u32(smem);
       for (int it = cluster; ok && it < n_items; it += n_clusters) {
-        const Item itm = pair_item(tab, ninst, it);
+        const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
         const int CS = itm.I->chunk_stages;
         for (int st = 0; ok && st < itm.nst; ++st, ++g) {
           const bool fresh = st % CS == 0;
@@ -189,12 +271,14 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
     uint32_t g = 0;
     bool ok = true, negative = false;
     for (int it = cluster; ok && it < n_items; it += n_clusters) {
-      const Item itm = pair_item(tab, ninst, it);
+      const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const float wmax = __uint_as_float(I.scal->wmax_bits);
       const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
       const float2 cx = I.gxt[min(itm.tm * 256 + (int)rank * kRows + kRows / 2, I.nx - 1)];
       const float2 cy = I.gyt[min(itm.tn * 256 + (int)rank * kRows + kRows / 2, I.ny - 1)];
+      RunCursor cur;
+      if (SPARSE) cur.init(I, itm.tm, itm.tn);
       for (int st = 0; ok && st < itm.nst; st += kGroup) {
         const int ng = min(kGroup, itm.nst - st);
         float4 P[kGroup][2];
@@ -204,9 +288,18 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh)
             if (u < ng) {
-              const int64_t p = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
-              P[u][hh] = __ldg(I.pts + p);
-              W[u][hh] = __ldg(I.wts + p);
+              const int64_t v = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
+              if (!SPARSE) {
+                P[u][hh] = __ldg(I.pts + v);
+                W[u][hh] = __ldg(I.wts + v);
+              } else if (v < itm.vend) {
+                const int64_t p = cur.map(v);
+                P[u][hh] = __ldg(I.pts + p);
+                W[u][hh] = __ldg(I.wts + p);
+              } else {  // past the piece: a zero-weight point (B = 0)
+                P[u][hh] = make_float4(0.f, 0.f, 0.f, 0.f);
+                W[u][hh] = 0.f;
+              }
             }
 #pragma unroll
         for (int u = 0; u < kGroup; ++u) {
@@ -241,7 +334,7 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
     uint32_t dc = 0;
     bool ok = true;
     for (int it = cluster; ok && it < n_items; it += n_clusters) {
-      const Item itm = pair_item(tab, ninst, it);
+      const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const int nx = I.nx, ny = I.ny, CS = I.chunk_stages;
       const float wmax = __uint_as_float(I.scal->wmax_bits);
@@ -249,7 +342,11 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
       const int i = itm.tm * 256 + (int)rank * kRows + q * 32 + lane;
       const int j0 = itm.tn * 256 + colh * 128;
       float* slot = I.part + (int64_t)itm.s * nx * ny;
-      if (itm.nst == 0) {
+      // sparse: the piece's own 256 x 256 partial, [j_local][i_local]
+      float* piece = SPARSE ? sp.part + itm.slot * 65536 + (int64_t)(colh * 128) * 256 +
+                                  (int)rank * kRows + q * 32 + lane
+                            : nullptr;
+      if (!SPARSE && itm.nst == 0) {
         if (i < nx)
           for (int c = 0; c < 128 && j0 + c < ny; ++c) slot[(int64_t)(j0 + c) * nx + i] = 0.f;
         continue;
@@ -271,7 +368,10 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 32; ++c) a[c] += r[c];
           }
-          if (final) {
+          if (final && SPARSE) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) piece[(cb * 32 + c) * 256] = a[c] * scale;
+          } else if (final) {
             if (i < nx) {
 #pragma unroll
               for (int c = 0; c < 32; ++c) {
@@ -302,7 +402,7 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
     uint32_t g = 0;
     bool ok = true;
     for (int it = cluster; ok && it < n_items; it += n_clusters) {
-      const Item itm = pair_item(tab, ninst, it);
+      const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       float gv;
       if (isA) {
@@ -385,14 +485,15 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
   }
 }
 
-template <bool SPLIT>
+template <bool SPLIT, bool SPARSE>
 cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
-                        CallScalars* err, cudaStream_t s) {
+                        const SparseCtl& sp, CallScalars* err, cudaStream_t s) {
   using C = PairCfg<SPLIT>;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_pair<SPLIT>,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_pair<SPLIT, SPARSE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  const int clusters = std::max(1, std::min(n_items, p.ctas / 2));
+  // the sparse work list's length is known only on the device
+  const int clusters = SPARSE ? std::max(1, p.ctas / 2) : std::max(1, std::min(n_items, p.ctas / 2));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * clusters);
   cfg.blockDim = dim3(C::kThreads);
@@ -405,7 +506,7 @@ cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_ite
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_tc_pair<SPLIT>, tab, ninst, n_items, err);
+  e = cudaLaunchKernelEx(&cfg, k_tc_pair<SPLIT, SPARSE>, tab, ninst, n_items, sp, err);
   note_launches(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -414,11 +515,17 @@ cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_ite
 }  // namespace
 
 cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
-                           CallScalars* err, cudaStream_t s) {
-  if (ninst < 1 || n_items < 1 || plan.ctas < 2 || plan.stage_points != kKS)
-    return cudaErrorInvalidValue;
-  return plan.split16 ? launch_pair<true>(plan, tab, ninst, n_items, err, s)
-                      : launch_pair<false>(plan, tab, ninst, n_items, err, s);
+                           const SparseCtl* sp, CallScalars* err, cudaStream_t s) {
+  if (ninst < 1 || plan.ctas < 2 || plan.stage_points != kKS) return cudaErrorInvalidValue;
+  if (sp) {
+    if (sp->tiles_total < 1 || sp->piece_len < kKS || sp->piece_len % kKS) return cudaErrorInvalidValue;
+    return plan.split16 ? launch_pair<true, true>(plan, tab, ninst, 0, *sp, err, s)
+                        : launch_pair<false, true>(plan, tab, ninst, 0, *sp, err, s);
+  }
+  if (n_items < 1) return cudaErrorInvalidValue;
+  const SparseCtl none = {};
+  return plan.split16 ? launch_pair<true, false>(plan, tab, ninst, n_items, none, err, s)
+                      : launch_pair<false, false>(plan, tab, ninst, n_items, none, err, s);
 }
 
 }  // namespace kde
