@@ -56,6 +56,8 @@ def _load():
         vp = ctypes.c_void_p
         lib.oracle_kernel_1d.argtypes = [i32, d]
         lib.oracle_kernel_1d.restype = d
+        lib.oracle_kernel_radial.argtypes = [i32, d]
+        lib.oracle_kernel_radial.restype = d
         lib.oracle_mercator.argtypes = [vp, i64, d, d, d, vp]
         lib.oracle_mercator.restype = None
         lib.oracle_kde_cells.argtypes = [vp, vp, i64, d, d, d, i32, i32, d, i32,
@@ -86,6 +88,18 @@ def _f64(a) -> np.ndarray:
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+RADIAL = 8  # kernel id of the radial variant of Table 1 kernel k: RADIAL + k
+
+
+def kernel_radial(kid: int, r) -> np.ndarray:
+    """K(r): the radial variant of Table 1 kernel kid (0..7) on the unit disk,
+    normalised over the plane."""
+    lib = _load()
+    r = np.asarray(r, dtype=np.float64)
+    out = np.array([lib.oracle_kernel_radial(int(kid), float(v)) for v in r.ravel()])
+    return out.reshape(r.shape)
 
 
 def kernel_1d(kid: int, s) -> np.ndarray:

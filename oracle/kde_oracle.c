@@ -10,7 +10,8 @@
  *
  * Passages followed (arXiv 2004.13653):
  *   - Mercator projection .................. Sec. III-A, Eq. 1-4
- *   - the eight 2-D product kernels ........ Sec. III-C, Table 1
+ *   - the eight 2-D product kernels ........ Sec. III-C, Table 1, and their
+ *     radial variants K(|u|) on the unit disk (kernel ids 8..15)
  *   - indicator I(.) (inclusive |s| <= 1) .. Sec. III-C, Eq. 8
  *   - density as a kernel sum over points .. Sec. III-C, Eq. 7, read as the
  *     direct sum F[i,j] = 1/(N h^2) sum_p w_p k((gx_i-x_p)/h) k((gy_j-y_p)/h)
@@ -80,6 +81,49 @@ double oracle_kernel_1d(int kid, double s) {
       return exp(-0.5 * s * s) / sqrt(2.0 * M_PI);
     case OR_COSINE:
       return inside ? (M_PI / 4.0) * cos(0.5 * M_PI * s) : 0.0;
+    default:
+      return NAN;
+  }
+}
+
+/* Radial variants of the Table 1 kernels (kernel ids 8..15 = 8 + the Table 1
+ * id): K(u) = c k~(|u|) on the unit disk, k~ the Table 1 profile without its
+ * 1-D constant, c = 1 / (2 pi int_0^1 r k~(r) dr) so that K integrates to one
+ * over the plane.  The integrals, by hand:
+ *   uniform 1            -> 1/2      c = 1/pi
+ *   triangular 1-r       -> 1/6      c = 3/pi
+ *   epanechnikov 1-r^2   -> 1/4      c = 2/pi
+ *   quartic (1-r^2)^2    -> 1/6      c = 3/pi
+ *   triweight (1-r^2)^3  -> 1/8      c = 4/pi
+ *   tricube (1-r^3)^3    -> 81/440   c = 220/(81 pi)
+ *   cosine cos(pi r/2)   -> 2/pi - 4/pi^2   c = pi/(4 pi - 8)
+ *   gaussian exp(-r^2/2) -> 1 (whole plane)  c = 1/(2 pi): the product kernel.
+ * kid here is the Table 1 id (0..7). */
+double oracle_kernel_radial(int kid, double r) {
+  const int inside = r <= 1.0;
+  switch (kid) {
+    case OR_UNIFORM:
+      return inside ? 1.0 / M_PI : 0.0;
+    case OR_TRIANGULAR:
+      return inside ? (3.0 / M_PI) * (1.0 - r) : 0.0;
+    case OR_EPANECHNIKOV:
+      return inside ? (2.0 / M_PI) * (1.0 - r * r) : 0.0;
+    case OR_QUARTIC: {
+      const double u = 1.0 - r * r;
+      return inside ? (3.0 / M_PI) * u * u : 0.0;
+    }
+    case OR_TRIWEIGHT: {
+      const double u = 1.0 - r * r;
+      return inside ? (4.0 / M_PI) * u * u * u : 0.0;
+    }
+    case OR_TRICUBE: {
+      const double u = 1.0 - r * r * r;
+      return inside ? (220.0 / (81.0 * M_PI)) * u * u * u : 0.0;
+    }
+    case OR_GAUSSIAN:
+      return exp(-0.5 * r * r) / (2.0 * M_PI);
+    case OR_COSINE:
+      return inside ? (M_PI / (4.0 * M_PI - 8.0)) * cos(0.5 * M_PI * r) : 0.0;
     default:
       return NAN;
   }
@@ -185,7 +229,10 @@ static void kde_body(void* vctx, int64_t lo, int64_t hi) {
       const double s = (gx - c->xy[2 * p]) / c->h;
       const double t = (gy - c->xy[2 * p + 1]) / c->h;
       const double wp = c->w ? c->w[p] : 1.0;
-      acc += wp * oracle_kernel_1d(c->kid, s) * oracle_kernel_1d(c->kid, t);
+      if (c->kid >= 8)
+        acc += wp * oracle_kernel_radial(c->kid - 8, sqrt(s * s + t * t));
+      else
+        acc += wp * oracle_kernel_1d(c->kid, s) * oracle_kernel_1d(c->kid, t);
     }
     c->out[q] = norm * acc;
   }
@@ -202,7 +249,7 @@ int oracle_kde_cells(const double* xy, const double* w, int64_t n, double ox,
     for (int64_t q = 0; q < ncells; ++q) out[q] = 0.0;
     return 0;
   }
-  if (kid < 0 || kid > 7 || nx <= 0 || ny <= 0 || !(h > 0)) return -1;
+  if (kid < 0 || kid > 15 || nx <= 0 || ny <= 0 || !(h > 0)) return -1;
   kde_ctx_t c = {xy, w, n, ox, oy, cell, h, nx, ny, kid, cells, out};
   parallel_for(ncells, 1, nthreads, kde_body, &c);
   return 0;
