@@ -35,10 +35,39 @@ METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at
 # one ncu capture (profiles/k_tc_pair_dram_20M_4096sq.md); reported only while the kernel's
 # sources hash to the value they had when the counters were taken.
 TRAFFIC = {("tc_split16", 4096, 40_000): {
-    "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh",
-                "paper_2004_13653_gb300/csrc/kde_internal.cuh"],
-    "sha256": "f3b1f267bfd72bc17be7f832b9c1002af55c756ed2355d0a06c4a1702d541616",
-    "bytes": 1412567808 + 535942912}}
+    "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh"],
+    "sha256": "b1ff2528aed7030f0b05527f4f27c28ab7e23f51777dbe7f61d0994a15917c68",
+    "bytes": 1399965184 + 534373888}}
+
+
+def sparse_products(xy, origin, cell, nx, ny, h):
+    """Point-tile pairs the block-sparse contraction multiplies out: for each
+    256 x 256 tile, the points of the 32 x 32-cell bins within 6.45 h sqrt(2 ln 2)
+    of it (the library's binning, in FP64 here).  Times 65536 cells and 2 FLOP
+    per product this is the contraction's algorithmic work."""
+    import numpy as np
+    reach, sigma = 6.45, 1.0 / (h * 1.17741002251547469101)
+    cs = cell * sigma
+    inv_binw = 1.0 / (32 * cs)
+    nbx, nby = (nx + 31) // 32, (ny + 31) // 32
+    X = (xy[:, 0] - origin[0]) * sigma
+    Y = (xy[:, 1] - origin[1]) * sigma
+    keep = (X >= -reach) & (Y >= -reach) & (X <= nx * cs + reach) & (Y <= ny * cs + reach)
+    bx = np.clip(np.floor(X[keep] * inv_binw), 0, nbx - 1).astype(np.int64)
+    by = np.clip(np.floor(Y[keep] * inv_binw), 0, nby - 1).astype(np.int64)
+    H = np.bincount(by * nbx + bx, minlength=nbx * nby).reshape(nby, nbx)
+    S = np.zeros((nby + 1, nbx + 1), np.int64)
+    S[1:, 1:] = H.cumsum(0).cumsum(1)
+    total = 0
+    for tn in range((ny + 255) // 256):
+        y0, y1 = (tn * 256 + 0.5) * cs - reach, (tn * 256 + 255.5) * cs + reach
+        ly, hy = max(0, int(np.floor(y0 * inv_binw))), min(nby - 1, int(np.floor(y1 * inv_binw)))
+        for tm in range((nx + 255) // 256):
+            x0, x1 = (tm * 256 + 0.5) * cs - reach, (tm * 256 + 255.5) * cs + reach
+            lx = max(0, int(np.floor(x0 * inv_binw)))
+            hx = min(nbx - 1, int(np.floor(x1 * inv_binw)))
+            total += S[hy + 1, hx + 1] - S[ly, hx + 1] - S[hy + 1, lx] + S[ly, lx]
+    return int(total)
 
 
 def measured_traffic(path, grid, points):
@@ -73,6 +102,7 @@ def parse():
                     help="grid side for the FP32 SIMT comparison (same points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the block-sparse leg")
     ap.add_argument("--cpu-cells", type=int, default=1200)
     ap.add_argument("--split-k", type=int, default=0)
     ap.add_argument("--k-chunk", type=int, default=0)
@@ -248,6 +278,10 @@ def run_ours(args):
     else:
         products = 3 if args.path == "tc_split16" else 1
         flops = 2.0 * products * evals
+        if args.flags & kde.FLAG_SKIP_ZERO:  # only the pairs within reach are multiplied
+            xy_proj = xy_dev.cpu().numpy().reshape(-1, 2)  # the projected fixes
+            flops = 2.0 * products * 65536.0 * sparse_products(xy_proj, origin, wl.cell, nx, ny,
+                                                                wl.h)
         peak = peaks["bf16_tflops_sustained"]
         achieved = flops / (kernel_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -322,9 +356,21 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"], sample = cpu_baseline(args, wl, origin, ll, lat0, out_dev)
 
-    if rank == 0 and args.path in ("tc_split16", "tc_fp16") and not args.flags:
+    if rank == 0 and args.path in ("tc_split16", "tc_fp16") and not args.flags \
+            and not args.no_sparse:
         result["block_sparse"] = sparse_leg(step, stream, out_dev, new_pair, kernel_ms, evals,
                                             sample)
+        products = 3 if args.path == "tc_split16" else 1
+        pt = sparse_products(xy_dev.cpu().numpy().reshape(-1, 2), origin, wl.cell, nx, ny, wl.h)
+        flops = 2.0 * products * 65536.0 * pt
+        ach = flops / (result["block_sparse"]["kernel_ms"] * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        result["block_sparse"]["point_tile_pairs"] = pt
+        result["block_sparse"]["roofline"] = {
+            "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "note": "FLOPs of the products within reach over the whole sparse step (sort, "
+                    "work list, contraction, reduce)"}
 
     if rank == 0 and args.extra:
         result["binned_estimator"] = binned_leg(dev, wl, xy_dev, origin, out_dev)
@@ -352,9 +398,9 @@ def _time(fn, reps=3):
 def extra_workloads(dev):
     """The other rows of the hot path on their own workloads: the binned
     cutoff path (1M lane points, 1024^2, Epanechnikov), the batched persistent
-    launch (256 instances, 1e4..2e6 points each) and the LSCV bandwidth fit
-    (1024^2, 200 Adam steps) on the 2M raw lane fixes (the Douglas-Peucker
-    thinning of that workload is an oracle-side step, so it is left out here)."""
+    launch (256 instances, 1e4..2e6 points each), the GPU Douglas-Peucker on
+    the 2M raw lane fixes (eps = 10 m) and the LSCV bandwidth fit (1024^2,
+    200 Adam steps) on its output."""
     import numpy as np
     import torch
 
@@ -396,15 +442,26 @@ def extra_workloads(dev):
     del insts, outs, g
     raw = workloads.config5_raw()
     xy = torch.as_tensor(raw.xy, dtype=torch.float64, device=dev)
-    w0 = torch.ones(xy.shape[0], dtype=torch.float32, device=dev)
+    off = torch.as_tensor(raw.offsets, device=dev)
+    dp_ms = _time(lambda: kde.dp_simplify(xy, off, 10.0), reps=3)
+    keep, thin, _, its = kde.dp_simplify(xy, off, 10.0)
+    # each kept fix stands for the raw fixes up to the next kept one
+    idx = np.flatnonzero(keep.cpu().numpy())
+    rep = np.diff(np.append(idx, raw.n)).astype(np.float32)
+    out["douglas_peucker_2M_eps10m"] = {
+        "points": int(raw.n), "kept": int(idx.size), "iterations": its, "ms": dp_ms,
+        "Mpoint_per_s": raw.n / dp_ms / 1e3}
+    w0 = torch.as_tensor(rep, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h, _, losses = kag.fit_bandwidth(xy, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,
+    h, _, losses = kag.fit_bandwidth(thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,
                                      steps=200, lr=0.05)
     torch.cuda.synchronize()
-    out["lscv_fit_200_steps"] = {"points": int(xy.shape[0]),
+    out["lscv_fit_200_steps"] = {"points": int(thin.shape[0]), "raw_points": int(raw.n),
                                  "seconds": time.perf_counter() - t0, "h_final_m": h,
-                                 "loss_first": losses[0], "loss_last": losses[-1]}
+                                 "loss_first": losses[0], "loss_last": losses[-1],
+                                 "input": "the GPU Douglas-Peucker output at eps = 10 m, weights "
+                                          "= raw fixes each kept fix stands for"}
     return out
 
 

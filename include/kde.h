@@ -55,13 +55,25 @@ typedef enum {
   KDE_TRIWEIGHT = 4,    /* k(s) = 35/32 (1 - s^2)^3         I(s)            */
   KDE_TRICUBE = 5,      /* k(s) = 70/81 (1 - |s|^3)^3       I(s)            */
   KDE_GAUSSIAN = 6,     /* k(s) = exp(-s^2/2) / sqrt(2 pi)                  */
-  KDE_COSINE = 7        /* k(s) = pi/4 cos(pi s / 2)        I(s)            */
+  KDE_COSINE = 7,       /* k(s) = pi/4 cos(pi s / 2)        I(s)            */
+  /* Radial variants K(u) = c k~(|u|) on the unit disk (id = 8 + Table 1 id;
+   * k~ the Table 1 profile without its constant, c = 1/(2 pi int r k~ dr) so
+   * that K integrates to one).  They run on the cutoff path; the radial
+   * Gaussian equals the product Gaussian and runs wherever KDE_GAUSSIAN does. */
+  KDE_RADIAL_UNIFORM = 8,       /* c = 1/pi                                  */
+  KDE_RADIAL_TRIANGULAR = 9,    /* c = 3/pi                                  */
+  KDE_RADIAL_EPANECHNIKOV = 10, /* c = 2/pi                                  */
+  KDE_RADIAL_QUARTIC = 11,      /* c = 3/pi                                  */
+  KDE_RADIAL_TRIWEIGHT = 12,    /* c = 4/pi                                  */
+  KDE_RADIAL_TRICUBE = 13,      /* c = 220/(81 pi)                           */
+  KDE_RADIAL_GAUSSIAN = 14,     /* = KDE_GAUSSIAN                            */
+  KDE_RADIAL_COSINE = 15        /* c = pi/(4 pi - 8)                         */
 } kde_kernel;
 
 /* ---- evaluation paths --------------------------------------------------- */
 typedef enum {
   KDE_PATH_AUTO = 0,       /* Gaussian -> TC_SPLIT16, compact -> CUTOFF       */
-  KDE_PATH_SIMT_FP32 = 1,  /* FP32 direct sum on the CUDA cores (any kernel)  */
+  KDE_PATH_SIMT_FP32 = 1,  /* FP32 direct sum on the CUDA cores (Table 1)    */
   KDE_PATH_TC_FP16 = 2,    /* Gaussian as F = A B^T on tcgen05, FP16 operands */
   KDE_PATH_TC_SPLIT16 = 3, /* same, hi/lo FP16 operands, three products       */
   KDE_PATH_CUTOFF = 4      /* binned gather over the compact support          */
@@ -220,6 +232,29 @@ int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t n
                     int64_t n, const double grid_origin[2], double cell, int nx, int ny,
                     double h, int kernel_id, int window, int interpolate, int32_t* counts_out,
                     float* out, int64_t* interpolated, const kde_opts* opts);
+
+/*
+ * kde_dp_simplify — Douglas-Peucker compression of vessel trajectories
+ * (Sec. III-B, Eq. 9), computed level-synchronously as in Sec. IV-A: all
+ * curve segments of all trajectories are split in the same iteration.  Both
+ * ends of every trajectory are kept; a segment is split at the point of
+ * largest VED (the first one on ties) when that VED is larger than eps; the
+ * VED is the distance to the line through the segment's ends, or to its start
+ * when both ends coincide.  The VED is evaluated in FP64 with every operation
+ * rounded as written, so the kept set equals a sequential FP64 evaluation.
+ * points: device [2n] interleaved metres (16-byte aligned); traj_offsets:
+ * device [ntraj+1] rising from 0 to n, or NULL for one trajectory; eps >= 0
+ * metres; keep: device [n] (1 = kept); out_points: device [2n] or NULL,
+ * receives the kept points in order; out_offsets: device [ntraj+1] or NULL,
+ * the trajectories' bounds in out_points; n_kept, iterations: host, optional.
+ * Synchronous (the loop ends when an iteration keeps no point; one host read
+ * per iteration).  Errors: KDE_EINVAL (n, eps, pointers, alignment, offsets
+ * that do not rise from 0 to n), KDE_EDATA (non-finite coordinate).
+ */
+int kde_dp_simplify(const double* points, const int64_t* traj_offsets, int64_t ntraj,
+                    int64_t n, double eps, uint8_t* keep, double* out_points,
+                    int64_t* out_offsets, int64_t* n_kept, int* iterations,
+                    const kde_opts* opts);
 
 /*
  * kde_grid_noalloc — the FP32 SIMT density (path KDE_PATH_SIMT_FP32, one

@@ -15,6 +15,8 @@ from . import build as _build
 
 KERNELS = {"uniform": 0, "triangular": 1, "epanechnikov": 2, "quartic": 3, "triweight": 4,
            "tricube": 5, "gaussian": 6, "cosine": 7}
+RADIAL = 8  # radial variant of Table 1 kernel k: RADIAL + k ("radial_<name>")
+KERNELS.update({"radial_" + k: RADIAL + v for k, v in list(KERNELS.items())})
 PATHS = {"auto": 0, "simt": 1, "tc_fp16": 2, "tc_split16": 3, "cutoff": 4}
 FLAG_SYNC, FLAG_SKIP_ZERO, FLAG_CTA_PAIR, FLAG_ONE_CTA = 1, 2, 4, 8
 
@@ -47,7 +49,7 @@ EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_project_mercator", "kde_grid_batched", "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
            "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
-           "kde_grid_binned")
+           "kde_grid_binned", "kde_dp_simplify")
 
 _lib = None
 
@@ -98,6 +100,9 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_grid_binned.argtypes = [vp, vp, i64, i64, P(ctypes.c_double * 2), d, i32, i32, d, i32,
                                     i32, i32, vp, vp, P(ctypes.c_int64), P(KdeOpts)]
     lib.kde_grid_binned.restype = i32
+    lib.kde_dp_simplify.argtypes = [vp, vp, i64, i64, d, vp, vp, vp, P(ctypes.c_int64),
+                                    P(ctypes.c_int), P(KdeOpts)]
+    lib.kde_dp_simplify.restype = i32
     lib.kde_diag_wait_timeout.argtypes = [i64, vp]
     lib.kde_diag_wait_timeout.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
@@ -314,6 +319,29 @@ def grid_binned(points, offsets, origin, cell, nx, ny, h, kernel="gaussian", win
                                  int(window), int(bool(interpolate)), _ptr(counts), _ptr(out),
                                  ctypes.byref(added) if count else None, ctypes.byref(o)))
     return out, counts, (int(added.value) if count else None)
+
+
+def dp_simplify(points, offsets, eps, stream=None, compact=True):
+    """kde_dp_simplify: (keep [n] uint8, kept points [n_kept, 2] float64 or None,
+    their trajectory offsets [ntraj+1] int64 or None, iterations)."""
+    import torch
+    dev = points.device
+    n = _count(points) // 2
+    keep = torch.empty(n, dtype=torch.uint8, device=dev)
+    ntraj = 1 if offsets is None else _count(offsets) - 1
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev) if compact else None
+    out_off = torch.empty(ntraj + 1, dtype=torch.int64, device=dev) if compact else None
+    kept = ctypes.c_int64(0)
+    its = ctypes.c_int(0)
+    if stream is None:
+        stream = _current_stream(dev)
+    o = make_opts("auto", 0, stream)
+    check(load().kde_dp_simplify(_ptr(points), _ptr(offsets), ntraj, n, float(eps), _ptr(keep),
+                                 _ptr(out), _ptr(out_off), ctypes.byref(kept), ctypes.byref(its),
+                                 ctypes.byref(o)))
+    if compact:
+        out = out[:kept.value]
+    return keep, out, out_off, its.value
 
 
 def project_mercator(lonlat, lat0_deg, out=None, stream=None):

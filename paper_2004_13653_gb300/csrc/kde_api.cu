@@ -89,6 +89,11 @@ int memory_kind(const void* p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// The radial Gaussian is the product Gaussian (exp(-|u|^2/2) factorises).
+int kid_of(const kde_args* a) {
+  return a->kernel_id == kRadial + KDE_GAUSSIAN ? KDE_GAUSSIAN : a->kernel_id;
+}
+
 int validate(const kde_args* a, const kde_opts* o) {
   if (!a) return fail(KDE_EINVAL, "args is NULL");
   if (a->n < 0) return fail(KDE_EINVAL, "n = %lld is negative", (long long)a->n);
@@ -101,8 +106,9 @@ int validate(const kde_args* a, const kde_opts* o) {
   if (!(a->h > 0) || !isfinite(a->h)) return fail(KDE_EINVAL, "h must be positive and finite");
   if (!isfinite(a->origin_x) || !isfinite(a->origin_y))
     return fail(KDE_EINVAL, "grid origin must be finite");
-  if (a->kernel_id < 0 || a->kernel_id > 7)
-    return fail(KDE_EINVAL, "kernel_id %d is not a Table 1 kernel (0..7)", a->kernel_id);
+  if (a->kernel_id < 0 || a->kernel_id > 15)
+    return fail(KDE_EINVAL, "kernel_id %d is neither a Table 1 kernel (0..7) nor a radial one (8..15)",
+                a->kernel_id);
   if (a->n > ((int64_t)1 << 31))
     return fail(KDE_EINVAL, "n = %lld exceeds 2^31 points per instance", (long long)a->n);
   // the kernels read points as double2 and write out as float
@@ -115,10 +121,12 @@ int validate(const kde_args* a, const kde_opts* o) {
     if (o->path < KDE_PATH_AUTO || o->path > KDE_PATH_CUTOFF)
       return fail(KDE_EINVAL, "unknown path %d", o->path);
     if ((o->path == KDE_PATH_TC_FP16 || o->path == KDE_PATH_TC_SPLIT16) &&
-        a->kernel_id != KDE_GAUSSIAN)
+        kid_of(a) != KDE_GAUSSIAN)
       return fail(KDE_ENOTSUP, "tensor-core paths need the Gaussian kernel");
-    if (o->path == KDE_PATH_CUTOFF && a->kernel_id == KDE_GAUSSIAN)
+    if (o->path == KDE_PATH_CUTOFF && kid_of(a) == KDE_GAUSSIAN)
       return fail(KDE_ENOTSUP, "the cutoff path needs a compact-support kernel");
+    if (o->path == KDE_PATH_SIMT_FP32 && kid_of(a) >= kRadial)
+      return fail(KDE_ENOTSUP, "radial compact kernels run on the cutoff path");
     if (o->split_k < 0 || o->split_k > 1024) return fail(KDE_EINVAL, "split_k out of range");
     if (o->k_chunk < 0 || (o->k_chunk % 32) != 0 || (o->k_chunk > 0 && o->k_chunk < 64))
       return fail(KDE_EINVAL, "k_chunk must be 0 or a multiple of 32 of at least 64");
@@ -136,7 +144,7 @@ int validate(const kde_args* a, const kde_opts* o) {
 int resolve_path(const kde_args* a, const kde_opts* o) {
   int path = o ? o->path : KDE_PATH_AUTO;
   if (path == KDE_PATH_AUTO)
-    path = a->kernel_id == KDE_GAUSSIAN ? KDE_PATH_TC_SPLIT16 : KDE_PATH_CUTOFF;
+    path = kid_of(a) == KDE_GAUSSIAN ? KDE_PATH_TC_SPLIT16 : KDE_PATH_CUTOFF;
   return path;
 }
 
@@ -516,7 +524,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     q.begin = I.prep_begin;
     q.ox = a->origin_x;
     q.oy = a->origin_y;
-    q.sigma = kernel_sigma(a->kernel_id, a->h);
+    q.sigma = kernel_sigma(kid_of(a), a->h);
     q.cell_sigma = a->cell * q.sigma;
     q.nx = a->nx;
     q.ny = a->ny;
@@ -525,8 +533,10 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     return P.in[k].splits > 1 ? reinterpret_cast<float*>(base + P.in[k].off_part) : out_dev[k];
   };
   auto compact_scale = [&](int k) {
-    const double c1 = kernel_const_1d(A[k].kernel_id);
-    return A[k].n > 0 ? (float)(c1 * c1 / ((double)A[k].n * A[k].h * A[k].h)) : 0.0f;
+    const int kid = kid_of(&A[k]);
+    const double c1 = kernel_const_1d(kid);
+    const double c = kid >= kRadial ? kernel_const_radial(kid - kRadial) : c1 * c1;
+    return A[k].n > 0 ? (float)(c / ((double)A[k].n * A[k].h * A[k].h)) : 0.0f;
   };
   int item_begin = 0;
   for (int k : P.tc_order) {
@@ -592,7 +602,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.bin_begin = I.bin_begin;
       q.nx = A[k].nx;
       q.ny = A[k].ny;
-      q.kid = A[k].kernel_id;
+      q.kid = kid_of(&A[k]);
       q.scale = compact_scale(k);
       cut.push_back(q);
     }
@@ -688,7 +698,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   for (int k = 0; k < count; ++k) {
     const InstPlan& I = P.in[k];
     if (I.path != KDE_PATH_SIMT_FP32) continue;
-    KDE_CUDA(launch_simt(A[k].kernel_id, prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
+    KDE_CUDA(launch_simt(kid_of(&A[k]), prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
                          prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k), part_of(k), s),
              "SIMT direct sum");
   }
@@ -804,7 +814,7 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
                       float* grad_weights, double* grad_h, const kde_opts* opts) {
   int rc = validate(a, opts);
   if (rc) return rc;
-  if (a->kernel_id != KDE_GAUSSIAN)
+  if (kid_of(a) != KDE_GAUSSIAN)
     return fail(KDE_ENOTSUP, "the adjoint is implemented for the Gaussian kernel");
   if (!grad_out || (a->n > 0 && !grad_points))
     return fail(KDE_EINVAL, "grad_out and grad_points are required");
@@ -897,7 +907,7 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
   if (!chk.out) chk.out = const_cast<float*>(F);  // out is not used here
   int rc = validate(&chk, opts);
   if (rc) return rc;
-  if (a->kernel_id != KDE_GAUSSIAN)
+  if (kid_of(a) != KDE_GAUSSIAN)
     return fail(KDE_ENOTSUP, "the LSCV loss is implemented for the Gaussian kernel");
   if (!F || !loss) return fail(KDE_EINVAL, "F and loss are required");
   if (memory_kind(F) != 0 || (grad_F && memory_kind(grad_F) != 0) ||
@@ -1025,6 +1035,7 @@ int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t n
   a.out = out;
   int rc = validate(&a, nullptr);
   if (rc) return rc;
+  if (kernel_id > 7) return fail(KDE_EINVAL, "the binned estimator takes the Table 1 kernels (0..7)");
   if (traj_offsets && ntraj < 1) return fail(KDE_EINVAL, "ntraj must be >= 1 with offsets");
   if (ny > 64 * 65535) return fail(KDE_EINVAL, "ny = %d exceeds 4194240 rows", ny);
   if (window < 0 || (window > 0 && ((window & 1) == 0 || window > 255)))
@@ -1060,6 +1071,49 @@ int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t n
     KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
     if (interpolated) *interpolated = (int64_t)hv;
   }
+  g_err[0] = 0;
+  return KDE_OK;
+}
+
+int kde_dp_simplify(const double* points, const int64_t* traj_offsets, int64_t ntraj, int64_t n,
+                    double eps, uint8_t* keep, double* out_points, int64_t* out_offsets,
+                    int64_t* n_kept, int* iterations, const kde_opts* opts) {
+  if (n < 0 || n >= ((int64_t)1 << 31) - 1)
+    return fail(KDE_EINVAL, "n = %lld must be in [0, 2^31 - 1)", (long long)n);
+  if (n > 0 && (!points || !keep)) return fail(KDE_EINVAL, "points or keep is NULL with n > 0");
+  if (!(eps >= 0.0) || !isfinite(eps)) return fail(KDE_EINVAL, "eps must be finite and >= 0");
+  if (traj_offsets && ntraj < 1) return fail(KDE_EINVAL, "ntraj must be >= 1 with offsets");
+  if (out_offsets && !traj_offsets && ntraj != 1)
+    return fail(KDE_EINVAL, "out_offsets without traj_offsets needs ntraj = 1");
+  if (!traj_offsets) ntraj = 1;
+  if ((points && (reinterpret_cast<uintptr_t>(points) & 15)) ||
+      (out_points && (reinterpret_cast<uintptr_t>(out_points) & 15)) ||
+      (traj_offsets && (reinterpret_cast<uintptr_t>(traj_offsets) & 7)) ||
+      (out_offsets && (reinterpret_cast<uintptr_t>(out_offsets) & 7)))
+    return fail(KDE_EINVAL, "points must be 16-byte and offsets 8-byte aligned");
+  const void* dev_ptrs[] = {points, keep, out_points, traj_offsets, out_offsets};
+  for (const void* q : dev_ptrs)
+    if (q && n > 0 && memory_kind(q) != 0)
+      return fail(KDE_EINVAL, "kde_dp_simplify needs device pointers");
+  cudaStream_t s = stream_of(opts);
+  const size_t need = align256(sizeof(CallScalars)) + dp_workspace_bytes(n);
+  void* wsv = nullptr;
+  int rc = acquire_workspace(opts, need, s, &wsv);
+  if (rc) return rc;
+  CallScalars* scal = static_cast<CallScalars*>(wsv);
+  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars), s), "clear scalars");
+  int64_t kept = 0;
+  int its = 0;
+  KDE_CUDA(launch_dp(points, n, traj_offsets, ntraj, eps, keep, out_points, out_offsets,
+                     static_cast<char*>(wsv) + align256(sizeof(CallScalars)), scal, &kept, &its, s),
+           "Douglas-Peucker");
+  CallScalars hs;
+  KDE_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s), "read status");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  if (hs.err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate");
+  if (hs.err & kErrBadArg) return fail(KDE_EINVAL, "traj_offsets must rise from 0 to n");
+  if (n_kept) *n_kept = kept;
+  if (iterations) *iterations = its;
   g_err[0] = 0;
   return KDE_OK;
 }

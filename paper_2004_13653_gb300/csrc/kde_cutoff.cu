@@ -171,8 +171,39 @@ __device__ __forceinline__ float kfactor_rt(int kid, float d) {
   }
 }
 
+// Radial kernels: KX / KY hold squared offsets, the profile is evaluated per
+// pair on q = u^2 + v^2.
+template <int KID>
+__device__ __forceinline__ void radial_batch(const float (*KX)[32], const float (*KY)[32],
+                                             const float* sW, int cnt, int cx, int cy0,
+                                             float (&acc)[4]) {
+  for (int c = 0; c < cnt; ++c) {
+    const float kx = KX[c][cx], w = sW[c];
+    const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
+    acc[0] = fmaf(w, kradial<KID>(kx + ky.x), acc[0]);
+    acc[1] = fmaf(w, kradial<KID>(kx + ky.y), acc[1]);
+    acc[2] = fmaf(w, kradial<KID>(kx + ky.z), acc[2]);
+    acc[3] = fmaf(w, kradial<KID>(kx + ky.w), acc[3]);
+  }
+}
+
+__device__ __forceinline__ void radial_batch_rt(int kid, const float (*KX)[32],
+                                                const float (*KY)[32], const float* sW, int cnt,
+                                                int cx, int cy0, float (&acc)[4]) {
+  switch (kid) {
+    case KDE_UNIFORM: radial_batch<KDE_UNIFORM>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    case KDE_TRIANGULAR: radial_batch<KDE_TRIANGULAR>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    case KDE_EPANECHNIKOV: radial_batch<KDE_EPANECHNIKOV>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    case KDE_QUARTIC: radial_batch<KDE_QUARTIC>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    case KDE_TRIWEIGHT: radial_batch<KDE_TRIWEIGHT>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    case KDE_TRICUBE: radial_batch<KDE_TRICUBE>(KX, KY, sW, cnt, cx, cy0, acc); break;
+    default: radial_batch<KDE_COSINE>(KX, KY, sW, cnt, cx, cy0, acc); break;
+  }
+}
+
 // One CTA per 32x32 output bin of some instance (blockIdx.x = global bin);
-// thread (cx, 4 rows).
+// thread (cx, 4 rows).  Product kernels (kid 0..7) use tabulated factors and
+// outer products; radial kernels (kid 8..15) tabulated squared offsets.
 __global__ void __launch_bounds__(256)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
              const float* __restrict__ W, const uint32_t* __restrict__ start) {
@@ -189,7 +220,9 @@ __global__ void __launch_bounds__(256)
   const CutInst& I = tab[lo];
   const int local = blockIdx.x - I.bin_begin;
   const int bx = local % I.nbx, by = local / I.nbx;
-  const int nx = I.nx, ny = I.ny, R = I.R, kid = I.kid;
+  const int nx = I.nx, ny = I.ny, R = I.R;
+  const bool radial = I.kid >= kRadial;
+  const int kid = radial ? I.kid - kRadial : I.kid;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int t = threadIdx.x;
   const int cx = t & 31, cy0 = (t >> 5) * 4;
@@ -219,19 +252,29 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float2 gx = sgx[ej0 + j], gy = sgy[ej0 + j];
-          KX[ec][ej0 + j] = kfactor_rt(kid, (gx.x - p.x) + (gx.y - p.y));
-          KY[ec][ej0 + j] = w * kfactor_rt(kid, (gy.x - p.z) + (gy.y - p.w));
+          const float u = (gx.x - p.x) + (gx.y - p.y), v = (gy.x - p.z) + (gy.y - p.w);
+          if (radial) {
+            KX[ec][ej0 + j] = u * u;
+            KY[ec][ej0 + j] = v * v;
+          } else {
+            KX[ec][ej0 + j] = kfactor_rt(kid, u);
+            KY[ec][ej0 + j] = w * kfactor_rt(kid, v);
+          }
         }
       }
       __syncthreads();
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int c = 0; c < cnt; ++c) {
-        const float kx = KX[c][cx];
-        const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
-        acc[0] = fmaf(kx, ky.x, acc[0]);
-        acc[1] = fmaf(kx, ky.y, acc[1]);
-        acc[2] = fmaf(kx, ky.z, acc[2]);
-        acc[3] = fmaf(kx, ky.w, acc[3]);
+      if (radial) {
+        radial_batch_rt(kid, KX, KY, sW, cnt, cx, cy0, acc);
+      } else {
+        for (int c = 0; c < cnt; ++c) {
+          const float kx = KX[c][cx];
+          const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
+          acc[0] = fmaf(kx, ky.x, acc[0]);
+          acc[1] = fmaf(kx, ky.y, acc[1]);
+          acc[2] = fmaf(kx, ky.z, acc[2]);
+          acc[3] = fmaf(kx, ky.w, acc[3]);
+        }
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r) two_sum_acc(run[r], acc[r]);

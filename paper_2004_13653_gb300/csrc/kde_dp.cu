@@ -1,0 +1,270 @@
+// Douglas-Peucker compression of the trajectories (Sec. III-B), in the
+// level-synchronous form of Sec. IV-A: every curve segment of every
+// trajectory is processed in the same iteration, so the recursion of the
+// textbook algorithm becomes a loop over tree levels.
+//
+// Each point carries the two ends (s, e) of the segment it lies in, which
+// plays the part of the paper's label set Lp.  One iteration:
+//   1. k_dp_ved    : the VED of every open point to its segment (Eq. 9); the
+//                    largest VED above eps per segment, by a segmented max over
+//                    each warp's lanes and one 64-bit atomicMax per run
+//                    (non-negative doubles order like their bit patterns);
+//   2. k_dp_arg    : the first point attaining that maximum (atomicMin), the
+//                    tie rule of the sequential algorithm;
+//   3. k_dp_split  : that point is kept; the others move their s or e to it
+//                    (the label update of Eq. 11); segments with nothing
+//                    above eps are closed.  The per-segment slots of the next
+//                    iteration (double-buffered) are cleared here.
+// The loop ends when an iteration keeps no point.  The VED is evaluated with
+// explicitly rounded FP64 operations in the order of Eq. 9, so every
+// comparison -- and therefore the kept set -- is identical to a sequential
+// FP64 evaluation.  The kept points are then compacted with the Sec. IV-A
+// exclusive scan.
+#include "kde_internal.cuh"
+
+namespace kde {
+namespace {
+
+constexpr uint8_t kKept = 1, kDone = 2;
+constexpr uint32_t kNoArg = 0xffffffffu;
+
+__device__ __forceinline__ double ved(double px, double py, double sx, double sy, double ex,
+                                      double ey) {
+  const double dx = __dsub_rn(ex, sx), dy = __dsub_rn(ey, sy);
+  const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+  const double vx = __dsub_rn(px, sx), vy = __dsub_rn(py, sy);
+  if (len == 0.0) return __dsqrt_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+  return __ddiv_rn(fabs(__dsub_rn(__dmul_rn(vx, dy), __dmul_rn(vy, dx))), len);
+}
+
+// Trajectory bounds of point p: the last k with off[k] <= p; bounds clamped to
+// [0, n] so that malformed offsets cannot index outside the points.
+__device__ __forceinline__ void traj_bounds(const int64_t* __restrict__ off, int64_t ntraj,
+                                            int64_t n, int64_t p, int64_t& a, int64_t& b) {
+  if (!off) {
+    a = 0;
+    b = n;
+    return;
+  }
+  int64_t lo = 0, hi = ntraj - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  a = min(max(off[lo], (int64_t)0), n);
+  b = min(max(off[lo + 1], a), n);
+}
+
+__global__ void k_dp_init(const double2* __restrict__ xy, int64_t n,
+                          const int64_t* __restrict__ off, int64_t ntraj, int32_t* __restrict__ s,
+                          int32_t* __restrict__ e, uint8_t* __restrict__ flag,
+                          unsigned long long* __restrict__ segmax, uint32_t* __restrict__ segarg,
+                          CallScalars* __restrict__ scal) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    int64_t a, b;
+    traj_bounds(off, ntraj, n, p, a, b);
+    const double2 q = xy[p];
+    bool bad = !(isfinite(q.x) && isfinite(q.y));
+    if (!(a <= p && p < b)) {  // offsets do not cover p: a trajectory of its own
+      bad = true;
+      a = p;
+      b = p + 1;
+    }
+    s[p] = (int32_t)a;
+    e[p] = (int32_t)(b - 1);
+    flag[p] = (p == a || p == b - 1 || bad) ? kKept : 0;
+    segmax[p] = 0ull;
+    segmax[n + p] = 0ull;
+    segarg[p] = kNoArg;
+    segarg[n + p] = kNoArg;
+    if (bad) atomicOr(&scal->err, kErrNonFinite);
+  }
+  if (off && blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[ntraj] != n))
+    atomicOr(&scal->err, kErrBadArg);
+}
+
+// Step 1.  Lanes of a warp hold consecutive points, so equal segment starts
+// form runs of lanes: a shuffle scan takes each run's maximum and its last
+// lane issues the atomic.
+__global__ void k_dp_ved(const double2* __restrict__ xy, int64_t n, double eps,
+                         const int32_t* __restrict__ s, const int32_t* __restrict__ e,
+                         const uint8_t* __restrict__ flag, double* __restrict__ dist,
+                         unsigned long long* __restrict__ segmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t p = base + threadIdx.x;
+    int64_t key = -1 - lane;  // lanes without a candidate never join a run
+    unsigned long long v = 0ull;
+    if (p < n && !(flag[p] & (kKept | kDone))) {
+      const int32_t sp = s[p], ep = e[p];
+      const double2 q = xy[p], a = xy[sp], b = xy[ep];
+      const double d = ved(q.x, q.y, a.x, a.y, b.x, b.y);
+      dist[p] = d;
+      key = sp;
+      if (d > eps) v = (unsigned long long)__double_as_longlong(d);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long vo = __shfl_up_sync(0xffffffffu, v, o);
+      const int64_t ko = __shfl_up_sync(0xffffffffu, key, o);
+      if (lane >= o && ko == key && vo > v) v = vo;
+    }
+    const int64_t knext = __shfl_down_sync(0xffffffffu, key, 1);
+    const bool last = lane == 31 || knext != key;
+    if (last && key >= 0 && v != 0ull) atomicMax(&segmax[key], v);
+  }
+}
+
+// Step 2: the first point of each segment whose VED equals the maximum.
+__global__ void k_dp_arg(int64_t n, const int32_t* __restrict__ s,
+                         const uint8_t* __restrict__ flag, const double* __restrict__ dist,
+                         const unsigned long long* __restrict__ segmax,
+                         uint32_t* __restrict__ segarg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    if (flag[p] & (kKept | kDone)) continue;
+    const int32_t sp = s[p];
+    const unsigned long long m = segmax[sp];
+    if (m != 0ull && (unsigned long long)__double_as_longlong(dist[p]) == m)
+      atomicMin(&segarg[sp], (uint32_t)p);
+  }
+}
+
+// Step 3: keep the split points, move the others' segment ends, close the
+// segments without a split, clear the next iteration's slots.
+__global__ void k_dp_split(int64_t n, int32_t* __restrict__ s, int32_t* __restrict__ e,
+                           uint8_t* __restrict__ flag, const uint32_t* __restrict__ segarg,
+                           unsigned long long* __restrict__ segmax_next,
+                           uint32_t* __restrict__ segarg_next,
+                           unsigned long long* __restrict__ kept_now) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long mine = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const uint8_t f = flag[p];
+    if (f & (kKept | kDone)) continue;
+    int32_t sp = s[p];
+    const uint32_t k = segarg[sp];
+    if (k == kNoArg) {
+      flag[p] = f | kDone;
+      continue;
+    }
+    if ((int64_t)k == p) {
+      flag[p] = kKept;
+      ++mine;
+      continue;
+    }
+    if (p < (int64_t)k) e[p] = (int32_t)k;
+    else s[p] = sp = (int32_t)k;
+    segmax_next[sp] = 0ull;
+    segarg_next[sp] = kNoArg;
+  }
+  if (mine) atomicAdd(kept_now, mine);
+}
+
+__global__ void k_dp_flags(const uint8_t* __restrict__ flag, int64_t n,
+                           uint32_t* __restrict__ kept32, uint8_t* __restrict__ keep) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += stride) {
+    const uint32_t k = p < n ? (flag[p] & kKept) : 0u;
+    kept32[p] = k;
+    if (p < n) keep[p] = (uint8_t)k;
+  }
+}
+
+__global__ void k_dp_compact(const double2* __restrict__ xy, int64_t n,
+                             const uint32_t* __restrict__ kept32, const uint32_t* __restrict__ pos,
+                             double2* __restrict__ out, const int64_t* __restrict__ off,
+                             int64_t ntraj, int64_t* __restrict__ out_off) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    if (out && kept32[p]) out[pos[p]] = xy[p];
+  if (out_off)
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= ntraj; k += stride) {
+      const int64_t o = off ? min(max(off[k], (int64_t)0), n) : (k == 0 ? 0 : n);
+      out_off[k] = pos[o];
+    }
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+}
+
+}  // namespace
+
+size_t dp_workspace_bytes(int64_t n) {
+  const size_t m = (size_t)n + 1;
+  return 256 * 12 + m * (4 + 4 + 1 + 16 + 8 + 8 + 4 + 4) + 4 * (scan_temp_words((int64_t)m, 2048) + 64);
+}
+
+cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t ntraj, double eps,
+                      uint8_t* keep, double* out_xy, int64_t* out_off, void* ws,
+                      CallScalars* scal, int64_t* n_kept, int* iterations, cudaStream_t st) {
+  const size_t m = (size_t)n + 1;
+  char* w = static_cast<char*>(ws);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { char* r = w + o; o = (o + bytes + 255) & ~(size_t)255; return r; };
+  int32_t* s = reinterpret_cast<int32_t*>(take(4 * m));
+  int32_t* e = reinterpret_cast<int32_t*>(take(4 * m));
+  uint8_t* flag = reinterpret_cast<uint8_t*>(take(m));
+  unsigned long long* segmax = reinterpret_cast<unsigned long long*>(take(16 * m));
+  double* dist = reinterpret_cast<double*>(take(8 * m));
+  uint32_t* segarg = reinterpret_cast<uint32_t*>(take(8 * m));
+  uint32_t* kept32 = reinterpret_cast<uint32_t*>(take(4 * m));
+  uint32_t* pos = reinterpret_cast<uint32_t*>(take(4 * m));
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(take(8));
+  uint32_t* scan_temp = reinterpret_cast<uint32_t*>(take(4 * (scan_temp_words((int64_t)m, 2048) + 64)));
+  const double2* P = reinterpret_cast<const double2*>(xy);
+  const int g = grid_for(n);
+  cudaError_t err = cudaSuccess;
+  int it = 0;
+  if (n > 0) {
+    k_dp_init<<<g, 256, 0, st>>>(P, n, off, ntraj, s, e, flag, segmax, segarg, scal);
+    note_launches(1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    unsigned long long kept_now = 0;
+    // every iteration keeps at least one point, so n iterations bound the loop
+    for (; it <= n; ++it) {
+      const int b = it & 1;
+      if ((err = cudaMemsetAsync(counter, 0, 8, st)) != cudaSuccess) break;
+      k_dp_ved<<<g, 256, 0, st>>>(P, n, eps, s, e, flag, dist, segmax + b * n);
+      k_dp_arg<<<g, 256, 0, st>>>(n, s, flag, dist, segmax + b * n, segarg + b * n);
+      k_dp_split<<<g, 256, 0, st>>>(n, s, e, flag, segarg + b * n, segmax + (b ^ 1) * n,
+                                    segarg + (b ^ 1) * n, counter);
+      note_launches(3);
+      if ((err = cudaGetLastError()) != cudaSuccess) break;
+      if ((err = cudaMemcpyAsync(&kept_now, counter, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        break;
+      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      if (kept_now == 0) {
+        ++it;
+        break;
+      }
+    }
+    if (err != cudaSuccess) return err;
+  }
+  if (iterations) *iterations = it;
+  k_dp_flags<<<grid_for(n + 1), 256, 0, st>>>(flag, n, kept32, keep);
+  note_launches(1);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if ((err = launch_exclusive_scan(kept32, pos, (int64_t)m, 2048, scan_temp, st)) != cudaSuccess)
+    return err;
+  if (out_xy || out_off) {
+    k_dp_compact<<<grid_for(std::max<int64_t>(n, ntraj + 1)), 256, 0, st>>>(
+        P, n, kept32, pos, reinterpret_cast<double2*>(out_xy), off, ntraj, out_off);
+    note_launches(1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  if (n_kept) {
+    uint32_t total = 0;
+    if ((err = cudaMemcpyAsync(&total, pos + n, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return err;
+    if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+    *n_kept = total;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace kde

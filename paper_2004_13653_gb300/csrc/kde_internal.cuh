@@ -47,6 +47,24 @@ __host__ __device__ inline double kernel_const_1d(int kid) {
   return 0.0;
 }
 
+// Kernel ids 8..15: radial variants K(u) = c k(|u|) of the Table 1 kernels
+// on the unit disk; c makes K integrate to one over the plane.
+constexpr int kRadial = 8;
+__host__ __device__ inline double kernel_const_radial(int kid) {
+  constexpr double pi = 3.14159265358979323846;
+  switch (kid) {
+    case KDE_UNIFORM: return 1.0 / pi;                 // int_0^1 r dr = 1/2
+    case KDE_TRIANGULAR: return 3.0 / pi;              // int r (1-r) = 1/6
+    case KDE_EPANECHNIKOV: return 2.0 / pi;            // int r (1-r^2) = 1/4
+    case KDE_QUARTIC: return 3.0 / pi;                 // int r (1-r^2)^2 = 1/6
+    case KDE_TRIWEIGHT: return 4.0 / pi;               // int r (1-r^2)^3 = 1/8
+    case KDE_TRICUBE: return 220.0 / (81.0 * pi);      // int r (1-r^3)^3 = 81/440
+    case KDE_GAUSSIAN: return 1.0 / (2.0 * pi);
+    case KDE_COSINE: return pi / (4.0 * pi - 8.0);     // int r cos(pi r/2) = 2/pi - 4/pi^2
+  }
+  return 0.0;
+}
+
 // Coordinate scale sigma for a kernel and bandwidth.
 inline double kernel_sigma(int kid, double h) {
   // Gaussian: exp(-s^2/2) = 2^(-u^2) with u = s / sqrt(2 ln 2)
@@ -227,6 +245,13 @@ cudaError_t launch_binned(const double* xy, int64_t n, const int64_t* off, int64
                           double ox, double oy, double cell, int nx, int ny, double h, int kid,
                           int window, int interpolate, int* counts, float* rowbuf,
                           unsigned long long* added, float* out, cudaStream_t s);
+
+// Douglas-Peucker compression of every trajectory (level-synchronous;
+// synchronous on `s`).  ws: dp_workspace_bytes(n) bytes.
+size_t dp_workspace_bytes(int64_t n);
+cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t ntraj, double eps,
+                      uint8_t* keep, double* out_xy, int64_t* out_off, void* ws,
+                      CallScalars* scal, int64_t* n_kept, int* iterations, cudaStream_t s);
 
 // Path (b): Gaussian as a tcgen05 contraction.
 struct TcPlan {

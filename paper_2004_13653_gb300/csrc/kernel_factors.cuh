@@ -59,6 +59,31 @@ __device__ __forceinline__ float kfactor(float d) {
   }
 }
 
+// The radial variant of a Table 1 kernel (kernel id 8 + KID) as a function of
+// q = |u|^2 (offsets in bandwidths), without its constant: the Table 1 profile
+// of r = sqrt(q) on the unit disk.
+template <int KID>
+__device__ __forceinline__ float kradial(float q) {
+  if constexpr (KID == KDE_UNIFORM) {
+    return q <= 1.0f ? 1.0f : 0.0f;
+  } else if constexpr (KID == KDE_TRIANGULAR) {
+    return fmaxf(1.0f - sqrtf(q), 0.0f);
+  } else if constexpr (KID == KDE_EPANECHNIKOV) {
+    return fmaxf(1.0f - q, 0.0f);
+  } else if constexpr (KID == KDE_QUARTIC) {
+    const float t = fmaxf(1.0f - q, 0.0f);
+    return t * t;
+  } else if constexpr (KID == KDE_TRIWEIGHT) {
+    const float t = fmaxf(1.0f - q, 0.0f);
+    return t * t * t;
+  } else if constexpr (KID == KDE_TRICUBE) {
+    const float t = fmaxf(fmaf(-q, sqrtf(q), 1.0f), 0.0f);
+    return t * t * t;
+  } else {  // KDE_COSINE: cos(pi/2 r), Taylor series in r^2 = q
+    return q <= 1.0f ? fmaxf(cos_half_pi(sqrtf(q)), 0.0f) : 0.0f;
+  }
+}
+
 __device__ __forceinline__ void two_sum_acc(float2& run, float v) {
   const float s = run.x + v;
   const float bb = s - run.x;

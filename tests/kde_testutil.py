@@ -36,3 +36,30 @@ def sample_cells(F_gpu, count=256, seed=0, neighbourhood=8):
     while len(cells) < count:
         cells.add(int(rng.integers(0, nx * ny)))
     return np.array(sorted(cells), dtype=np.int64)
+
+
+def clear_of_support_edge(wl, radial, margin=1e-5):
+    """The uniform kernel jumps at the edge of its support, and the GPU takes
+    that decision in FP32 while the oracle takes it in FP64: a pair within
+    rounding of the edge may count on one side only.  Returns the workload
+    without the points that have a cell centre within `margin` (relative) of
+    the edge (|s| = 1 or |t| = 1; |u| = 1 for the radial kernel)."""
+    import dataclasses
+    ox, oy = wl.origin
+    x = wl.xy[:, 0]
+    y = wl.xy[:, 1]
+    i0 = np.floor((x - ox) / wl.cell - wl.h / wl.cell - 1).astype(np.int64)
+    j0 = np.floor((y - oy) / wl.cell - wl.h / wl.cell - 1).astype(np.int64)
+    span = int(np.ceil(2 * wl.h / wl.cell)) + 3
+    di = np.arange(span)
+    s = (ox + (i0[:, None] + di[None, :] + 0.5) * wl.cell - x[:, None]) / wl.h
+    t = (oy + (j0[:, None] + di[None, :] + 0.5) * wl.cell - y[:, None]) / wl.h
+    if radial:
+        r = np.sqrt(s[:, :, None] ** 2 + t[:, None, :] ** 2)
+        bad = np.any(np.abs(r - 1.0) < margin, axis=(1, 2))
+    else:
+        bad = np.any(np.abs(np.abs(s) - 1.0) < margin, axis=1) | \
+            np.any(np.abs(np.abs(t) - 1.0) < margin, axis=1)
+    keep = ~bad
+    return dataclasses.replace(wl, local=wl.local[keep], w=wl.w[keep],
+                               offsets=np.array([0, int(keep.sum())], dtype=np.int64))

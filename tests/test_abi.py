@@ -71,7 +71,7 @@ BAD = [
     ("inf h", dict(h=float("inf"), out=8)),
     ("zero cell", dict(cell=0.0, out=8)),
     ("nan origin", dict(origin_x=float("nan"), out=8)),
-    ("kernel id", dict(kernel_id=8, out=8)),
+    ("kernel id", dict(kernel_id=16, out=8)),
     ("negative kernel id", dict(kernel_id=-1, out=8)),
 ]
 

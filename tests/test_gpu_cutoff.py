@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads
-from kde_testutil import TOL_FP32, rel_linf, sample_cells
+from kde_testutil import TOL_FP32, clear_of_support_edge, rel_linf, sample_cells
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -35,6 +35,8 @@ def test_all_compact_kernels_ragged(kid):
     """Ragged 32x32 bins on both axes, weights U(0.5, 2), points partly
     outside the grid (some beyond reach, some within a bandwidth)."""
     wl = workloads.random_points(500 + kid, 2500, 3000.0, 10.0, 300, 150, 35.0, kid)
+    if kid == oracle.UNIFORM:
+        wl = clear_of_support_edge(wl, radial=False)
     F = run_gpu(wl, kid)
     ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
     assert rel_linf(F, ref) <= TOL_FP32
@@ -80,3 +82,40 @@ def test_single_point_and_auto_path():
     F = run_gpu(wl, oracle.TRIWEIGHT, path="auto")
     ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.TRIWEIGHT)
     assert rel_linf(F, ref) <= TOL_FP32
+
+
+RADIAL_COMPACT = [oracle.RADIAL + k for k in COMPACT]
+
+
+@pytest.mark.parametrize("kid", RADIAL_COMPACT,
+                         ids=["radial_" + oracle.KERNEL_NAMES[k - oracle.RADIAL]
+                              for k in RADIAL_COMPACT])
+def test_radial_kernels_ragged(kid):
+    """Radial variants on the disk (cutoff path, AUTO): ragged bins, weights,
+    points partly outside the grid."""
+    wl = workloads.random_points(530 + kid, 2500, 3000.0, 10.0, 300, 150, 35.0, kid)
+    if kid == oracle.RADIAL + oracle.UNIFORM:
+        wl = clear_of_support_edge(wl, radial=True)
+    F = run_gpu(wl, kid, path="auto")
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+def test_radial_wide_bandwidth_sampled():
+    """1M lane points on 1024^2, h = 150 m (3 cells), radial Epanechnikov,
+    sampled cells."""
+    kid = oracle.RADIAL + oracle.EPANECHNIKOV
+    wl = workloads.config2(kernel=kid)
+    F = run_gpu(wl, kid)
+    cells = sample_cells(F, 256, seed=23)
+    ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
+    assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
+
+
+def test_radial_gaussian_is_the_gaussian_and_simt_rejects_radial():
+    wl = workloads.config1()
+    a = run_gpu(wl, oracle.GAUSSIAN, path="tc_split16")
+    b = run_gpu(wl, oracle.RADIAL + oracle.GAUSSIAN, path="tc_split16")
+    np.testing.assert_array_equal(a, b)
+    with pytest.raises(RuntimeError):
+        run_gpu(wl, oracle.RADIAL + oracle.EPANECHNIKOV, path="simt")
