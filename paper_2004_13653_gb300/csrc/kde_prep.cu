@@ -18,18 +18,101 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kWgs84A = 6378137.0;
 constexpr double kWgs84E2 = 0.00669437999014;
 
-// Eq. 1-4: x = lambda r0, y = q r0 with the isometric latitude q.
-__global__ void k_mercator(const double* __restrict__ lonlat, int64_t n, double r0, double e,
-                           double* __restrict__ xy) {
+// Eq. 1-4: x = lambda r0, y = q r0 with the isometric latitude q.  Near the
+// standard latitude phi0 (|phi - phi0| <= m.range) y comes from the
+// Taylor series of q about phi0: the constant, linear and quadratic terms in
+// FP64, the terms of order 3..7 (a few metres at most) in FP32.  Elsewhere the
+// closed form is evaluated in FP64.  GB300's FP64 rate makes the closed form
+// (two logarithms, a tangent and a sine per point) the slow part.
+struct MercSeries {
+  double r0, kx, phi0, y0, c1, c2;  // kx = r0 pi/180; y0 = r0 q(phi0); c_k = r0 q^(k)(phi0)/k!
+  double range;                     // |phi - phi0| up to which the series is used
+  float c[5];                       // c3 .. c7
+};
+
+__global__ void k_mercator(const double* __restrict__ lonlat, int64_t n, double e,
+                           const __grid_constant__ MercSeries m, double* __restrict__ xy) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const double2 ll = reinterpret_cast<const double2*>(lonlat)[p];
-    const double lam = ll.x * (kPi / 180.0);
     const double phi = ll.y * (kPi / 180.0);
-    const double es = e * sin(phi);
-    const double q = log(tan(0.25 * kPi + 0.5 * phi)) + 0.5 * e * log((1.0 - es) / (1.0 + es));
-    reinterpret_cast<double2*>(xy)[p] = make_double2(lam * r0, q * r0);
+    const double d = phi - m.phi0;
+    double y;
+    if (fabs(d) <= m.range) {
+      const float df = (float)d;
+      float t = m.c[4];
+      t = fmaf(t, df, m.c[3]);
+      t = fmaf(t, df, m.c[2]);
+      t = fmaf(t, df, m.c[1]);
+      t = fmaf(t, df, m.c[0]);
+      y = fma(m.c2, d * d, fma(m.c1, d, m.y0)) + (double)(t * (df * df * df));
+    } else {
+      const double es = e * sin(phi);
+      const double q = log(tan(0.25 * kPi + 0.5 * phi)) + 0.5 * e * log((1.0 - es) / (1.0 + es));
+      y = q * m.r0;
+    }
+    reinterpret_cast<double2*>(xy)[p] = make_double2(ll.x * m.kx, y);
   }
+}
+
+// Truncated power series in d (order kOrd) on the host.
+constexpr int kOrd = 8;
+struct Series {
+  double a[kOrd + 1];
+};
+Series series_mul(const Series& x, const Series& y) {
+  Series r = {};
+  for (int i = 0; i <= kOrd; ++i)
+    for (int j = 0; i + j <= kOrd; ++j) r.a[i + j] += x.a[i] * y.a[j];
+  return r;
+}
+Series series_recip(const Series& x) {  // x.a[0] != 0
+  Series r = {};
+  r.a[0] = 1.0 / x.a[0];
+  for (int k = 1; k <= kOrd; ++k) {
+    double s = 0.0;
+    for (int j = 1; j <= k; ++j) s += x.a[j] * r.a[k - j];
+    r.a[k] = -s / x.a[0];
+  }
+  return r;
+}
+
+// Taylor coefficients of q(phi0 + d) - q(phi0) from
+// q'(phi) = (1 - e^2) / ((1 - e^2 sin^2 phi) cos phi), integrated term by term.
+MercSeries mercator_series(double phi0, double r0, double e2) {
+  Series sd = {}, cd = {};  // sin d, cos d
+  double f = 1.0;
+  for (int k = 0; k <= kOrd; ++k) {
+    if (k > 0) f /= k;
+    const double v = f * ((k / 2) % 2 ? -1.0 : 1.0);
+    if (k % 2) sd.a[k] = v; else cd.a[k] = v;
+  }
+  Series sn = {}, cs = {};  // sin(phi0 + d), cos(phi0 + d)
+  for (int k = 0; k <= kOrd; ++k) {
+    sn.a[k] = sin(phi0) * cd.a[k] + cos(phi0) * sd.a[k];
+    cs.a[k] = cos(phi0) * cd.a[k] - sin(phi0) * sd.a[k];
+  }
+  Series den = series_mul(sn, sn);
+  for (int k = 0; k <= kOrd; ++k) den.a[k] = (k == 0 ? 1.0 : 0.0) - e2 * den.a[k];
+  den = series_mul(den, cs);
+  const Series qp = series_recip(den);  // q'/(1 - e^2)
+  MercSeries m;
+  const double e = sqrt(e2);
+  const double s0 = sin(phi0);
+  m.r0 = r0;
+  m.kx = r0 * (kPi / 180.0);
+  m.phi0 = phi0;
+  m.y0 = r0 * (log(tan(0.25 * kPi + 0.5 * phi0)) + 0.5 * e * log((1.0 - e * s0) / (1.0 + e * s0)));
+  m.c1 = r0 * (1.0 - e2) * qp.a[0];
+  m.c2 = r0 * (1.0 - e2) * qp.a[1] / 2.0;
+  for (int k = 3; k <= 7; ++k) m.c[k - 3] = (float)(r0 * (1.0 - e2) * qp.a[k - 1] / k);
+  // range: the FP32 rounding of the order-3 term plus the first omitted term
+  // stay below 2e-7 m (at most 0.01 rad, ~64 km of latitude)
+  const double c3 = fabs(r0 * (1.0 - e2) * qp.a[2] / 3), c8 = fabs(r0 * (1.0 - e2) * qp.a[7] / 8);
+  m.range = 0.01;
+  while (m.range > 1e-4 && c3 * pow(m.range, 3) * 1.2e-7 + c8 * pow(m.range, 8) > 2e-7)
+    m.range *= 0.9;
+  return m;
 }
 
 __device__ __forceinline__ float2 split_hi_lo(double v) {
@@ -120,7 +203,8 @@ cudaError_t launch_mercator(const double* lonlat, int64_t n, double lat0_deg, do
   if (n <= 0) return cudaSuccess;
   const double phi0 = lat0_deg * (kPi / 180.0);
   const double r0 = kWgs84A * cos(phi0) / sqrt(1.0 - kWgs84E2 * sin(phi0) * sin(phi0));
-  k_mercator<<<blocks_for(n, 256), 256, 0, s>>>(lonlat, n, r0, sqrt(kWgs84E2), xy);
+  const MercSeries m = mercator_series(phi0, r0, kWgs84E2);
+  k_mercator<<<blocks_for(n, 256), 256, 0, s>>>(lonlat, n, sqrt(kWgs84E2), m, xy);
   note_launches(1);
   return cudaGetLastError();
 }

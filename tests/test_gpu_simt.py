@@ -120,6 +120,22 @@ def test_mercator_matches_oracle():
     np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("lat0", [-45.0, 0.0, 31.35, 60.0, 80.0])
+def test_mercator_series_and_closed_form(lat0):
+    """Latitudes within and beyond the range where the projection uses its
+    series about lat0 (the rest take the closed form), both hemispheres, high
+    latitude; 1e-6 m of the oracle everywhere."""
+    rng = np.random.default_rng(int(lat0 * 10) + 1000)
+    lat = lat0 + np.concatenate([rng.uniform(-0.5, 0.5, 4000), rng.uniform(-3.0, 3.0, 1000),
+                                 [0.0, 0.57, -0.57]])
+    lat = np.clip(lat, -85.0, 85.0)
+    ll = np.stack([rng.uniform(-180.0, 180.0, lat.size), lat], axis=1)
+    got = kde.project_mercator(_dev(ll, torch.float64), lat0)
+    torch.cuda.synchronize()
+    ref = oracle.mercator(ll, lat0)
+    np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=1e-6)
+
+
 def test_lonlat_pipeline_matches_oracle():
     """Project on the GPU, then the density; the oracle projects on its own."""
     wl = workloads.config1()
