@@ -40,7 +40,7 @@ constexpr int kGroup = 4;   // stages the loader fetches at once
 
 enum Role : int { kRoleMma = 11, kRoleLoader = 12, kRoleEpilogue = 13, kRoleProducer = 14 };
 
-template <bool SPLIT>
+template <bool SPLIT, bool SPARSE>
 struct PairCfg {
   static constexpr int kRowBytes = 2 * kKS;
   static constexpr int kABytes = kRows * kRowBytes;
@@ -48,7 +48,12 @@ struct PairCfg {
   static constexpr int kParts = SPLIT ? 2 : 1;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kStages = (192 * 1024) / kStageBytes;
-  static constexpr int kProducers = 2 * kRows;
+  // producer threads per operand row, each taking 64 / kPerRow points of a
+  // stage: two give the dense kernel more warps to hide the exponentials'
+  // latency (16 producer warps, 832 threads, <= 72 registers); the sparse
+  // kernel, whose loader walks bin runs, keeps one (576 threads)
+  static constexpr int kPerRow = SPARSE ? 1 : 2;
+  static constexpr int kProducers = 2 * kRows * kPerRow;
   static constexpr int kProducerWarps = kProducers / 32;
   static constexpr int kEpiWarps = 8;
   static constexpr int kFirstProducerWarp = 2 + kEpiWarps;
@@ -168,10 +173,10 @@ struct RunCursor {
 };
 
 template <bool SPLIT, bool SPARSE>
-__global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
+__global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
     k_tc_pair(const TcInst* __restrict__ tab, int ninst, int n_items_arg,
               const __grid_constant__ SparseCtl sp, CallScalars* __restrict__ scal) {
-  using C = PairCfg<SPLIT>;
+  using C = PairCfg<SPLIT, SPARSE>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* params = reinterpret_cast<float*>(smem + C::kOffParams);
@@ -359,28 +364,28 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
         const uint32_t acc_col = tmem_base + lane_off + colh * 128;
         const uint32_t run_col = acc_col + 256;
 #pragma unroll 1
-        for (int cb = 0; cb < 4; ++cb) {
-          float a[32];
-          tmem_ld32(acc_col + cb * 32, a);
+        for (int cb = 0; cb < 8; ++cb) {
+          float a[16];
+          tmem_ld16(acc_col + cb * 16, a);
           if (!first) {
-            float r[32];
-            tmem_ld32(run_col + cb * 32, r);
+            float r[16];
+            tmem_ld16(run_col + cb * 16, r);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) a[c] += r[c];
+            for (int c = 0; c < 16; ++c) a[c] += r[c];
           }
           if (final && SPARSE) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) piece[(cb * 32 + c) * 256] = a[c] * scale;
+            for (int c = 0; c < 16; ++c) piece[(cb * 16 + c) * 256] = a[c] * scale;
           } else if (final) {
             if (i < nx) {
 #pragma unroll
-              for (int c = 0; c < 32; ++c) {
-                const int j = j0 + cb * 32 + c;
+              for (int c = 0; c < 16; ++c) {
+                const int j = j0 + cb * 16 + c;
                 if (j < ny) slot[(int64_t)j * nx + i] = a[c] * scale;
               }
             }
           } else {
-            tmem_st32(run_col + cb * 32, a);
+            tmem_st16(run_col + cb * 16, a);
           }
         }
         if (!final) tmem_wait_st();
@@ -393,8 +398,10 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
   } else {
     // ------------------------------------------------------------ producers
     const int t = threadIdx.x - C::kFirstProducerWarp * 32;
-    const bool isA = t < kRows;  // warp-uniform
-    const int r = isA ? t : t - kRows;
+    const bool isA = t < kRows * C::kPerRow;  // warp-uniform
+    const int tl = isA ? t : t - kRows * C::kPerRow;
+    const int r = tl % kRows;
+    const int chunk0 = (tl / kRows) * (8 / C::kPerRow);  // first 8-point chunk of this thread
     const int lo_off = isA ? C::kABytes : C::kBBytes;
     uint32_t full_leader[C::kStages];
 #pragma unroll
@@ -426,8 +433,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
             smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
         const float4* crd = reinterpret_cast<const float4*>(params + ps * 3 * kKS + (isA ? 0 : kKS));
         const float4* cbv = reinterpret_cast<const float4*>(params + ps * 3 * kKS + 2 * kKS);
-#pragma unroll 4
-        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+        for (int c = chunk0; c < chunk0 + 8 / C::kPerRow; ++c) {
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
           float4 c0 = make_float4(15.f, 15.f, 15.f, 15.f), c1 = c0;
           if (!isA) {
@@ -462,9 +469,10 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
           if (SPLIT)
             *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        // each writer orders its stores before async-proxy reads by either
-        // CTA, then the warp signals the leader's stage barrier once
-        fence_proxy_async_all();
+        // each writer orders its stores to this CTA's shared memory before
+        // the tensor core's (async-proxy) reads of it, then the warp signals
+        // the leader's stage barrier once
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive_cluster(full_leader[s]);
@@ -488,7 +496,7 @@ __global__ void __launch_bounds__(PairCfg<SPLIT>::kThreads, 1)
 template <bool SPLIT, bool SPARSE>
 cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
                         const SparseCtl& sp, CallScalars* err, cudaStream_t s) {
-  using C = PairCfg<SPLIT>;
+  using C = PairCfg<SPLIT, SPARSE>;
   cudaError_t e = cudaFuncSetAttribute(k_tc_pair<SPLIT, SPARSE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
