@@ -36,8 +36,8 @@ METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at
 # sources hash to the value they had when the counters were taken.
 TRAFFIC = {("tc_split16", 4096, 40_000): {
     "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh"],
-    "sha256": "fe6109350aa4bd1094d46d4ef849ebbafc048c5bc3abd94b03b02734608d09ff",
-    "bytes": 1248635136 + 531412480}}
+    "sha256": "b83b23efe5f8ecfca0953122c08ac53829b80d8c425afba1eeac1eac643f97d7",
+    "bytes": 1234056448 + 531219712}}
 
 
 def sparse_products(xy, origin, cell, nx, ny, h):
@@ -452,6 +452,18 @@ def extra_workloads(dev):
         "points": int(raw.n), "kept": int(idx.size), "iterations": its, "ms": dp_ms,
         "Mpoint_per_s": raw.n / dp_ms / 1e3}
     w0 = torch.as_tensor(rep, device=dev)
+    # one forward, one adjoint (dL/dpoints, dL/dw, dL/dh for a random cotangent)
+    # and one grid-LSCV evaluation on the thinned fixes, h = 150 m
+    G = torch.rand((raw.ny, raw.nx), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    args5 = (thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0)
+    fwd_ms = _time(lambda: kde.grid(*args5, "gaussian"), reps=5)
+    bwd_ms = _time(lambda: kde.grid_backward(*args5, G), reps=5)
+    F5 = kde.grid(*args5, "gaussian")
+    lscv_ms = _time(lambda: kde.lscv_grid(F5, *args5), reps=5)
+    out["forward_adjoint_lscv_1024sq"] = {
+        "points": int(thin.shape[0]), "forward_ms": fwd_ms, "adjoint_ms": bwd_ms,
+        "lscv_ms": lscv_ms,
+        "note": "adjoint: one warp per point over its +-8h window (dL/dw, dL/dpoints, dL/dh)"}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h, _, losses = kag.fit_bandwidth(thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,

@@ -49,10 +49,9 @@ struct PairCfg {
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kStages = (192 * 1024) / kStageBytes;
   // producer threads per operand row, each taking 64 / kPerRow points of a
-  // stage: two give the dense kernel more warps to hide the exponentials'
-  // latency (16 producer warps, 832 threads, <= 72 registers); the sparse
-  // kernel, whose loader walks bin runs, keeps one (576 threads)
-  static constexpr int kPerRow = SPARSE ? 1 : 2;
+  // stage (one: 576 threads, which leaves the epilogue the registers for
+  // 32-column drain slices)
+  static constexpr int kPerRow = 1;
   static constexpr int kProducers = 2 * kRows * kPerRow;
   static constexpr int kProducerWarps = kProducers / 32;
   static constexpr int kEpiWarps = 8;
@@ -363,35 +362,44 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
         tc_fence_after();
         const uint32_t acc_col = tmem_base + lane_off + colh * 128;
         const uint32_t run_col = acc_col + 256;
+        // 32-column slices, the accumulator and running-sum loads in flight
+        // together; the accumulator is released as soon as its last slice is
+        // in registers (the MMAs never touch the running sum's columns)
 #pragma unroll 1
-        for (int cb = 0; cb < 8; ++cb) {
-          float a[16];
-          tmem_ld16(acc_col + cb * 16, a);
-          if (!first) {
-            float r[16];
-            tmem_ld16(run_col + cb * 16, r);
+        for (int cb = 0; cb < 4; ++cb) {
+          uint32_t ra[32], rr[32];
+          tmem_ld32_async(acc_col + cb * 32, ra);
+          if (!first) tmem_ld32_async(run_col + cb * 32, rr);
+          tmem_wait_ld();
+          if (cb == 3) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(accempty_leader);
+          }
+          float a[32];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) a[c] += r[c];
+          for (int c = 0; c < 32; ++c) a[c] = __uint_as_float(ra[c]);
+          if (!first) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) a[c] += __uint_as_float(rr[c]);
           }
           if (final && SPARSE) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) piece[(cb * 16 + c) * 256] = a[c] * scale;
+            for (int c = 0; c < 32; ++c) piece[(cb * 32 + c) * 256] = a[c] * scale;
           } else if (final) {
             if (i < nx) {
 #pragma unroll
-              for (int c = 0; c < 16; ++c) {
-                const int j = j0 + cb * 16 + c;
+              for (int c = 0; c < 32; ++c) {
+                const int j = j0 + cb * 32 + c;
                 if (j < ny) slot[(int64_t)j * nx + i] = a[c] * scale;
               }
             }
           } else {
-            tmem_st16(run_col + cb * 16, a);
+            tmem_st32(run_col + cb * 32, a);
           }
         }
+        // the running sum's stores complete before this thread's next loads
         if (!final) tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(accempty_leader);
       }
     }
     if (!ok && lane == 0) propagate_abort();
