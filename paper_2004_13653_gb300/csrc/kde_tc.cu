@@ -335,15 +335,24 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
         tc_fence_after();
         const uint32_t acc_col = tmem_base + lane_off + h * HN;
         const uint32_t run_col = tmem_base + lane_off + BN + h * HN;
+        // 32-column slices, both loads in flight together; the half is
+        // released to the MMA as soon as its last slice is in registers
 #pragma unroll 1
         for (int cb = 0; cb < HN / 32; ++cb) {
+          uint32_t ra[32], rr[32];
+          tmem_ld32_async(acc_col + cb * 32, ra);
+          if (!first) tmem_ld32_async(run_col + cb * 32, rr);
+          tmem_wait_ld();
+          if (cb == HN / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&accempty[h]);
+          }
           float a[32];
-          tmem_ld32(acc_col + cb * 32, a);
-          if (!first) {
-            float r[32];
-            tmem_ld32(run_col + cb * 32, r);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) a[c] += r[c];
+          for (int c = 0; c < 32; ++c) a[c] = __uint_as_float(ra[c]);
+          if (!first) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) a[c] += __uint_as_float(rr[c]);
           }
           if (final) {
             if (i < nx) {
@@ -357,9 +366,8 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
             tmem_st32(run_col + cb * 32, a);
           }
         }
+        // the running sum's stores complete before this thread's next loads
         if (!final) tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(&accempty[h]);
         if (h) {
           if (final) done1 = true; else { cs1 = eh + 1; first1 = false; }
         } else {
