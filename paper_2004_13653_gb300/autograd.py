@@ -98,7 +98,9 @@ def fit_bandwidth(points, weights0, origin, cell, nx, ny, h0, steps=200, lr=0.05
         start, losses = int(st["step"]), list(st["losses"])
     for step in range(start, steps):
         opt.zero_grad(set_to_none=True)
-        w = (n * torch.softmax(omega, dim=0)).to(torch.float32)
+        # the logits stay FP64 for Adam; the softmax runs in FP32 (the weights
+        # are FP32 for the kernels anyway)
+        w = n * torch.softmax(omega.to(torch.float32), dim=0)
         L = lscv_loss(points, w, torch.exp(log_h), origin, cell, nx, ny, path)
         L.backward()
         opt.step()
@@ -110,5 +112,5 @@ def fit_bandwidth(points, weights0, origin, cell, nx, ny, h0, steps=200, lr=0.05
             torch.save({"log_h": log_h.detach(), "omega": omega.detach(),
                         "opt": opt.state_dict(), "step": step + 1, "losses": losses}, tmp)
             os.replace(tmp, checkpoint)
-    w = (n * torch.softmax(omega.detach(), dim=0)).to(torch.float32)
+    w = n * torch.softmax(omega.detach().to(torch.float32), dim=0)
     return float(torch.exp(log_h.detach())), w, losses

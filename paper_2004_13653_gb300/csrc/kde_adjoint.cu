@@ -22,10 +22,12 @@ namespace kde {
 namespace {
 
 constexpr float kLog2e = 1.44269504088896340736f;
-constexpr int kColsPerLane = 8;  // window columns a lane keeps in registers per block
 
 __device__ __forceinline__ float gauss(float s) { return ex2_approx(-0.5f * kLog2e * s * s); }
 
+// COLS: window columns a lane keeps in registers per block of 32 * COLS
+// columns (the host picks the smallest power of two that covers the window).
+template <int COLS>
 __global__ void __launch_bounds__(256)
     k_adjoint_gauss(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n,
                     const float* __restrict__ G, const float2* __restrict__ gxt,
@@ -45,26 +47,28 @@ __global__ void __launch_bounds__(256)
     const int j0 = max(jc - R, 0), j1 = min(jc + R, ny - 1);
     float aw = 0.f, ax = 0.f, ay = 0.f, ah = 0.f;
     if (i0 <= i1 && j0 <= j1) {
-      for (int ib = i0; ib <= i1; ib += 32 * kColsPerLane) {
-        float A[kColsPerLane], S[kColsPerLane];
-        int col[kColsPerLane];
+      for (int ib = i0; ib <= i1; ib += 32 * COLS) {
+        float A[COLS], S[COLS];
+        int col[COLS];
 #pragma unroll
-        for (int k = 0; k < kColsPerLane; ++k) {
+        for (int k = 0; k < COLS; ++k) {
           const int i = ib + lane + 32 * k;
           col[k] = i <= i1 ? i : -1;
           const float2 g = gxt[min(i, nx - 1)];
           S[k] = (g.x - P.x) + (g.y - P.y);
           A[k] = col[k] >= 0 ? gauss(S[k]) : 0.f;
         }
+        // rows in order, four per iteration so their loads are in flight together
+#pragma unroll 4
         for (int j = j0; j <= j1; ++j) {
           const float2 g = gyt[j];
           const float t = (g.x - P.z) + (g.y - P.w);
           const float B = gauss(t);
           const float* Grow = G + (int64_t)j * nx;
 #pragma unroll
-          for (int k = 0; k < kColsPerLane; ++k) {
-            if (col[k] < 0) continue;
-            const float q = Grow[col[k]] * B * A[k];
+          for (int k = 0; k < COLS; ++k) {
+            const float Gv = col[k] >= 0 ? __ldg(Grow + col[k]) : 0.f;
+            const float q = Gv * B * A[k];
             aw += q;
             ax = fmaf(S[k], q, ax);
             ay = fmaf(t, q, ay);
@@ -217,9 +221,16 @@ cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n,
   if (n <= 0) return cudaSuccess;
   const int R = (int)ceil(8.0 * h / cell) + 1;
   const float c = (float)(1.0 / (2.0 * 3.14159265358979323846 * (double)n * h * h));
-  k_adjoint_gauss<<<grid_blocks(n * 32, 256, 152 * 64), 256, 0, s>>>(
-      pts, wts, n, G, gxt, gyt, nx, ny, cell / h, R, c, (float)(1.0 / h), grad_xy, grad_w, hterm,
-      lterm);
+  const int width = 2 * R + 1;
+  const int blocks = grid_blocks(n * 32, 256, 152 * 64);
+#define KDE_ADJ(C)                                                                          \
+  k_adjoint_gauss<C><<<blocks, 256, 0, s>>>(pts, wts, n, G, gxt, gyt, nx, ny, cell / h, R, c, \
+                                            (float)(1.0 / h), grad_xy, grad_w, hterm, lterm)
+  if (width <= 32) KDE_ADJ(1);
+  else if (width <= 64) KDE_ADJ(2);
+  else if (width <= 128) KDE_ADJ(4);
+  else KDE_ADJ(8);
+#undef KDE_ADJ
   note_launches(1);
   return cudaGetLastError();
 }

@@ -1,95 +1,102 @@
 // Path (a): FP32 direct sum on the CUDA cores, any Table 1 kernel.
 //
-// Every Table 1 kernel is a product f(s,t) = k(s) k(t) (Sec. III-C), so a
-// thread that owns an 8x8 block of cells evaluates 8 x-factors and 8
-// y-factors per point and accumulates their outer product: 16 kernel
-// evaluations and 64 FMAs per point instead of 64 evaluations.  Points are
-// staged in shared memory in tiles of 256 (coalesced float4 loads, then
-// broadcast reads).  Each thread sums one tile of points in registers and
-// adds that partial into a (hi, lo) running sum in shared memory with an
-// error-free two-sum, so the result does not degrade with the number of
-// points a cell sees.
+// Every Table 1 kernel is a product f(s,t) = k(s) k(t) (Sec. III-C).  A CTA
+// owns 128 x 64 cells; for each batch of 32 points it first tabulates the
+// 128 x-factors and 64 (weighted) y-factors of every point in shared memory,
+// each evaluated once, then every thread accumulates the outer products of its
+// 8 x 8 cells: per point two 32-byte reads of each table and 64 FMAs.  Points
+// arrive in tiles of 256; each thread sums one tile in registers and adds that
+// partial into a (hi, lo) running sum in shared memory with an error-free
+// two-sum, so the result does not degrade with the number of points a cell
+// sees.  The factors and the order of every sum are those of a thread that
+// evaluates its own factors, so the result does not depend on the tabulation.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 
 namespace kde {
 namespace {
 
-constexpr int kThreads = 128;  // 16 (x) x 8 (y) threads
-constexpr int kTileX = 128;    // cells along x per CTA (16 threads x 8, stride 16)
-constexpr int kTileY = 64;     // cells along y per CTA (8 threads x 8, stride 8)
-constexpr int kPtsTile = 256;  // points per shared-memory tile
+constexpr int kThreads = 128;  // 16 (x) x 8 (y) threads, 8 x 8 consecutive cells each
+constexpr int kTileX = 128;    // cells along x per CTA
+constexpr int kTileY = 64;     // cells along y per CTA
+constexpr int kPtsTile = 256;  // points per register partial (two-sum cadence)
+constexpr int kBatch = 32;     // points per factor table (two CTAs fit an SM)
 
 template <int KID>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
     k_simt(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n_pad,
            int64_t per_split, const float2* __restrict__ gxt, const float2* __restrict__ gyt,
            int nx, int ny, float scale, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* sp = reinterpret_cast<float4*>(smem);                       // [kPtsTile]
-  float* sw = reinterpret_cast<float*>(sp + kPtsTile);                // [kPtsTile]
-  float2* run = reinterpret_cast<float2*>(sw + kPtsTile);             // [64][kThreads]
+  float* KX = reinterpret_cast<float*>(smem);                         // [kBatch][kTileX]
+  float* KY = KX + kBatch * kTileX;                                   // [kBatch][kTileY]
+  float2* run = reinterpret_cast<float2*>(KY + kBatch * kTileY);      // [64][kThreads]
+  float4* sp = reinterpret_cast<float4*>(run + 64 * kThreads);        // [kBatch]
+  float* sw = reinterpret_cast<float*>(sp + kBatch);                  // [kBatch]
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int x0 = blockIdx.x * kTileX + tx;
-  const int y0 = blockIdx.y * kTileY + ty;
-
-  float gxh[8], gxl[8], gyh[8], gyl[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int x = min(x0 + 16 * a, nx - 1);
-    const float2 g = gxt[x];
-    gxh[a] = g.x;
-    gxl[a] = g.y;
-  }
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int y = min(y0 + 8 * b, ny - 1);
-    const float2 g = gyt[y];
-    gyh[b] = g.x;
-    gyl[b] = g.y;
-  }
+  const int cx0 = blockIdx.x * kTileX, cy0 = blockIdx.y * kTileY;
 #pragma unroll
   for (int c = 0; c < 64; ++c) run[c * kThreads + tid] = make_float2(0.f, 0.f);
 
   const int64_t p_begin = (int64_t)blockIdx.z * per_split;
   int64_t p_end = p_begin + per_split;
   if (p_end > n_pad) p_end = n_pad;
+  // factor roles: x column tid; y row frow for points fq0 .. fq0 + kBatch/2 - 1
+  static_assert(kThreads == kTileX && kThreads == 2 * kTileY, "factor roles");
+  const float2 gxr = gxt[min(cx0 + tid, nx - 1)];
+  const int frow = tid & (kTileY - 1), fq0 = (tid / kTileY) * (kBatch / 2);
+  const float2 gyr = gyt[min(cy0 + frow, ny - 1)];
 
   for (int64_t base = p_begin; base < p_end; base += kPtsTile) {
-    __syncthreads();
-    for (int q = tid; q < kPtsTile; q += kThreads) {
-      const int64_t p = base + q;
-      if (p < p_end) {
-        sp[q] = pts[p];
-        sw[q] = wts[p];
-      } else {
-        sp[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        sw[q] = 0.f;
-      }
-    }
-    __syncthreads();
-
     float acc[8][8];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int a = 0; a < 8; ++a) acc[b][a] = 0.f;
 
-#pragma unroll 1
-    for (int q = 0; q < kPtsTile; ++q) {
-      const float4 P = sp[q];
-      const float wq = sw[q];
-      float kx[8], ky[8];
+    for (int bb = 0; bb < kPtsTile; bb += kBatch) {
+      __syncthreads();  // the previous batch's tables are consumed
+      if (tid < kBatch) {
+        const int64_t p = base + bb + tid;
+        if (p < p_end) {
+          sp[tid] = pts[p];
+          sw[tid] = wts[p];
+        } else {
+          sp[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sw[tid] = 0.f;
+        }
+      }
+      __syncthreads();
+      // x-factors: thread = column, all points of the batch; y-factors:
+      // thread = row, half of the points (consecutive lanes write consecutive
+      // words, so the stores are conflict-free)
+#pragma unroll 8
+      for (int q = 0; q < kBatch; ++q) {
+        const float4 P = sp[q];
+        KX[q * kTileX + tid] = kfactor<KID>((gxr.x - P.x) + (gxr.y - P.y));
+      }
+#pragma unroll 8
+      for (int k = 0; k < kBatch / 2; ++k) {
+        const int q = fq0 + k;
+        const float4 P = sp[q];
+        KY[q * kTileY + frow] = sw[q] * kfactor<KID>((gyr.x - P.z) + (gyr.y - P.w));
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int q = 0; q < kBatch; ++q) {
+        const float4 xa = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 8);
+        const float4 xb = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 8 + 4);
+        const float4 ya = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8);
+        const float4 yb = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8 + 4);
+        const float kx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+        const float ky[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-      for (int a = 0; a < 8; ++a) kx[a] = kfactor<KID>((gxh[a] - P.x) + (gxl[a] - P.y));
+        for (int b = 0; b < 8; ++b)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) ky[b] = wq * kfactor<KID>((gyh[b] - P.z) + (gyl[b] - P.w));
-#pragma unroll
-      for (int b = 0; b < 8; ++b)
-#pragma unroll
-        for (int a = 0; a < 8; ++a) acc[b][a] = fmaf(kx[a], ky[b], acc[b][a]);
+          for (int a = 0; a < 8; ++a) acc[b][a] = fmaf(kx[a], ky[b], acc[b][a]);
+      }
     }
 #pragma unroll
     for (int b = 0; b < 8; ++b)
@@ -104,11 +111,11 @@ __global__ void __launch_bounds__(kThreads, 3)
   float* dst = part + (int64_t)blockIdx.z * nx * ny;
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
-    const int y = y0 + 8 * b;
+    const int y = cy0 + ty * 8 + b;
     if (y >= ny) continue;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      const int x = x0 + 16 * a;
+      const int x = cx0 + tx * 8 + a;
       if (x >= nx) continue;
       const float2 r = run[(b * 8 + a) * kThreads + tid];
       dst[(int64_t)y * nx + x] = (r.x + r.y) * scale;
@@ -116,8 +123,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
 }
 
-constexpr size_t kSmem = kPtsTile * (sizeof(float4) + sizeof(float)) +
-                         64 * kThreads * sizeof(float2);
+constexpr size_t kSmem = kBatch * (kTileX + kTileY) * sizeof(float) +
+                         64 * kThreads * sizeof(float2) +
+                         kBatch * (sizeof(float4) + sizeof(float));
 
 template <int KID>
 cudaError_t launch_kid(const float4* pts, const float* wts, int64_t n_pad, const float2* gxt,
