@@ -71,18 +71,19 @@ def sparse_products(xy, origin, cell, nx, ny, h):
 
 
 def cutoff_pairs(xy, origin, cell, nx, ny, h):
-    """Point-cell pairs the cutoff path evaluates: every 32 x 32-cell output bin
-    reads the points of the bins within ceil((h/cell + 1)/32) of it (the
+    """Point-cell pairs the cutoff path evaluates: every 16 x 16-cell output bin
+    reads the points of the bins within ceil((h/cell + 1)/16) of it (the
     library's binning, in FP64 here)."""
     import numpy as np
-    nbx, nby = (nx + 31) // 32, (ny + 31) // 32
-    R = int(np.ceil((h / cell + 1.0) / 32))
+    B = 16
+    nbx, nby = (nx + B - 1) // B, (ny + B - 1) // B
+    R = int(np.ceil((h / cell + 1.0) / B))
     X = (xy[:, 0] - origin[0]) / h
     Y = (xy[:, 1] - origin[1]) / h
     cs = cell / h
     keep = (X >= -1) & (Y >= -1) & (X <= nx * cs + 1) & (Y <= ny * cs + 1)
-    bx = np.clip(np.floor(X[keep] / (32 * cs)), 0, nbx - 1).astype(np.int64)
-    by = np.clip(np.floor(Y[keep] / (32 * cs)), 0, nby - 1).astype(np.int64)
+    bx = np.clip(np.floor(X[keep] / (B * cs)), 0, nbx - 1).astype(np.int64)
+    by = np.clip(np.floor(Y[keep] / (B * cs)), 0, nby - 1).astype(np.int64)
     H = np.bincount(by * nbx + bx, minlength=nbx * nby).reshape(nby, nbx)
     S = np.zeros((nby + 1, nbx + 1), np.int64)
     S[1:, 1:] = H.cumsum(0).cumsum(1)
@@ -90,7 +91,7 @@ def cutoff_pairs(xy, origin, cell, nx, ny, h):
     y0, y1 = np.clip(jy - R, 0, nby - 1), np.clip(jy + R, 0, nby - 1)
     x0, x1 = np.clip(ix - R, 0, nbx - 1), np.clip(ix + R, 0, nbx - 1)
     reach = S[y1 + 1, x1 + 1] - S[y0, x1 + 1] - S[y1 + 1, x0] + S[y0, x0]
-    return int(1024 * reach.sum())
+    return int(B * B * reach.sum())
 
 
 def measured_traffic(path, grid, points):

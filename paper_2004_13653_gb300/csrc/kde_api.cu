@@ -338,7 +338,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       ++P->n_tc;
     } else {  // cutoff
       splits = 1;
-      I.geo = cutoff_geometry(a->nx, a->ny, a->cell / a->h, 1.0);
+      I.geo = cutoff_geometry(a->nx, a->ny, a->cell / a->h, 1.0, kCutoffBin);
       I.bin_begin = (int)P->total_bins;
       P->total_bins += I.geo.nbins;
       I.cut_begin = P->cut_m;
@@ -364,7 +364,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       const kde_args* a = &A[k];
       InstPlan& I = P->in[k];
       const double cs = a->cell * kernel_sigma(KDE_GAUSSIAN, a->h);
-      I.geo = cutoff_geometry(a->nx, a->ny, cs, kSparseReach);
+      I.geo = cutoff_geometry(a->nx, a->ny, cs, kSparseReach, kSparseBin);
       I.bin_begin = (int)P->total_bins;
       P->total_bins += I.geo.nbins;
       I.cut_begin = P->cut_m;

@@ -1,22 +1,25 @@
 // Path (c): the compact kernels of Table 1 evaluated over their support only.
 //
 // With the indicator of Eq. 8 a point contributes to the cells within one
-// bandwidth of it.  The grid is cut into 32x32-cell bins; every point gets the
+// bandwidth of it.  The grid is cut into 16x16-cell bins; every point gets the
 // key of its bin (points farther than a bandwidth outside the grid are
 // dropped), the (key, index) pairs are sorted with a stable LSD radix sort,
-// and each output bin is then computed by one CTA that reads the points of
-// the bins within reach, in sorted order, a batch of 64 at a time: for each
-// batch the CTA tabulates the x and y kernel factors of its 32 columns and 32
-// rows in shared memory, and each thread adds the outer products into its
-// four cells.  Nothing is accumulated with atomics, and the order of every
-// sum is fixed, so results are reproducible bit for bit.
+// and each output bin is then computed by one 64-thread CTA that reads the
+// points of the bins within reach, in sorted order, a batch of 64 at a time:
+// for each batch the CTA tabulates the x and y kernel factors of its 16
+// columns and 16 rows in shared memory, and each thread adds the outer
+// products into its four cells.  Nothing is accumulated with atomics, and the
+// order of every sum is fixed, so results are reproducible bit for bit.  The
+// same sort, with 32-cell bins and a wider reach, orders the points of the
+// block-sparse tensor-core path.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 
 namespace kde {
 namespace {
 
-constexpr int kBin = 32;            // cells per bin side (= output tile side)
+constexpr int kBin = kCutoffBin;    // cells per bin side (= output tile side)
+constexpr int kCutThreads = kBin * kBin / 4;  // one thread per column and 4 rows
 constexpr int kSortThreads = 256;   // 8 warps
 constexpr int kSortRounds = 8;      // 32-element rounds per warp
 constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
@@ -174,7 +177,7 @@ __device__ __forceinline__ float kfactor_rt(int kid, float d) {
 // Radial kernels: KX / KY hold squared offsets, the profile is evaluated per
 // pair on q = u^2 + v^2.
 template <int KID>
-__device__ __forceinline__ void radial_batch(const float (*KX)[32], const float (*KY)[32],
+__device__ __forceinline__ void radial_batch(const float (*KX)[kBin], const float (*KY)[kBin],
                                              const float* sW, int cnt, int cx, int cy0,
                                              float (&acc)[4]) {
   for (int c = 0; c < cnt; ++c) {
@@ -187,8 +190,8 @@ __device__ __forceinline__ void radial_batch(const float (*KX)[32], const float 
   }
 }
 
-__device__ __forceinline__ void radial_batch_rt(int kid, const float (*KX)[32],
-                                                const float (*KY)[32], const float* sW, int cnt,
+__device__ __forceinline__ void radial_batch_rt(int kid, const float (*KX)[kBin],
+                                                const float (*KY)[kBin], const float* sW, int cnt,
                                                 int cx, int cy0, float (&acc)[4]) {
   switch (kid) {
     case KDE_UNIFORM: radial_batch<KDE_UNIFORM>(KX, KY, sW, cnt, cx, cy0, acc); break;
@@ -201,10 +204,13 @@ __device__ __forceinline__ void radial_batch_rt(int kid, const float (*KX)[32],
   }
 }
 
-// One CTA per 32x32 output bin of some instance (blockIdx.x = global bin);
+// One CTA per 16x16 output bin of some instance (blockIdx.x = global bin);
 // thread (cx, 4 rows).  Product kernels (kid 0..7) use tabulated factors and
 // outer products; radial kernels (kid 8..15) tabulated squared offsets.
-__global__ void __launch_bounds__(256)
+// Bins of 16 cells keep the cells a CTA evaluates close to the support of
+// the points it reads (the support of a compact kernel is a few cells at the
+// bandwidths of interest), and spread a dense region over more CTAs.
+__global__ void __launch_bounds__(kCutThreads)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
              const float* __restrict__ W, const uint32_t* __restrict__ start) {
   __shared__ float4 sP[kBatch];
@@ -225,14 +231,16 @@ __global__ void __launch_bounds__(256)
   const int kid = radial ? I.kid - kRadial : I.kid;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int t = threadIdx.x;
-  const int cx = t & 31, cy0 = (t >> 5) * 4;
+  const int cx = t % kBin, cy0 = (t / kBin) * 4;
   if (t < kBin) sgx[t] = I.gxt[min(x0 + t, nx - 1)];
   else if (t < 2 * kBin) sgy[t - kBin] = I.gyt[min(y0 + t - kBin, ny - 1)];
   float2 run[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) run[r] = make_float2(0.f, 0.f);
-  // evaluation role: point c = t / 4, eight columns / rows starting at j0
-  const int ec = t >> 2, ej0 = (t & 3) * 8;
+  // evaluation role: point ec, kEval columns / rows starting at ej0
+  constexpr int kTPP = kCutThreads / kBatch, kEval = kBin / kTPP;
+  static_assert(kTPP >= 1 && kBin % kTPP == 0, "evaluation roles");
+  const int ec = t / kTPP, ej0 = (t % kTPP) * kEval;
 
   for (int qy = max(by - R, 0); qy <= min(by + R, I.nby - 1); ++qy) {
     const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(256)
         const float4 p = sP[ec];
         const float w = sW[ec];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kEval; ++j) {
           const float2 gx = sgx[ej0 + j], gy = sgy[ej0 + j];
           const float u = (gx.x - p.x) + (gx.y - p.y), v = (gy.x - p.z) + (gy.y - p.w);
           if (radial) {
@@ -297,14 +305,14 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
-CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach) {
+CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach, int bin) {
   CutoffGeom g;
-  g.nbx = (nx + kBin - 1) / kBin;
-  g.nby = (ny + kBin - 1) / kBin;
+  g.nbx = (nx + bin - 1) / bin;
+  g.nby = (ny + bin - 1) / bin;
   g.nbins = g.nbx * g.nby;
-  // bins a point can reach: its support plus half a cell, in 32-cell bins
-  g.R = (int)ceil((reach / cs + 1.0) / kBin);
-  g.inv_binw = 1.0 / (kBin * cs);
+  // bins a point can reach: its support plus half a cell, in bins of `bin` cells
+  g.R = (int)ceil((reach / cs + 1.0) / bin);
+  g.inv_binw = 1.0 / (bin * cs);
   g.ext_x = nx * cs + reach;
   g.ext_y = ny * cs + reach;
   return g;
@@ -357,7 +365,7 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
 cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
                                const CutoffScratch& ws, cudaStream_t s) {
   if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
-  k_cutoff<<<(unsigned)cut_bins, 256, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
+  k_cutoff<<<(unsigned)cut_bins, kCutThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
   note_launches(1);
   return cudaGetLastError();
 }

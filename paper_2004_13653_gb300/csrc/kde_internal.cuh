@@ -194,8 +194,12 @@ struct CutoffGeom {
   int nbx, nby, nbins, R;
   double inv_binw, ext_x, ext_y;
 };
+// Bin sides in cells: the cutoff path's output tiles, and the block-sparse
+// tensor-core work list's bins.
+constexpr int kCutoffBin = 16;
+constexpr int kSparseBin = 32;
 // cs: cell side in prepared units; reach: support radius in prepared units.
-CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach);
+CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach, int bin);
 struct CutoffScratch {
   uint32_t* keys[2];
   uint32_t* vals[2];
