@@ -447,6 +447,11 @@ def extra_workloads(dev):
     out["cutoff_epanechnikov_1M_1024sq"] = {
         "ms": ms, "Gpoint_cell_per_s": wl.n * wl.nx * wl.ny / ms / 1e6,
         "note": "definition-level rate (N nx ny / time); the path evaluates only the support"}
+    ms = _time(lambda: kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                                "radial_epanechnikov", out=F))
+    out["cutoff_radial_epanechnikov_1M_1024sq"] = {
+        "ms": ms, "Gpoint_cell_per_s": wl.n * wl.nx * wl.ny / ms / 1e6,
+        "note": "the radial variant K(|u|) on the unit disk, same points and grid"}
     inst = workloads.config4_instances()
     insts = [dict(points=torch.as_tensor(x.xy, dtype=torch.float64, device=dev),
                   weights=torch.as_tensor(x.w, device=dev), origin=x.origin, cell=x.cell,

@@ -217,7 +217,6 @@ __global__ void __launch_bounds__(kCutThreads)
   __shared__ float sW[kBatch];
   __shared__ __align__(16) float KX[kBatch][kBin];
   __shared__ __align__(16) float KY[kBatch][kBin];
-  __shared__ float2 sgx[kBin], sgy[kBin];
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -232,15 +231,15 @@ __global__ void __launch_bounds__(kCutThreads)
   const int x0 = bx * kBin, y0 = by * kBin;
   const int t = threadIdx.x;
   const int cx = t % kBin, cy0 = (t / kBin) * 4;
-  if (t < kBin) sgx[t] = I.gxt[min(x0 + t, nx - 1)];
-  else if (t < 2 * kBin) sgy[t - kBin] = I.gyt[min(y0 + t - kBin, ny - 1)];
+  const float2 gxe = I.gxt[min(x0 + t % kBin, nx - 1)];
+  const float2 gye = I.gyt[min(y0 + t % kBin, ny - 1)];
   float2 run[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) run[r] = make_float2(0.f, 0.f);
-  // evaluation role: point ec, kEval columns / rows starting at ej0
-  constexpr int kTPP = kCutThreads / kBatch, kEval = kBin / kTPP;
-  static_assert(kTPP >= 1 && kBin % kTPP == 0, "evaluation roles");
-  const int ec = t / kTPP, ej0 = (t % kTPP) * kEval;
+  // evaluation role: column (and row) ej of the bin for points eq0 .. eq0 + kEvalPts - 1
+  constexpr int kEvalPts = kBatch * kBin / kCutThreads;
+  static_assert(kCutThreads % kBin == 0 && kBatch * kBin % kCutThreads == 0, "evaluation roles");
+  const int ej = t % kBin, eq0 = (t / kBin) * kEvalPts;
 
   for (int qy = max(by - R, 0); qy <= min(by + R, I.nby - 1); ++qy) {
     const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
@@ -254,19 +253,21 @@ __global__ void __launch_bounds__(kCutThreads)
         sW[t] = W[b + t];
       }
       __syncthreads();
-      if (ec < cnt) {
-        const float4 p = sP[ec];
-        const float w = sW[ec];
-#pragma unroll
-        for (int j = 0; j < kEval; ++j) {
-          const float2 gx = sgx[ej0 + j], gy = sgy[ej0 + j];
-          const float u = (gx.x - p.x) + (gx.y - p.y), v = (gy.x - p.z) + (gy.y - p.w);
+      // factor tables: thread = column ej (and row ej) for points eq0.. (the
+      // lanes of a warp write consecutive words: conflict-free)
+#pragma unroll 4
+      for (int k = 0; k < kEvalPts; ++k) {
+        const int c = eq0 + k;
+        if (c < cnt) {
+          const float4 p = sP[c];
+          const float w = sW[c];
+          const float u = (gxe.x - p.x) + (gxe.y - p.y), v = (gye.x - p.z) + (gye.y - p.w);
           if (radial) {
-            KX[ec][ej0 + j] = u * u;
-            KY[ec][ej0 + j] = v * v;
+            KX[c][ej] = u * u;
+            KY[c][ej] = v * v;
           } else {
-            KX[ec][ej0 + j] = kfactor_rt(kid, u);
-            KY[ec][ej0 + j] = w * kfactor_rt(kid, v);
+            KX[c][ej] = kfactor_rt(kid, u);
+            KY[c][ej] = w * kfactor_rt(kid, v);
           }
         }
       }

@@ -4,7 +4,8 @@
 // owns 128 x 64 cells; for each batch of 32 points it first tabulates the
 // 128 x-factors and 64 (weighted) y-factors of every point in shared memory,
 // each evaluated once, then every thread accumulates the outer products of its
-// 8 x 8 cells: per point two 32-byte reads of each table and 64 FMAs.  Points
+// 8 x 8 cells (columns 4t..4t+3 and 64+4t..64+4t+3, eight consecutive rows):
+// per point two 16-byte reads of each table and 64 FMAs.  Points
 // arrive in tiles of 256; each thread sums one tile in registers and adds that
 // partial into a (hi, lo) running sum in shared memory with an error-free
 // two-sum, so the result does not degrade with the number of points a cell
@@ -16,7 +17,7 @@
 namespace kde {
 namespace {
 
-constexpr int kThreads = 128;  // 16 (x) x 8 (y) threads, 8 x 8 consecutive cells each
+constexpr int kThreads = 128;  // 16 (x) x 8 (y) threads, 8 x 8 cells each
 constexpr int kTileX = 128;    // cells along x per CTA
 constexpr int kTileY = 64;     // cells along y per CTA
 constexpr int kPtsTile = 256;  // points per register partial (two-sum cadence)
@@ -86,8 +87,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
 #pragma unroll 2
       for (int q = 0; q < kBatch; ++q) {
-        const float4 xa = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 8);
-        const float4 xb = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 8 + 4);
+        // columns 4tx.. and 64+4tx..: a half-warp reads 256 contiguous bytes
+        const float4 xa = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 4);
+        const float4 xb = *reinterpret_cast<const float4*>(KX + q * kTileX + 64 + tx * 4);
         const float4 ya = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8);
         const float4 yb = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8 + 4);
         const float kx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (y >= ny) continue;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      const int x = cx0 + tx * 8 + a;
+      const int x = cx0 + (a < 4 ? tx * 4 + a : 64 + tx * 4 + a - 4);
       if (x >= nx) continue;
       const float2 r = run[(b * 8 + a) * kThreads + tid];
       dst[(int64_t)y * nx + x] = (r.x + r.y) * scale;
