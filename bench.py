@@ -36,7 +36,7 @@ METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at
 # sources hash to the value they had when the counters were taken.
 TRAFFIC = {("tc_split16", 4096, 40_000): {
     "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh"],
-    "sha256": "b83b23efe5f8ecfca0953122c08ac53829b80d8c425afba1eeac1eac643f97d7",
+    "sha256": "22724af14a0b43dd6bb852792ddf0887579786e81251588bcdb1f5ee7c5e019f",
     "bytes": 1234056448 + 531219712}}
 
 
