@@ -241,18 +241,42 @@ __global__ void __launch_bounds__(kCutThreads)
   static_assert(kCutThreads % kBin == 0 && kBatch * kBin % kCutThreads == 0, "evaluation roles");
   const int ej = t % kBin, eq0 = (t / kBin) * kEvalPts;
 
-  for (int qy = max(by - R, 0); qy <= min(by + R, I.nby - 1); ++qy) {
-    const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
-    const int row = I.bin_begin + qy * I.nbx;
-    const uint32_t s = start[row + qx0], e = start[row + qx1 + 1];
-    for (uint32_t b = s; b < e; b += kBatch) {
+  // The batches of the bin rows within reach, in order; each batch's points
+  // are fetched into registers while the previous batch is computed.
+  const int qy_end = min(by + R, I.nby - 1);
+  const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
+  int qy = max(by - R, 0);
+  uint32_t b = 0, e = 0;
+  auto seek = [&]() {  // first batch of the next non-empty row (b == e: none left)
+    while (b >= e && qy <= qy_end) {
+      const int row = I.bin_begin + qy * I.nbx;
+      b = start[row + qx0];
+      e = start[row + qx1 + 1];
+      ++qy;
+    }
+  };
+  seek();
+  float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+  float wf = 0.f;
+  if (b < e && t < (int)min((uint32_t)kBatch, e - b)) {
+    pf = P[b + t];
+    wf = W[b + t];
+  }
+  while (b < e) {
+    {
       const int cnt = (int)min((uint32_t)kBatch, e - b);
       __syncthreads();  // previous batch fully consumed
       if (t < cnt) {
-        sP[t] = P[b + t];
-        sW[t] = W[b + t];
+        sP[t] = pf;
+        sW[t] = wf;
       }
       __syncthreads();
+      b += kBatch;
+      if (b >= e) seek();
+      if (b < e && t < (int)min((uint32_t)kBatch, e - b)) {  // next batch, in flight
+        pf = P[b + t];
+        wf = W[b + t];
+      }
       // factor tables: thread = column ej (and row ej) for points eq0.. (the
       // lanes of a warp write consecutive words: conflict-free)
 #pragma unroll 4
