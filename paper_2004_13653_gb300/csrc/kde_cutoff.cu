@@ -300,7 +300,27 @@ __global__ void __launch_bounds__(kCutThreads)
       if (radial) {
         radial_batch_rt(kid, KX, KY, sW, cnt, cx, cy0, acc);
       } else {
-        for (int c = 0; c < cnt; ++c) {
+        // four points per step so their table reads are in flight together,
+        // the rest of a short batch one at a time (the order of the sums is
+        // unchanged)
+        int c = 0;
+        for (; c + 4 <= cnt; c += 4) {
+          float kx[4];
+          float4 ky[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            kx[u] = KX[c + u][cx];
+            ky[u] = *reinterpret_cast<const float4*>(&KY[c + u][cy0]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[0] = fmaf(kx[u], ky[u].x, acc[0]);
+            acc[1] = fmaf(kx[u], ky[u].y, acc[1]);
+            acc[2] = fmaf(kx[u], ky[u].z, acc[2]);
+            acc[3] = fmaf(kx[u], ky[u].w, acc[3]);
+          }
+        }
+        for (; c < cnt; ++c) {
           const float kx = KX[c][cx];
           const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
           acc[0] = fmaf(kx, ky.x, acc[0]);
