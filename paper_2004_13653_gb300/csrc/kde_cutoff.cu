@@ -19,7 +19,8 @@ namespace kde {
 namespace {
 
 constexpr int kBin = kCutoffBin;    // cells per bin side (= output tile side)
-constexpr int kCutThreads = kBin * kBin / 4;  // one thread per column and 4 rows
+constexpr int kGroupThreads = kBin * kBin / 4;  // a point group: one thread per column, 4 rows
+constexpr int kGroups = 4;          // point groups per CTA (one bin)
 constexpr int kSortThreads = 256;   // 8 warps
 constexpr int kSortRounds = 8;      // 32-element rounds per warp
 constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
@@ -162,61 +163,164 @@ __global__ void k_permute(const float4* __restrict__ pts, const float* __restric
   }
 }
 
-__device__ __forceinline__ float kfactor_rt(int kid, float d) {
-  switch (kid) {
-    case KDE_UNIFORM: return kfactor<KDE_UNIFORM>(d);
-    case KDE_TRIANGULAR: return kfactor<KDE_TRIANGULAR>(d);
-    case KDE_EPANECHNIKOV: return kfactor<KDE_EPANECHNIKOV>(d);
-    case KDE_QUARTIC: return kfactor<KDE_QUARTIC>(d);
-    case KDE_TRIWEIGHT: return kfactor<KDE_TRIWEIGHT>(d);
-    case KDE_TRICUBE: return kfactor<KDE_TRICUBE>(d);
-    default: return kfactor<KDE_COSINE>(d);
-  }
-}
 
-// Radial kernels: KX / KY hold squared offsets, the profile is evaluated per
-// pair on q = u^2 + v^2.
-template <int KID>
-__device__ __forceinline__ void radial_batch(const float (*KX)[kBin], const float (*KY)[kBin],
-                                             const float* sW, int cnt, int cx, int cy0,
-                                             float (&acc)[4]) {
-  for (int c = 0; c < cnt; ++c) {
-    const float kx = KX[c][cx], w = sW[c];
+// Accumulate one batch's outer products into a thread's four cells (column
+// cx, rows cy0..cy0+3): product kernels from tabulated factors, radial kernels
+// from tabulated squared offsets and the profile per pair.
+template <int KID, bool RADIAL>
+__device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float (*KY)[kBin],
+                                           const float* sW, int cnt, int cx, int cy0,
+                                           float (&acc)[4]) {
+  int c = 0;
+  if (!RADIAL) {  // four points per step so their table reads are in flight together
+    for (; c + 4 <= cnt; c += 4) {
+      float kx[4];
+      float4 ky[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kx[u] = KX[c + u][cx];
+        ky[u] = *reinterpret_cast<const float4*>(&KY[c + u][cy0]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc[0] = fmaf(kx[u], ky[u].x, acc[0]);
+        acc[1] = fmaf(kx[u], ky[u].y, acc[1]);
+        acc[2] = fmaf(kx[u], ky[u].z, acc[2]);
+        acc[3] = fmaf(kx[u], ky[u].w, acc[3]);
+      }
+    }
+  }
+  for (; c < cnt; ++c) {
+    const float kx = KX[c][cx];
     const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
-    acc[0] = fmaf(w, kradial<KID>(kx + ky.x), acc[0]);
-    acc[1] = fmaf(w, kradial<KID>(kx + ky.y), acc[1]);
-    acc[2] = fmaf(w, kradial<KID>(kx + ky.z), acc[2]);
-    acc[3] = fmaf(w, kradial<KID>(kx + ky.w), acc[3]);
+    if (RADIAL) {
+      const float w = sW[c];
+      acc[0] = fmaf(w, kradial<KID>(kx + ky.x), acc[0]);
+      acc[1] = fmaf(w, kradial<KID>(kx + ky.y), acc[1]);
+      acc[2] = fmaf(w, kradial<KID>(kx + ky.z), acc[2]);
+      acc[3] = fmaf(w, kradial<KID>(kx + ky.w), acc[3]);
+    } else {
+      acc[0] = fmaf(kx, ky.x, acc[0]);
+      acc[1] = fmaf(kx, ky.y, acc[1]);
+      acc[2] = fmaf(kx, ky.z, acc[2]);
+      acc[3] = fmaf(kx, ky.w, acc[3]);
+    }
   }
 }
 
-__device__ __forceinline__ void radial_batch_rt(int kid, const float (*KX)[kBin],
-                                                const float (*KY)[kBin], const float* sW, int cnt,
-                                                int cx, int cy0, float (&acc)[4]) {
-  switch (kid) {
-    case KDE_UNIFORM: radial_batch<KDE_UNIFORM>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    case KDE_TRIANGULAR: radial_batch<KDE_TRIANGULAR>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    case KDE_EPANECHNIKOV: radial_batch<KDE_EPANECHNIKOV>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    case KDE_QUARTIC: radial_batch<KDE_QUARTIC>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    case KDE_TRIWEIGHT: radial_batch<KDE_TRIWEIGHT>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    case KDE_TRICUBE: radial_batch<KDE_TRICUBE>(KX, KY, sW, cnt, cx, cy0, acc); break;
-    default: radial_batch<KDE_COSINE>(KX, KY, sW, cnt, cx, cy0, acc); break;
+// Position in the sequence of batches of one bin: the rows of bins within
+// reach in order, each row's points in kBatch-point batches.
+struct BatchPos {
+  int qy;
+  uint32_t b, e;
+};
+
+// Shared-memory tables of one point group.
+struct GroupTables {
+  float4 P[kBatch];
+  float W[kBatch];
+  __align__(16) float KX[kBatch][kBin];
+  __align__(16) float KY[kBatch][kBin];
+};
+
+// The bin's work, for one kernel: group g of the CTA takes batches g, g+G,
+// g+2G, ... of the bin's sequence (fetching the next while computing the
+// current), and ends with the two-sum of its four cells in run.
+template <int KID, bool RADIAL>
+__device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
+                                             const float* __restrict__ W,
+                                             const uint32_t* __restrict__ start, int bx, int by,
+                                             int g, int tg, GroupTables& T, float2 (&run)[4]) {
+  const int nx = I.nx, ny = I.ny, R = I.R;
+  const int x0 = bx * kBin, y0 = by * kBin;
+  const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
+  // table role: column (and row) ej for points eq0 .. eq0 + kEvalPts - 1
+  constexpr int kEvalPts = kBatch * kBin / kGroupThreads;
+  static_assert(kGroupThreads % kBin == 0 && kBatch * kBin % kGroupThreads == 0, "table roles");
+  const int ej = tg % kBin, eq0 = (tg / kBin) * kEvalPts;
+  const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
+  const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
+  const int qy_end = min(by + R, I.nby - 1);
+  const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
+  auto next_row = [&](BatchPos& q) {  // first batch of the next non-empty row
+    while (q.b >= q.e && q.qy <= qy_end) {
+      const int row = I.bin_begin + q.qy * I.nbx;
+      q.b = start[row + qx0];
+      q.e = start[row + qx1 + 1];
+      ++q.qy;
+    }
+  };
+  auto skip = [&](BatchPos& q, int k) {  // move k batches on
+    while (k > 0 && q.b < q.e) {
+      const uint32_t rem = (q.e - q.b + kBatch - 1) / kBatch;
+      if ((uint32_t)k < rem) {
+        q.b += (uint32_t)k * kBatch;
+        k = 0;
+      } else {
+        k -= (int)rem;
+        q.b = q.e;
+        next_row(q);
+      }
+    }
+  };
+  auto group_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads)); };
+  BatchPos q = {max(by - R, 0), 0u, 0u};
+  next_row(q);
+  skip(q, g);
+  float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+  float wf = 0.f;
+  if (q.b < q.e && tg < (int)min((uint32_t)kBatch, q.e - q.b)) {
+    pf = P[q.b + tg];
+    wf = W[q.b + tg];
+  }
+  while (q.b < q.e) {
+    const int cnt = (int)min((uint32_t)kBatch, q.e - q.b);
+    group_sync();  // the group's previous batch is consumed
+    if (tg < cnt) {
+      T.P[tg] = pf;
+      T.W[tg] = wf;
+    }
+    group_sync();
+    skip(q, kGroups);
+    if (q.b < q.e && tg < (int)min((uint32_t)kBatch, q.e - q.b)) {  // next batch, in flight
+      pf = P[q.b + tg];
+      wf = W[q.b + tg];
+    }
+    // the lanes of a warp write consecutive words: conflict-free
+#pragma unroll 4
+    for (int k = 0; k < kEvalPts; ++k) {
+      const int c = eq0 + k;
+      if (c < cnt) {
+        const float4 p = T.P[c];
+        const float u = (gxe.x - p.x) + (gxe.y - p.y), v = (gye.x - p.z) + (gye.y - p.w);
+        if (RADIAL) {
+          T.KX[c][ej] = u * u;
+          T.KY[c][ej] = v * v;
+        } else {
+          T.KX[c][ej] = kfactor<KID>(u);
+          T.KY[c][ej] = T.W[c] * kfactor<KID>(v);
+        }
+      }
+    }
+    group_sync();
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    accumulate<KID, RADIAL>(T.KX, T.KY, T.W, cnt, cx, cy0, acc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) two_sum_acc(run[r], acc[r]);
   }
 }
 
-// One CTA per 16x16 output bin of some instance (blockIdx.x = global bin);
-// thread (cx, 4 rows).  Product kernels (kid 0..7) use tabulated factors and
-// outer products; radial kernels (kid 8..15) tabulated squared offsets.
-// Bins of 16 cells keep the cells a CTA evaluates close to the support of
-// the points it reads (the support of a compact kernel is a few cells at the
-// bandwidths of interest), and spread a dense region over more CTAs.
-__global__ void __launch_bounds__(kCutThreads)
+// One CTA per 16x16 output bin of some instance (blockIdx.x = global bin),
+// kGroups point groups of 64 threads: a dense bin's points are shared out
+// over the groups, whose (hi, lo) sums are added in group order at the end,
+// so results are reproducible.  Bins of 16 cells keep the cells a CTA
+// evaluates close to the support of the points it reads (a few cells at the
+// bandwidths of interest) and spread a dense region over more CTAs.
+__global__ void __launch_bounds__(kGroups * kGroupThreads)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
              const float* __restrict__ W, const uint32_t* __restrict__ start) {
-  __shared__ float4 sP[kBatch];
-  __shared__ float sW[kBatch];
-  __shared__ __align__(16) float KX[kBatch][kBin];
-  __shared__ __align__(16) float KY[kBatch][kBin];
+  __shared__ GroupTables tables[kGroups];
+  __shared__ float2 part[kGroups][kGroupThreads][4];
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -225,120 +329,45 @@ __global__ void __launch_bounds__(kCutThreads)
   const CutInst& I = tab[lo];
   const int local = blockIdx.x - I.bin_begin;
   const int bx = local % I.nbx, by = local / I.nbx;
-  const int nx = I.nx, ny = I.ny, R = I.R;
-  const bool radial = I.kid >= kRadial;
-  const int kid = radial ? I.kid - kRadial : I.kid;
-  const int x0 = bx * kBin, y0 = by * kBin;
-  const int t = threadIdx.x;
-  const int cx = t % kBin, cy0 = (t / kBin) * 4;
-  const float2 gxe = I.gxt[min(x0 + t % kBin, nx - 1)];
-  const float2 gye = I.gyt[min(y0 + t % kBin, ny - 1)];
+  const int g = threadIdx.x / kGroupThreads, tg = threadIdx.x % kGroupThreads;
   float2 run[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) run[r] = make_float2(0.f, 0.f);
-  // evaluation role: column (and row) ej of the bin for points eq0 .. eq0 + kEvalPts - 1
-  constexpr int kEvalPts = kBatch * kBin / kCutThreads;
-  static_assert(kCutThreads % kBin == 0 && kBatch * kBin % kCutThreads == 0, "evaluation roles");
-  const int ej = t % kBin, eq0 = (t / kBin) * kEvalPts;
-
-  // The batches of the bin rows within reach, in order; each batch's points
-  // are fetched into registers while the previous batch is computed.
-  const int qy_end = min(by + R, I.nby - 1);
-  const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
-  int qy = max(by - R, 0);
-  uint32_t b = 0, e = 0;
-  auto seek = [&]() {  // first batch of the next non-empty row (b == e: none left)
-    while (b >= e && qy <= qy_end) {
-      const int row = I.bin_begin + qy * I.nbx;
-      b = start[row + qx0];
-      e = start[row + qx1 + 1];
-      ++qy;
-    }
-  };
-  seek();
-  float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
-  float wf = 0.f;
-  if (b < e && t < (int)min((uint32_t)kBatch, e - b)) {
-    pf = P[b + t];
-    wf = W[b + t];
+  GroupTables& T = tables[g];
+  switch (I.kid) {
+#define KDE_CUT(K)                                                                      \
+  case K:                                                                               \
+    cutoff_group<K, false>(I, P, W, start, bx, by, g, tg, T, run);                      \
+    break;                                                                              \
+  case kRadial + K:                                                                     \
+    cutoff_group<K, true>(I, P, W, start, bx, by, g, tg, T, run);                       \
+    break;
+    KDE_CUT(KDE_UNIFORM)
+    KDE_CUT(KDE_TRIANGULAR)
+    KDE_CUT(KDE_EPANECHNIKOV)
+    KDE_CUT(KDE_QUARTIC)
+    KDE_CUT(KDE_TRIWEIGHT)
+    KDE_CUT(KDE_TRICUBE)
+    KDE_CUT(KDE_COSINE)
+#undef KDE_CUT
+    default: break;
   }
-  while (b < e) {
-    {
-      const int cnt = (int)min((uint32_t)kBatch, e - b);
-      __syncthreads();  // previous batch fully consumed
-      if (t < cnt) {
-        sP[t] = pf;
-        sW[t] = wf;
-      }
-      __syncthreads();
-      b += kBatch;
-      if (b >= e) seek();
-      if (b < e && t < (int)min((uint32_t)kBatch, e - b)) {  // next batch, in flight
-        pf = P[b + t];
-        wf = W[b + t];
-      }
-      // factor tables: thread = column ej (and row ej) for points eq0.. (the
-      // lanes of a warp write consecutive words: conflict-free)
-#pragma unroll 4
-      for (int k = 0; k < kEvalPts; ++k) {
-        const int c = eq0 + k;
-        if (c < cnt) {
-          const float4 p = sP[c];
-          const float w = sW[c];
-          const float u = (gxe.x - p.x) + (gxe.y - p.y), v = (gye.x - p.z) + (gye.y - p.w);
-          if (radial) {
-            KX[c][ej] = u * u;
-            KY[c][ej] = v * v;
-          } else {
-            KX[c][ej] = kfactor_rt(kid, u);
-            KY[c][ej] = w * kfactor_rt(kid, v);
-          }
-        }
-      }
-      __syncthreads();
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      if (radial) {
-        radial_batch_rt(kid, KX, KY, sW, cnt, cx, cy0, acc);
-      } else {
-        // four points per step so their table reads are in flight together,
-        // the rest of a short batch one at a time (the order of the sums is
-        // unchanged)
-        int c = 0;
-        for (; c + 4 <= cnt; c += 4) {
-          float kx[4];
-          float4 ky[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            kx[u] = KX[c + u][cx];
-            ky[u] = *reinterpret_cast<const float4*>(&KY[c + u][cy0]);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            acc[0] = fmaf(kx[u], ky[u].x, acc[0]);
-            acc[1] = fmaf(kx[u], ky[u].y, acc[1]);
-            acc[2] = fmaf(kx[u], ky[u].z, acc[2]);
-            acc[3] = fmaf(kx[u], ky[u].w, acc[3]);
-          }
-        }
-        for (; c < cnt; ++c) {
-          const float kx = KX[c][cx];
-          const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
-          acc[0] = fmaf(kx, ky.x, acc[0]);
-          acc[1] = fmaf(kx, ky.y, acc[1]);
-          acc[2] = fmaf(kx, ky.z, acc[2]);
-          acc[3] = fmaf(kx, ky.w, acc[3]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) two_sum_acc(run[r], acc[r]);
-    }
-  }
-  const int x = x0 + cx;
-  if (x < nx) {
+  for (int r = 0; r < 4; ++r) part[g][tg][r] = run[r];
+  __syncthreads();
+  if (g == 0) {
+    const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
+    const int x = bx * kBin + cx;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int y = y0 + cy0 + r;
-      if (y < ny) I.out[(int64_t)y * nx + x] = (run[r].x + run[r].y) * I.scale;
+      float2 sum = part[0][tg][r];
+      for (int h = 1; h < kGroups; ++h) {
+        const float2 o = part[h][tg][r];
+        two_sum_acc(sum, o.x);
+        sum.y += o.y;
+      }
+      const int y = by * kBin + cy0 + r;
+      if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
     }
   }
 }
@@ -410,7 +439,8 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
 cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
                                const CutoffScratch& ws, cudaStream_t s) {
   if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
-  k_cutoff<<<(unsigned)cut_bins, kCutThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw, ws.start);
+  k_cutoff<<<(unsigned)cut_bins, kGroups * kGroupThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw,
+                                                                   ws.start);
   note_launches(1);
   return cudaGetLastError();
 }
