@@ -36,8 +36,8 @@ METRIC = "KDE Gpoint·cell/s, 20M pts×4096² grid: split-FP16 tensor vs FP32 at
 # sources hash to the value they had when the counters were taken.
 TRAFFIC = {("tc_split16", 4096, 40_000): {
     "sources": ["paper_2004_13653_gb300/csrc/kde_tc2.cu", "paper_2004_13653_gb300/csrc/tc_ptx.cuh"],
-    "sha256": "22724af14a0b43dd6bb852792ddf0887579786e81251588bcdb1f5ee7c5e019f",
-    "bytes": 1234056448 + 531219712}}
+    "sha256": "47e69bb292466c355803a3516ebf30a3d369c3488f78af2d9088b698acfbb2d2",
+    "bytes": 1260884224 + 532821248}}
 
 
 def sparse_products(xy, origin, cell, nx, ny, h):
@@ -71,27 +71,40 @@ def sparse_products(xy, origin, cell, nx, ny, h):
 
 
 def cutoff_pairs(xy, origin, cell, nx, ny, h):
-    """Point-cell pairs the cutoff path evaluates: every 16 x 16-cell output bin
-    reads the points of the bins within ceil((h/cell + 1)/16) of it (the
+    """Point-cell pairs the cutoff path evaluates: every 16 x 16-cell output
+    block reads the points of the sort bins (4, 8 or 16 cells, chosen from
+    h/cell) whose points can lie within a bandwidth of its cell centres (the
     library's binning, in FP64 here)."""
     import numpy as np
-    B = 16
-    nbx, nby = (nx + B - 1) // B, (ny + B - 1) // B
-    R = int(np.ceil((h / cell + 1.0) / B))
+    rc = h / cell
+    S = 4 if rc <= 6.0 else 8 if rc <= 16.0 else 16
+    while S < 64 and ((nx + S - 1) // S) * ((ny + S - 1) // S) > (1 << 24):
+        S *= 2
+    B, cs, reach = 16, cell / h, 1.0 + 1e-6
+    inv_binw = 1.0 / (S * cs)
+    nbx, nby = (nx + S - 1) // S, (ny + S - 1) // S
     X = (xy[:, 0] - origin[0]) / h
     Y = (xy[:, 1] - origin[1]) / h
-    cs = cell / h
     keep = (X >= -1) & (Y >= -1) & (X <= nx * cs + 1) & (Y <= ny * cs + 1)
-    bx = np.clip(np.floor(X[keep] / (B * cs)), 0, nbx - 1).astype(np.int64)
-    by = np.clip(np.floor(Y[keep] / (B * cs)), 0, nby - 1).astype(np.int64)
+    bx = np.clip(np.floor(X[keep] * inv_binw), 0, nbx - 1).astype(np.int64)
+    by = np.clip(np.floor(Y[keep] * inv_binw), 0, nby - 1).astype(np.int64)
     H = np.bincount(by * nbx + bx, minlength=nbx * nby).reshape(nby, nbx)
-    S = np.zeros((nby + 1, nbx + 1), np.int64)
-    S[1:, 1:] = H.cumsum(0).cumsum(1)
-    jy, ix = np.meshgrid(np.arange(nby), np.arange(nbx), indexing="ij")
-    y0, y1 = np.clip(jy - R, 0, nby - 1), np.clip(jy + R, 0, nby - 1)
-    x0, x1 = np.clip(ix - R, 0, nbx - 1), np.clip(ix + R, 0, nbx - 1)
-    reach = S[y1 + 1, x1 + 1] - S[y0, x1 + 1] - S[y1 + 1, x0] + S[y0, x0]
-    return int(B * B * reach.sum())
+    C = np.zeros((nby + 1, nbx + 1), np.int64)
+    C[1:, 1:] = H.cumsum(0).cumsum(1)
+
+    def lo_hi(c0, n):
+        lo = np.clip(np.floor(((c0 + 0.5) * cs - reach) * inv_binw), 0, n).astype(np.int64)
+        hi = np.minimum(np.floor(((c0 + B - 0.5) * cs + reach) * inv_binw), n - 1).astype(np.int64)
+        return lo, hi
+    lx, hx = lo_hi(np.arange(0, nx, B), nbx)
+    ly, hy = lo_hi(np.arange(0, ny, B), nby)
+    LY, LX = np.meshgrid(ly, lx, indexing="ij")
+    HY, HX = np.meshgrid(hy, hx, indexing="ij")
+    ok = (LX <= HX) & (LY <= HY)
+    HX1, HY1 = np.where(ok, HX + 1, 0), np.where(ok, HY + 1, 0)
+    LX, LY = np.where(ok, LX, 0), np.where(ok, LY, 0)
+    reach_pts = C[HY1, HX1] - C[LY, HX1] - C[HY1, LX] + C[LY, LX]
+    return int(B * B * reach_pts.sum())
 
 
 def measured_traffic(path, grid, points):
@@ -368,27 +381,38 @@ def run_ours(args):
         w_host = torch.as_tensor(wl.w).pin_memory()
         out_host = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
 
-        def e2e_step():
+        def e2e_step(events=None):
             lonlat_dev.copy_(lonlat_host, non_blocking=True)
             w_dev.copy_(w_host, non_blocking=True)
-            step()
+            step(events)
             out_host.copy_(out_dev, non_blocking=True)
 
         e2e_step()
+        e2e_pairs = [new_pair() for _ in range(args.steps)]
         torch.cuda.synchronize()
         barrier(world)
+        e2e_clocks = ClockSampler(local)
+        e2e_clocks.start()
+        time.sleep(0.3)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        for k in range(args.steps):
+            e2e_step(kde.event_pair(*e2e_pairs[k]))
         e1.record(stream)
         torch.cuda.synchronize()
+        barrier(world)
         ems = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
         result["e2e"] = {"value": replica_value(world, evals, ems), "unit": UNIT,
                          "ms_per_step": ems,
                          "h2d_bytes_per_step": int(lonlat_host.numel() * 8 + w_host.numel() * 4),
-                         "d2h_bytes_per_step": int(out_host.numel() * 4)}
+                         "d2h_bytes_per_step": int(out_host.numel() * 4),
+                         # the dominant kernel's own time inside this loop and the
+                         # clocks seen meanwhile: the step minus the kernel is copies
+                         # and projection, a kernel slower than in the device-resident
+                         # loop is a clock difference
+                         "kernel_ms": statistics.mean(a.elapsed_time(b) for a, b in e2e_pairs),
+                         "clocks": e2e_clocks.stop()}
 
     sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -188,6 +188,7 @@ struct InstPlan {
   // cutoff path, and the bin sort of block-sparse tensor-core instances
   CutoffGeom geo;
   int bin_begin;
+  int obx, oby, out_begin;  // cutoff: output blocks of kCutoffBin cells, first CTA
   int64_t cut_begin;
   int tile_begin;  // block-sparse: first tile in the batch's tile numbering
 };
@@ -207,7 +208,8 @@ struct BatchPlan {
   int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0, cut_bins = 0;
   bool sparse = false;  // block-sparse tensor-core instances
   int tiles_total = 0, piece_len = 0, max_pieces = 0;
-  size_t off_sp_total = 0, off_sp_np = 0, off_sp_pb = 0, off_sp_temp = 0, off_sp_part = 0;
+  size_t off_sp_total = 0, off_sp_np = 0, off_sp_pb = 0, off_sp_nf = 0, off_sp_fb = 0,
+         off_sp_tail = 0, off_sp_temp = 0, off_sp_part = 0;
   CutoffSizes cz;
   bool host_pts = false, host_w = false, host_out = false;
   size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
@@ -338,9 +340,14 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       ++P->n_tc;
     } else {  // cutoff
       splits = 1;
-      I.geo = cutoff_geometry(a->nx, a->ny, a->cell / a->h, 1.0, kCutoffBin);
+      I.geo = cutoff_geometry(a->nx, a->ny, a->cell / a->h, 1.0,
+                              cutoff_sort_bin(a->nx, a->ny, a->h / a->cell));
       I.bin_begin = (int)P->total_bins;
       P->total_bins += I.geo.nbins;
+      I.obx = (a->nx + kCutoffBin - 1) / kCutoffBin;
+      I.oby = (a->ny + kCutoffBin - 1) / kCutoffBin;
+      I.out_begin = (int)P->cut_bins;
+      P->cut_bins += (int64_t)I.obx * I.oby;
       I.cut_begin = P->cut_m;
       P->cut_m += I.n_pad;
       ++P->n_cut;
@@ -355,7 +362,6 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   std::stable_sort(P->tc_order.begin(), P->tc_order.end(), [&](int x, int y) {
     return P->in[x].per_split > P->in[y].per_split;
   });
-  P->cut_bins = P->total_bins;
   if (P->sparse) {
     // bins of the block-sparse instances follow the cutoff bins in the sort
     double est = 0.0;
@@ -376,7 +382,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     // pieces of about an eighth of each CTA pair's share, in whole drain chunks
     const int clusters = std::max(1, ctas / 2);
     int64_t L = (int64_t)(est / (8.0 * clusters));
-    L = std::max<int64_t>(2048, std::min<int64_t>(32768, L));
+    L = std::max<int64_t>(2048, std::min<int64_t>(kSparseMaxPiece, L));
     L = (L + t.k_chunk - 1) / t.k_chunk * t.k_chunk;
     P->piece_len = (int)L;
     for (int k : P->tc_order) {
@@ -432,6 +438,9 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     P->off_sp_total = take(u * (size_t)P->tiles_total);
     P->off_sp_np = take(u * ((size_t)P->tiles_total + 1));
     P->off_sp_pb = take(u * ((size_t)P->tiles_total + 1));
+    P->off_sp_nf = take(u * ((size_t)P->tiles_total + 1));
+    P->off_sp_fb = take(u * ((size_t)P->tiles_total + 1));
+    P->off_sp_tail = take(u * (size_t)P->tiles_total);
     P->off_sp_temp = take(u * sparse_scan_words(P->tiles_total));
     P->off_sp_part = take(sizeof(float) * 65536 * (size_t)P->max_pieces);
   }
@@ -587,7 +596,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   for (int k = 0; k < count; ++k) {
     const InstPlan& I = P.in[k];
     if (I.path == KDE_PATH_CUTOFF) {
-      CutInst q;
+      CutInst q = {};
       q.gxt = prep[k].gxt;
       q.gyt = prep[k].gyt;
       q.out = out_dev[k];
@@ -599,10 +608,13 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.ext_x = I.geo.ext_x;
       q.ext_y = I.geo.ext_y;
       q.reach = 1.0;
+      q.cs = A[k].cell / A[k].h;
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
-      q.R = I.geo.R;
       q.bin_begin = I.bin_begin;
+      q.obx = I.obx;
+      q.oby = I.oby;
+      q.out_begin = I.out_begin;
       q.nx = A[k].nx;
       q.ny = A[k].ny;
       q.kid = kid_of(&A[k]);
@@ -635,9 +647,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.ext_x = I.geo.ext_x;
       q.ext_y = I.geo.ext_y;
       q.reach = kSparseReach;
+      q.cs = A[k].cell * kernel_sigma(KDE_GAUSSIAN, A[k].h);
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
-      q.R = I.geo.R;
       q.bin_begin = I.bin_begin;
       q.nx = A[k].nx;
       q.ny = A[k].ny;
@@ -682,12 +694,15 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   if (P.n_tc && P.sparse) {
     SparseCtl sp;
     sp.piece_begin = reinterpret_cast<const uint32_t*>(base + P.off_sp_pb);
+    sp.full_begin = reinterpret_cast<const uint32_t*>(base + P.off_sp_fb);
+    sp.tail_tile = reinterpret_cast<const uint32_t*>(base + P.off_sp_tail);
     sp.tile_total = reinterpret_cast<const uint32_t*>(base + P.off_sp_total);
     sp.part = reinterpret_cast<float*>(base + P.off_sp_part);
     sp.tiles_total = P.tiles_total;
     sp.piece_len = P.piece_len;
     sp.max_pieces = P.max_pieces;
     KDE_CUDA(launch_sparse_plan(d_tc, P.n_tc, sp, reinterpret_cast<uint32_t*>(base + P.off_sp_np),
+                                reinterpret_cast<uint32_t*>(base + P.off_sp_nf),
                                 reinterpret_cast<uint32_t*>(base + P.off_sp_temp), batch_scal, s),
              "block-sparse work list");
     KDE_CUDA(launch_tc_pair(P.tc, d_tc, P.n_tc, 0, &sp, batch_scal, s),

@@ -1,24 +1,24 @@
 // Path (c): the compact kernels of Table 1 evaluated over their support only.
 //
 // With the indicator of Eq. 8 a point contributes to the cells within one
-// bandwidth of it.  The grid is cut into 16x16-cell bins; every point gets the
-// key of its bin (points farther than a bandwidth outside the grid are
-// dropped), the (key, index) pairs are sorted with a stable LSD radix sort,
-// and each output bin is then computed by one 64-thread CTA that reads the
-// points of the bins within reach, in sorted order, a batch of 64 at a time:
-// for each batch the CTA tabulates the x and y kernel factors of its 16
-// columns and 16 rows in shared memory, and each thread adds the outer
-// products into its four cells.  Nothing is accumulated with atomics, and the
-// order of every sum is fixed, so results are reproducible bit for bit.  The
-// same sort, with 32-cell bins and a wider reach, orders the points of the
-// block-sparse tensor-core path.
+// bandwidth of it.  Every point gets the key of its sort bin (4, 8 or 16
+// cells a side, chosen from the bandwidth; points farther than a bandwidth
+// outside the grid are dropped), the (key, index) pairs are sorted with a
+// stable LSD radix sort, and each 16x16-cell output block is then computed by
+// one CTA that reads the points of the sort bins within reach of its cells,
+// in sorted order, a batch of 64 at a time: for each batch a point group
+// tabulates the x and y kernel factors of its 16 columns and 16 rows in shared
+// memory, and each thread adds the outer products into its four cells.
+// Nothing is accumulated with atomics, and the order of every sum is fixed,
+// so results are reproducible bit for bit.  The same sort, with 32-cell bins
+// and a wider reach, orders the points of the block-sparse tensor-core path.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 
 namespace kde {
 namespace {
 
-constexpr int kBin = kCutoffBin;    // cells per bin side (= output tile side)
+constexpr int kBin = kCutoffBin;    // cells per output block side
 constexpr int kGroupThreads = kBin * kBin / 4;  // a point group: one thread per column, 4 rows
 constexpr int kGroups = 4;          // point groups per CTA (one bin)
 constexpr int kSortThreads = 256;   // 8 warps
@@ -208,13 +208,6 @@ __device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float 
   }
 }
 
-// Position in the sequence of batches of one bin: the rows of bins within
-// reach in order, each row's points in kBatch-point batches.
-struct BatchPos {
-  int qy;
-  uint32_t b, e;
-};
-
 // Shared-memory tables of one point group.
 struct GroupTables {
   float4 P[kBatch];
@@ -223,68 +216,55 @@ struct GroupTables {
   __align__(16) float KY[kBatch][kBin];
 };
 
-// The bin's work, for one kernel: group g of the CTA takes batches g, g+G,
-// g+2G, ... of the bin's sequence (fetching the next while computing the
-// current), and ends with the two-sum of its four cells in run.
+// The block's work, for one kernel.  The points that can reach the block are
+// the runs of the sort bins in its range, one run per bin row; their
+// concatenation is cut into kBatch-point batches, and group g of the CTA takes
+// batches g, g+G, g+2G, ... (fetching the next while computing the current)
+// and ends with the two-sum of its four cells in run.
 template <int KID, bool RADIAL>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
                                              int g, int tg, GroupTables& T, float2 (&run)[4]) {
-  const int nx = I.nx, ny = I.ny, R = I.R;
+  const int nx = I.nx, ny = I.ny;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
   // table role: column (and row) ej for points eq0 .. eq0 + kEvalPts - 1
   constexpr int kEvalPts = kBatch * kBin / kGroupThreads;
   static_assert(kGroupThreads % kBin == 0 && kBatch * kBin % kGroupThreads == 0, "table roles");
+  static_assert(kGroupThreads == kBatch, "one point per thread per batch");
   const int ej = tg % kBin, eq0 = (tg / kBin) * kEvalPts;
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
-  const int qy_end = min(by + R, I.nby - 1);
-  const int qx0 = max(bx - R, 0), qx1 = min(bx + R, I.nbx - 1);
-  auto next_row = [&](BatchPos& q) {  // first batch of the next non-empty row
-    while (q.b >= q.e && q.qy <= qy_end) {
-      const int row = I.bin_begin + q.qy * I.nbx;
-      q.b = start[row + qx0];
-      q.e = start[row + qx1 + 1];
-      ++q.qy;
-    }
-  };
-  auto skip = [&](BatchPos& q, int k) {  // move k batches on
-    while (k > 0 && q.b < q.e) {
-      const uint32_t rem = (q.e - q.b + kBatch - 1) / kBatch;
-      if ((uint32_t)k < rem) {
-        q.b += (uint32_t)k * kBatch;
-        k = 0;
-      } else {
-        k -= (int)rem;
-        q.b = q.e;
-        next_row(q);
-      }
-    }
-  };
+  // (a millionth of a bandwidth wider than the support: the points left out
+  // have |u| or |v| above 1 in FP32 too, so their factors are exactly zero)
+  const BinRange br = block_bins(I.cs, I.reach + 1e-6, I.inv_binw, I.nbx, I.nby, x0, y0, kBin);
+  if (range_empty(br)) return;
+  const int64_t total = range_total(start, I.bin_begin, I.nbx, br);
+  RunCursor cur;
+  cur.init(start, I.bin_begin, I.nbx, br);
+  constexpr int64_t kStride = (int64_t)kGroups * kBatch;
   auto group_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads)); };
-  BatchPos q = {max(by - R, 0), 0u, 0u};
-  next_row(q);
-  skip(q, g);
+  int64_t v = (int64_t)g * kBatch + tg;  // this thread's point of the group's current batch
   float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
   float wf = 0.f;
-  if (q.b < q.e && tg < (int)min((uint32_t)kBatch, q.e - q.b)) {
-    pf = P[q.b + tg];
-    wf = W[q.b + tg];
+  if (v < total) {
+    const int64_t p = cur.map(v);
+    pf = P[p];
+    wf = W[p];
   }
-  while (q.b < q.e) {
-    const int cnt = (int)min((uint32_t)kBatch, q.e - q.b);
+  for (int64_t b0 = (int64_t)g * kBatch; b0 < total; b0 += kStride, v += kStride) {
+    const int cnt = (int)min((int64_t)kBatch, total - b0);
     group_sync();  // the group's previous batch is consumed
     if (tg < cnt) {
       T.P[tg] = pf;
       T.W[tg] = wf;
     }
     group_sync();
-    skip(q, kGroups);
-    if (q.b < q.e && tg < (int)min((uint32_t)kBatch, q.e - q.b)) {  // next batch, in flight
-      pf = P[q.b + tg];
-      wf = W[q.b + tg];
+    if (v + kStride < total) {  // next batch, in flight
+      const int64_t p = cur.map(v + kStride);
+      pf = P[p];
+      wf = W[p];
     }
     // the lanes of a warp write consecutive words: conflict-free
 #pragma unroll 4
@@ -292,13 +272,13 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
       const int c = eq0 + k;
       if (c < cnt) {
         const float4 p = T.P[c];
-        const float u = (gxe.x - p.x) + (gxe.y - p.y), v = (gye.x - p.z) + (gye.y - p.w);
+        const float u = (gxe.x - p.x) + (gxe.y - p.y), w = (gye.x - p.z) + (gye.y - p.w);
         if (RADIAL) {
           T.KX[c][ej] = u * u;
-          T.KY[c][ej] = v * v;
+          T.KY[c][ej] = w * w;
         } else {
           T.KX[c][ej] = kfactor<KID>(u);
-          T.KY[c][ej] = T.W[c] * kfactor<KID>(v);
+          T.KY[c][ej] = T.W[c] * kfactor<KID>(w);
         }
       }
     }
@@ -310,12 +290,12 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   }
 }
 
-// One CTA per 16x16 output bin of some instance (blockIdx.x = global bin),
-// kGroups point groups of 64 threads: a dense bin's points are shared out
-// over the groups, whose (hi, lo) sums are added in group order at the end,
-// so results are reproducible.  Bins of 16 cells keep the cells a CTA
-// evaluates close to the support of the points it reads (a few cells at the
-// bandwidths of interest) and spread a dense region over more CTAs.
+// One CTA per 16x16-cell output block of some instance (blockIdx.x = global
+// block), kGroups point groups of 64 threads: a dense block's points are
+// shared out over the groups, whose (hi, lo) sums are added in group order at
+// the end, so results are reproducible.  Blocks of 16 cells spread a dense
+// region over many CTAs; the finer sort bins keep the points a block reads
+// close to those its cells' supports actually reach.
 __global__ void __launch_bounds__(kGroups * kGroupThreads)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
              const float* __restrict__ W, const uint32_t* __restrict__ start) {
@@ -324,11 +304,11 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (tab[mid].bin_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    if (tab[mid].out_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
   const CutInst& I = tab[lo];
-  const int local = blockIdx.x - I.bin_begin;
-  const int bx = local % I.nbx, by = local / I.nbx;
+  const int local = blockIdx.x - I.out_begin;
+  const int bx = local % I.obx, by = local / I.obx;
   const int g = threadIdx.x / kGroupThreads, tg = threadIdx.x % kGroupThreads;
   float2 run[4];
 #pragma unroll
@@ -381,15 +361,22 @@ int grid_for(int64_t n) {
 
 CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach, int bin) {
   CutoffGeom g;
+  g.bin = bin;
   g.nbx = (nx + bin - 1) / bin;
   g.nby = (ny + bin - 1) / bin;
   g.nbins = g.nbx * g.nby;
-  // bins a point can reach: its support plus half a cell, in bins of `bin` cells
-  g.R = (int)ceil((reach / cs + 1.0) / bin);
   g.inv_binw = 1.0 / (bin * cs);
   g.ext_x = nx * cs + reach;
   g.ext_y = ny * cs + reach;
   return g;
+}
+
+int cutoff_sort_bin(int nx, int ny, double reach_cells) {
+  // an output block reads about (16 + 2 reach + bin)^2 cells' points, of which
+  // (16 + 2 reach)^2 can reach it; finer bins mean more bins to sort
+  int bin = reach_cells <= 6.0 ? 4 : reach_cells <= 16.0 ? 8 : 16;
+  while (bin < 64 && ((int64_t)(nx + bin - 1) / bin) * ((ny + bin - 1) / bin) > (1 << 24)) bin *= 2;
+  return bin;
 }
 
 CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {

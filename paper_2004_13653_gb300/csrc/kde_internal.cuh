@@ -108,43 +108,114 @@ struct TcInst {
   int nbx, nby, bin_begin, tile_begin;
 };
 
-// Points of bin rows lo_by..hi_by, columns lo_bx..hi_bx can reach the 256 x 256
-// tile (tm, tn): every other point lies farther than `reach` (prepared units)
-// from each of the tile's cell centres along x or along y.  Used by both the
-// planning kernel and the contraction, so the two agree bit for bit.
+// Points of bin rows lo_by..hi_by, columns lo_bx..hi_bx can reach the block
+// of side x side cells whose first cell is (cx0, cy0): every other point lies
+// farther than `reach` (prepared units) from each of the block's cell centres
+// along x or along y.  Used by the kernels that plan work and those that do it,
+// so the two agree bit for bit.  An empty range has lo > hi.
 struct BinRange {
   int lo_bx, hi_bx, lo_by, hi_by;
 };
-__host__ __device__ inline BinRange tile_bins(double cs, double reach, double inv_binw, int nbx,
-                                              int nby, int tm, int tn) {
+__host__ __device__ inline BinRange block_bins(double cs, double reach, double inv_binw, int nbx,
+                                               int nby, int cx0, int cy0, int side) {
   BinRange r;
-  const double x0 = ((double)tm * 256 + 0.5) * cs - reach, x1 = ((double)tm * 256 + 255.5) * cs + reach;
-  const double y0 = ((double)tn * 256 + 0.5) * cs - reach, y1 = ((double)tn * 256 + 255.5) * cs + reach;
-  r.lo_bx = (int)fmax(0.0, floor(x0 * inv_binw));
+  const double x0 = ((double)cx0 + 0.5) * cs - reach, x1 = ((double)cx0 + side - 0.5) * cs + reach;
+  const double y0 = ((double)cy0 + 0.5) * cs - reach, y1 = ((double)cy0 + side - 0.5) * cs + reach;
+  r.lo_bx = (int)fmin((double)nbx, fmax(0.0, floor(x0 * inv_binw)));
   r.hi_bx = (int)fmin((double)(nbx - 1), floor(x1 * inv_binw));
-  r.lo_by = (int)fmax(0.0, floor(y0 * inv_binw));
+  r.lo_by = (int)fmin((double)nby, fmax(0.0, floor(y0 * inv_binw)));
   r.hi_by = (int)fmin((double)(nby - 1), floor(y1 * inv_binw));
   return r;
+}
+// the 256 x 256 tile (tm, tn) of the tensor-core paths
+__host__ __device__ inline BinRange tile_bins(double cs, double reach, double inv_binw, int nbx,
+                                              int nby, int tm, int tn) {
+  return block_bins(cs, reach, inv_binw, nbx, nby, tm * 256, tn * 256, 256);
+}
+
+// Walks the bin-row runs of a block's range (the points of bins lo_bx..hi_bx
+// of each row, contiguous in the sorted order) in increasing position order
+// and maps a position of their concatenation to an index of the sorted
+// points.  Positions must not decrease from call to call.
+struct RunCursor {
+  const uint32_t* start;
+  int row0, nbx, lo_bx, hi_bx, by, hi_by;
+  int64_t vr;         // position of the current run's first point
+  uint32_t ra, rb;    // the current run in the sorted points
+  __device__ __forceinline__ void load_run() {
+    const int row = row0 + by * nbx;
+    ra = __ldg(start + row + lo_bx);
+    rb = __ldg(start + row + hi_bx + 1);
+  }
+  // start: bin starts of the sort; row0: first bin of the instance; the range
+  // must not be empty
+  __device__ __forceinline__ void init(const uint32_t* start_, int row0_, int nbx_,
+                                       const BinRange& br) {
+    start = start_;
+    row0 = row0_;
+    nbx = nbx_;
+    lo_bx = br.lo_bx;
+    hi_bx = br.hi_bx;
+    by = br.lo_by;
+    hi_by = br.hi_by;
+    vr = 0;
+    load_run();
+  }
+  // index of position v (v below the range's total)
+  __device__ __forceinline__ int64_t map(int64_t v) {
+    while (v >= vr + (int64_t)(rb - ra) && by < hi_by) {
+      vr += rb - ra;
+      ++by;
+      load_run();
+    }
+    return (int64_t)ra + (v - vr);
+  }
+};
+// points in a non-empty range
+__device__ __forceinline__ int64_t range_total(const uint32_t* start, int row0, int nbx,
+                                               const BinRange& br) {
+  int64_t total = 0;
+  for (int by = br.lo_by; by <= br.hi_by; ++by) {
+    const int row = row0 + by * nbx;
+    total += __ldg(start + row + br.hi_bx + 1) - __ldg(start + row + br.lo_bx);
+  }
+  return total;
+}
+__host__ __device__ inline bool range_empty(const BinRange& br) {
+  return br.lo_bx > br.hi_bx || br.lo_by > br.hi_by;
 }
 
 // Work list of the block-sparse contraction: each tile's points (its bin
 // rows' runs, concatenated) cut into pieces of piece_len points; piece p of
-// all tiles is work item piece_begin[tile] + p and owns partial tile p of
-// `part` (256 x 256 floats, [j_local][i_local]).
+// a tile has id piece_begin[tile] + p and owns partial tile `id` of `part`
+// (256 x 256 floats, [j_local][i_local]).  The contraction takes the pieces
+// in schedule order: first every full piece (tile by tile), then the
+// shorter last pieces, longest first (tail_tile), dealt to the CTA pairs in
+// snake order so their loads come out even.  The schedule decides only
+// which CTA pair computes a piece, never what is summed or in which order.
 struct SparseCtl {
   const uint32_t* piece_begin;  // [tiles_total + 1], exclusive scan of pieces per tile
+  const uint32_t* full_begin;   // [tiles_total + 1], exclusive scan of full pieces per tile
+  const uint32_t* tail_tile;    // [tiles_total] tiles with a short last piece, longest first
   const uint32_t* tile_total;   // [tiles_total] points that can reach each tile
   float* part;                  // [max_pieces][256][256]
   int tiles_total, piece_len, max_pieces;
 };
+// Longest piece the planner makes.
+constexpr int kSparseMaxPiece = 32768;
 
+// An instance of the bin sort (cutoff or block-sparse) and, for the cutoff
+// path, of its evaluation.  Sort bins: nbx x nby bins of `bin` cells, keys
+// from bin_begin; output blocks (cutoff): obx x oby blocks of kCutoffBin
+// cells, CTAs from out_begin.
 struct CutInst {
   const float2* gxt;
   const float2* gyt;
   float* out;
   int64_t n, n_pad, prep_begin, cut_begin;  // point ranges (prepared / cutoff spaces)
-  double inv_binw, ext_x, ext_y, reach;     // reach: support radius in prepared units
-  int nbx, nby, R, bin_begin, nx, ny, kid;
+  double inv_binw, ext_x, ext_y, reach, cs; // reach: support radius, cs: cell side (prepared units)
+  int nbx, nby, bin_begin, nx, ny, kid;
+  int obx, oby, out_begin;
   float scale;
 };
 
@@ -191,15 +262,20 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t m, 
 
 // Path (c): binned cutoff evaluation of the compact kernels.
 struct CutoffGeom {
-  int nbx, nby, nbins, R;
+  int nbx, nby, nbins, bin;
   double inv_binw, ext_x, ext_y;
 };
-// Bin sides in cells: the cutoff path's output tiles, and the block-sparse
-// tensor-core work list's bins.
+// Block sides in cells: the cutoff path's output blocks (one CTA each), and
+// the block-sparse tensor-core work list's sort bins.
 constexpr int kCutoffBin = 16;
 constexpr int kSparseBin = 32;
-// cs: cell side in prepared units; reach: support radius in prepared units.
+// Sort bins of `bin` cells; cs: cell side in prepared units; reach: support
+// radius in prepared units.
 CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach, int bin);
+// The cutoff path's sort-bin side for a support of reach_cells cells: small
+// enough that an output block reads little beyond its support's reach, large
+// enough that the number of bins stays bounded.
+int cutoff_sort_bin(int nx, int ny, double reach_cells);
 struct CutoffScratch {
   uint32_t* keys[2];
   uint32_t* vals[2];
@@ -220,7 +296,8 @@ CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
 cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
                             const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                             CutoffScratch ws, cudaStream_t s);
-// The cutoff evaluation of the first ninst instances (bins 0..cut_bins-1).
+// The cutoff evaluation of the first ninst instances (output blocks
+// 0..cut_bins-1, one CTA each).
 cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
                                const CutoffScratch& ws, cudaStream_t s);
 
@@ -279,11 +356,13 @@ cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_it
 // list (their count is read on the device).
 cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
                            const SparseCtl* sp, CallScalars* err, cudaStream_t s);
-// Block-sparse work list: tile totals, pieces per tile, their exclusive scan.
+// Block-sparse work list: tile totals, pieces and full pieces per tile and
+// their exclusive scans, the tail pieces ordered longest first.  npieces and
+// nfull are [tiles_total + 1] scratch words.
 size_t sparse_scan_words(int tiles_total);
 cudaError_t launch_sparse_plan(const TcInst* tab, int ninst, const SparseCtl& sp,
-                               uint32_t* npieces, uint32_t* scan_temp, CallScalars* err,
-                               cudaStream_t s);
+                               uint32_t* npieces, uint32_t* nfull, uint32_t* scan_temp,
+                               CallScalars* err, cudaStream_t s);
 // Sum each tile's piece partials in order into the instance outputs.
 cudaError_t launch_sparse_reduce(const TcInst* tab, int ninst, const SparseCtl& sp,
                                  cudaStream_t s);

@@ -5,12 +5,16 @@
 // 128 x-factors and 64 (weighted) y-factors of every point in shared memory,
 // each evaluated once, then every thread accumulates the outer products of its
 // 8 x 8 cells (columns 4t..4t+3 and 64+4t..64+4t+3, eight consecutive rows):
-// per point two 16-byte reads of each table and 64 FMAs.  Points
-// arrive in tiles of 256; each thread sums one tile in registers and adds that
-// partial into a (hi, lo) running sum in shared memory with an error-free
-// two-sum, so the result does not degrade with the number of points a cell
-// sees.  The factors and the order of every sum are those of a thread that
-// evaluates its own factors, so the result does not depend on the tabulation.
+// per point two 16-byte reads of each table and 64 FMAs.  The tables are
+// double-buffered, so one barrier per batch separates a batch's tabulation
+// from its use; each point's table reads are issued while the previous
+// point's FMAs run, and the next batch's points are loaded into registers
+// while the current batch is accumulated.  Points arrive in tiles of 256; each thread sums one tile
+// in registers and adds that partial into a (hi, lo) running sum in shared
+// memory with an error-free two-sum, so the result does not degrade with the
+// number of points a cell sees.  The factors and the order of every sum are
+// those of a thread that evaluates its own factors, so the result does not
+// depend on the tabulation.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 
@@ -21,7 +25,23 @@ constexpr int kThreads = 128;  // 16 (x) x 8 (y) threads, 8 x 8 cells each
 constexpr int kTileX = 128;    // cells along x per CTA
 constexpr int kTileY = 64;     // cells along y per CTA
 constexpr int kPtsTile = 256;  // points per register partial (two-sum cadence)
-constexpr int kBatch = 32;     // points per factor table (two CTAs fit an SM)
+constexpr int kBatch = 32;     // points per factor table
+constexpr int kTable = kBatch * (kTileX + kTileY);  // floats per table buffer
+
+struct TableRow {
+  float4 xa, xb, ya, yb;
+};
+
+__device__ __forceinline__ TableRow table_row(const float* KX, const float* KY, int q, int tx,
+                                              int ty) {
+  // columns 4tx.. and 64+4tx..: a half-warp reads 256 contiguous bytes
+  TableRow r;
+  r.xa = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 4);
+  r.xb = *reinterpret_cast<const float4*>(KX + q * kTileX + 64 + tx * 4);
+  r.ya = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8);
+  r.yb = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8 + 4);
+  return r;
+}
 
 template <int KID>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -29,13 +49,9 @@ __global__ void __launch_bounds__(kThreads, 2)
            int64_t per_split, const float2* __restrict__ gxt, const float2* __restrict__ gyt,
            int nx, int ny, float scale, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* KX = reinterpret_cast<float*>(smem);                         // [kBatch][kTileX]
-  float* KY = KX + kBatch * kTileX;                                   // [kBatch][kTileY]
-  float2* run = reinterpret_cast<float2*>(KY + kBatch * kTileY);      // [64][kThreads]
-  float4* sp = reinterpret_cast<float4*>(run + 64 * kThreads);        // [kBatch]
-  float* sw = reinterpret_cast<float*>(sp + kBatch);                  // [kBatch]
-
-  const int tid = threadIdx.x;
+  float* tables = reinterpret_cast<float*>(smem);                        // [2][kTable]
+  float2* run = reinterpret_cast<float2*>(tables + 2 * kTable);          // [64][kThreads]
+  const int tid = threadIdx.x, lane = tid & 31;
   const int tx = tid & 15, ty = tid >> 4;
   const int cx0 = blockIdx.x * kTileX, cy0 = blockIdx.y * kTileY;
 #pragma unroll
@@ -46,10 +62,26 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (p_end > n_pad) p_end = n_pad;
   // factor roles: x column tid; y row frow for points fq0 .. fq0 + kBatch/2 - 1
   static_assert(kThreads == kTileX && kThreads == 2 * kTileY, "factor roles");
+  static_assert(kPtsTile % kBatch == 0 && kBatch == 32, "one point per lane per batch");
   const float2 gxr = gxt[min(cx0 + tid, nx - 1)];
   const int frow = tid & (kTileY - 1), fq0 = (tid / kTileY) * (kBatch / 2);
   const float2 gyr = gyt[min(cy0 + frow, ny - 1)];
 
+  // Every warp holds the points of the next batch in registers, one per
+  // lane, loaded while the current batch is accumulated (the global-memory
+  // latency hides behind a whole batch); the tabulation broadcasts them with
+  // shuffles.
+  float4 nP;
+  float nW;
+  auto fetch = [&](int64_t first) {
+    const int64_t p = first + lane;
+    const bool in = p < p_end;
+    nP = in ? pts[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    nW = in ? wts[p] : 0.f;
+  };
+  fetch(p_begin);
+
+  int buf = 0;
   for (int64_t base = p_begin; base < p_end; base += kPtsTile) {
     float acc[8][8];
 #pragma unroll
@@ -57,47 +89,41 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int a = 0; a < 8; ++a) acc[b][a] = 0.f;
 
-    for (int bb = 0; bb < kPtsTile; bb += kBatch) {
-      __syncthreads();  // the previous batch's tables are consumed
-      if (tid < kBatch) {
-        const int64_t p = base + bb + tid;
-        if (p < p_end) {
-          sp[tid] = pts[p];
-          sw[tid] = wts[p];
-        } else {
-          sp[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-          sw[tid] = 0.f;
-        }
-      }
-      __syncthreads();
-      // x-factors: thread = column, all points of the batch; y-factors:
-      // thread = row, half of the points (consecutive lanes write consecutive
-      // words, so the stores are conflict-free)
+    for (int bb = 0; bb < kPtsTile; bb += kBatch, buf ^= 1) {
+      float* KX = tables + buf * kTable;  // [kBatch][kTileX]
+      float* KY = KX + kBatch * kTileX;   // [kBatch][kTileY]
+      const float4 P = nP;
+      const float W = nW;
+      // This buffer was last read two batches ago, before the barrier of the
+      // previous batch, which every thread has passed.
 #pragma unroll 8
       for (int q = 0; q < kBatch; ++q) {
-        const float4 P = sp[q];
-        KX[q * kTileX + tid] = kfactor<KID>((gxr.x - P.x) + (gxr.y - P.y));
+        const float px = __shfl_sync(0xffffffffu, P.x, q), pxl = __shfl_sync(0xffffffffu, P.y, q);
+        KX[q * kTileX + tid] = kfactor<KID>((gxr.x - px) + (gxr.y - pxl));
       }
 #pragma unroll 8
       for (int k = 0; k < kBatch / 2; ++k) {
         const int q = fq0 + k;
-        const float4 P = sp[q];
-        KY[q * kTileY + frow] = sw[q] * kfactor<KID>((gyr.x - P.z) + (gyr.y - P.w));
+        const float py = __shfl_sync(0xffffffffu, P.z, q), pyl = __shfl_sync(0xffffffffu, P.w, q);
+        const float w = __shfl_sync(0xffffffffu, W, q);
+        KY[q * kTileY + frow] = w * kfactor<KID>((gyr.x - py) + (gyr.y - pyl));
       }
       __syncthreads();
+      fetch(base + bb + kBatch);
+      TableRow cur = table_row(KX, KY, 0, tx, ty);
 #pragma unroll 2
       for (int q = 0; q < kBatch; ++q) {
-        // columns 4tx.. and 64+4tx..: a half-warp reads 256 contiguous bytes
-        const float4 xa = *reinterpret_cast<const float4*>(KX + q * kTileX + tx * 4);
-        const float4 xb = *reinterpret_cast<const float4*>(KX + q * kTileX + 64 + tx * 4);
-        const float4 ya = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8);
-        const float4 yb = *reinterpret_cast<const float4*>(KY + q * kTileY + ty * 8 + 4);
-        const float kx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-        const float ky[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+        TableRow nxt = cur;
+        if (q + 1 < kBatch) nxt = table_row(KX, KY, q + 1, tx, ty);
+        const float kx[8] = {cur.xa.x, cur.xa.y, cur.xa.z, cur.xa.w,
+                             cur.xb.x, cur.xb.y, cur.xb.z, cur.xb.w};
+        const float ky[8] = {cur.ya.x, cur.ya.y, cur.ya.z, cur.ya.w,
+                             cur.yb.x, cur.yb.y, cur.yb.z, cur.yb.w};
 #pragma unroll
         for (int b = 0; b < 8; ++b)
 #pragma unroll
           for (int a = 0; a < 8; ++a) acc[b][a] = fmaf(kx[a], ky[b], acc[b][a]);
+        cur = nxt;
       }
     }
 #pragma unroll
@@ -125,9 +151,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-constexpr size_t kSmem = kBatch * (kTileX + kTileY) * sizeof(float) +
-                         64 * kThreads * sizeof(float2) +
-                         kBatch * (sizeof(float4) + sizeof(float));
+// 48 KB of tables + 64 KB of running sums: two CTAs per SM
+constexpr size_t kSmem = 2 * kTable * sizeof(float) + 64 * kThreads * sizeof(float2);
 
 template <int KID>
 cudaError_t launch_kid(const float4* pts, const float* wts, int64_t n_pad, const float2* gxt,

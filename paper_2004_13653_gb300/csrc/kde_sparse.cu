@@ -14,7 +14,10 @@
 // within reach, i.e. one contiguous run of sorted points per bin row.  This
 // file builds the work list (points per tile, cut into pieces of a fixed
 // length, and the exclusive scan of the pieces per tile) and sums each
-// tile's piece partials, in piece order, into the output.
+// tile's piece partials, in piece order, into the output.  The pieces of a
+// tile all hold piece_len points except its last; the schedule lists the full
+// pieces first and then the last pieces by decreasing length, so that dealing
+// them to the CTA pairs in snake order balances the pairs' work.
 #include "kde_internal.cuh"
 
 namespace kde {
@@ -29,15 +32,17 @@ __device__ __forceinline__ int inst_of_tile(const TcInst* __restrict__ tab, int 
   return a;
 }
 
-// One thread per tile: the points its bin rows hold, and its piece count.
-// npieces has tiles_total + 1 entries; the last is zero so that the exclusive
-// scan ends with the total.
+// One thread per tile: the points its bin rows hold, its piece count and its
+// count of full pieces.  npieces and nfull have tiles_total + 1 entries; the
+// last are zero so that the exclusive scans end with the totals.
 __global__ void k_sparse_totals(const TcInst* __restrict__ tab, int ninst, SparseCtl sp,
-                                uint32_t* __restrict__ tile_total, uint32_t* __restrict__ npieces) {
+                                uint32_t* __restrict__ tile_total, uint32_t* __restrict__ npieces,
+                                uint32_t* __restrict__ nfull) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t > sp.tiles_total) return;
   if (t == sp.tiles_total) {
     npieces[t] = 0;
+    nfull[t] = 0;
     return;
   }
   const TcInst& I = tab[inst_of_tile(tab, ninst, t)];
@@ -51,6 +56,65 @@ __global__ void k_sparse_totals(const TcInst* __restrict__ tab, int ninst, Spars
   }
   tile_total[t] = (uint32_t)total;
   npieces[t] = (uint32_t)((total + sp.piece_len - 1) / sp.piece_len);
+  nfull[t] = (uint32_t)(total / sp.piece_len);
+}
+
+// Lists the tiles whose last piece is short, longest first: a counting sort
+// on the piece's length in 512 classes (64-point MMA stages for the longest
+// pieces the planner makes; one CTA; the order among tails of the same class
+// is whatever the atomics give, which changes no result).
+constexpr int kTailClasses = 512;
+constexpr int kTailKeys = kTailClasses + 1;  // keys 1 .. kTailClasses
+constexpr int kTailThreads = 1024;
+static_assert(kTailKeys <= kTailThreads, "one key per thread in the scan");
+
+// class of a short piece of rem points, 1 <= rem < L
+__device__ __forceinline__ int tail_key(uint32_t rem, uint32_t L) {
+  return 1 + (int)(((uint64_t)(rem - 1) * kTailClasses) / L);
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_sparse_tails(SparseCtl sp) {
+  __shared__ uint32_t cnt[kTailKeys];
+  __shared__ uint32_t warp_sum[kTailThreads / 32];
+  const int tid = threadIdx.x;
+  const uint32_t L = (uint32_t)sp.piece_len;
+  if (tid < kTailKeys) cnt[tid] = 0;
+  __syncthreads();
+  for (int t = tid; t < sp.tiles_total; t += kTailThreads) {
+    const uint32_t rem = __ldg(sp.tile_total + t) % L;
+    if (rem) atomicAdd(&cnt[tail_key(rem, L)], 1u);
+  }
+  __syncthreads();
+  // exclusive scan with the longest key first: thread r holds key kTailKeys-1-r
+  const int key = kTailKeys - 1 - tid;
+  const uint32_t c = tid < kTailKeys ? cnt[key] : 0u;
+  uint32_t v = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if ((tid & 31) >= o) v += n;
+  }
+  if ((tid & 31) == 31) warp_sum[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    uint32_t w = warp_sum[tid];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n = __shfl_up_sync(0xffffffffu, w, o);
+      if (tid >= o) w += n;
+    }
+    warp_sum[tid] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  const uint32_t before = v - c + ((tid >> 5) ? warp_sum[(tid >> 5) - 1] : 0u);
+  __syncthreads();
+  if (tid < kTailKeys) cnt[key] = before;  // now the cursor of each key
+  __syncthreads();
+  uint32_t* tail = const_cast<uint32_t*>(sp.tail_tile);
+  for (int t = tid; t < sp.tiles_total; t += kTailThreads) {
+    const uint32_t rem = __ldg(sp.tile_total + t) % L;
+    if (rem) tail[atomicAdd(&cnt[tail_key(rem, L)], 1u)] = t;
+  }
 }
 
 // out cell (i, j) of tile t = sum over the tile's pieces, in order.  Grid:
@@ -81,17 +145,23 @@ size_t sparse_scan_words(int tiles_total) {
 }
 
 cudaError_t launch_sparse_plan(const TcInst* tab, int ninst, const SparseCtl& sp,
-                               uint32_t* npieces, uint32_t* scan_temp, CallScalars* err,
-                               cudaStream_t s) {
+                               uint32_t* npieces, uint32_t* nfull, uint32_t* scan_temp,
+                               CallScalars* err, cudaStream_t s) {
   (void)err;
+  if (sp.piece_len <= 0) return cudaErrorInvalidValue;
   const int m = sp.tiles_total + 1;
-  k_sparse_totals<<<(m + 255) / 256, 256, 0, s>>>(tab, ninst, sp,
-                                                  const_cast<uint32_t*>(sp.tile_total), npieces);
+  k_sparse_totals<<<(m + 255) / 256, 256, 0, s>>>(
+      tab, ninst, sp, const_cast<uint32_t*>(sp.tile_total), npieces, nfull);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_exclusive_scan(npieces, const_cast<uint32_t*>(sp.piece_begin), m, 2048, scan_temp,
-                               s);
+  e = launch_exclusive_scan(npieces, const_cast<uint32_t*>(sp.piece_begin), m, 2048, scan_temp, s);
+  if (e != cudaSuccess) return e;
+  e = launch_exclusive_scan(nfull, const_cast<uint32_t*>(sp.full_begin), m, 2048, scan_temp, s);
+  if (e != cudaSuccess) return e;
+  k_sparse_tails<<<1, kTailThreads, 0, s>>>(sp);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_reduce(const TcInst* tab, int ninst, const SparseCtl& sp,

@@ -100,16 +100,27 @@ __device__ __forceinline__ Item pair_item(const TcInst* __restrict__ tab, int ni
   return r;
 }
 
-// Block-sparse work item `it`: the tile whose pieces contain it, the piece's
-// range of positions in the concatenation of the tile's bin-row runs.
+// Block-sparse work item at schedule position `pos`: full pieces first (tile
+// by tile), then the tiles' short last pieces, longest first.  Returns the
+// tile, the piece's range of positions in the concatenation of the tile's
+// bin-row runs, and the piece id (its partial slot).
 __device__ __forceinline__ Item sparse_item(const TcInst* __restrict__ tab, int ninst,
-                                            const SparseCtl& sp, int it) {
-  int lo = 0, hi = sp.tiles_total - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((int)__ldg(sp.piece_begin + mid) <= it) lo = mid; else hi = mid - 1;
+                                            const SparseCtl& sp, int pos) {
+  const int n_full = (int)__ldg(sp.full_begin + sp.tiles_total);
+  int t, p;
+  if (pos < n_full) {
+    int lo = 0, hi = sp.tiles_total - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((int)__ldg(sp.full_begin + mid) <= pos) lo = mid; else hi = mid - 1;
+    }
+    t = lo;
+    p = pos - (int)__ldg(sp.full_begin + t);
+  } else {
+    t = (int)__ldg(sp.tail_tile + (pos - n_full));
+    p = (int)(__ldg(sp.piece_begin + t + 1) - __ldg(sp.piece_begin + t)) - 1;
   }
-  const int t = lo;
+  const int it = (int)__ldg(sp.piece_begin + t) + p;
   int a = 0, b = ninst - 1;
   while (a < b) {
     const int mid = (a + b + 1) >> 1;
@@ -121,7 +132,7 @@ __device__ __forceinline__ Item sparse_item(const TcInst* __restrict__ tab, int 
   r.tm = local % r.I->tiles_m;
   r.tn = local / r.I->tiles_m;
   r.s = 0;
-  r.k_begin = (int64_t)(it - (int)__ldg(sp.piece_begin + t)) * sp.piece_len;
+  r.k_begin = (int64_t)p * sp.piece_len;
   const int64_t total = __ldg(sp.tile_total + t);
   r.vend = min(total, r.k_begin + (int64_t)sp.piece_len);
   r.nst = r.vend > r.k_begin ? (int)((r.vend - r.k_begin + kKS - 1) / kKS) : 0;
@@ -136,40 +147,15 @@ __device__ __forceinline__ Item get_item(const TcInst* __restrict__ tab, int nin
   return pair_item(tab, ninst, it);
 }
 
-// Walks the bin-row runs of one tile in increasing position order and maps a
-// position to an index of the sorted points.
-struct RunCursor {
-  const uint32_t* start;
-  int row0, nbx, lo_bx, hi_bx, by, hi_by;
-  int64_t vr;         // position of the current run's first point
-  uint32_t ra, rb;    // the current run in the sorted points
-  __device__ __forceinline__ void load_run() {
-    const int row = row0 + by * nbx;
-    ra = __ldg(start + row + lo_bx);
-    rb = __ldg(start + row + hi_bx + 1);
-  }
-  __device__ __forceinline__ void init(const TcInst& I, int tm, int tn) {
-    const BinRange br = tile_bins(I.cs, I.reach, I.inv_binw, I.nbx, I.nby, tm, tn);
-    start = I.start;
-    row0 = I.bin_begin;
-    nbx = I.nbx;
-    lo_bx = br.lo_bx;
-    hi_bx = br.hi_bx;
-    by = br.lo_by;
-    hi_by = br.hi_by;
-    vr = 0;
-    load_run();
-  }
-  // index of position v (v below the tile's total)
-  __device__ __forceinline__ int64_t map(int64_t v) {
-    while (v >= vr + (int64_t)(rb - ra) && by < hi_by) {
-      vr += rb - ra;
-      ++by;
-      load_run();
-    }
-    return (int64_t)ra + (v - vr);
-  }
-};
+// Schedule position of CTA pair c (of nc) in round r.  Dense items go round
+// robin; block-sparse items are listed longest first and are dealt in snake
+// order (forward in even rounds, backward in odd ones), so that the pairs'
+// sums of piece lengths come out nearly equal.  Every role of both CTAs
+// walks the same sequence.
+template <bool SPARSE>
+__device__ __forceinline__ int sched_pos(int r, int c, int nc) {
+  return r * nc + ((SPARSE && (r & 1)) ? nc - 1 - c : c);
+}
 
 template <bool SPLIT, bool SPARSE>
 __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
@@ -194,7 +180,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
   int n_items = n_items_arg;
   if (SPARSE) {  // the work list was built on the device by the preceding launches
     const int listed = (int)__ldg(sp.piece_begin + sp.tiles_total);
-    n_items = min(listed, sp.max_pieces);
+    // a list longer than the partial buffer is an error: no piece is computed
+    n_items = listed > sp.max_pieces ? 0 : listed;
     if (listed > sp.max_pieces && blockIdx.x == 0 && threadIdx.x == 0)
       atomicOr(&scal->err, kErrBadArg);
   }
@@ -233,7 +220,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
       uint32_t g = 0, mc = 0;
       bool ok = true;
       const uint32_t smem_base = smem_u32(smem);
-      for (int it = cluster; ok && it < n_items; it += n_clusters) {
+      for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+           it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
         const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
         const int CS = itm.I->chunk_stages;
         for (int st = 0; ok && st < itm.nst; ++st, ++g) {
@@ -274,7 +262,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
     // --------------------------------------------------------- point loader
     uint32_t g = 0;
     bool ok = true, negative = false;
-    for (int it = cluster; ok && it < n_items; it += n_clusters) {
+    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const float wmax = __uint_as_float(I.scal->wmax_bits);
@@ -282,7 +271,9 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
       const float2 cx = I.gxt[min(itm.tm * 256 + (int)rank * kRows + kRows / 2, I.nx - 1)];
       const float2 cy = I.gyt[min(itm.tn * 256 + (int)rank * kRows + kRows / 2, I.ny - 1)];
       RunCursor cur;
-      if (SPARSE) cur.init(I, itm.tm, itm.tn);
+      if (SPARSE)  // items exist only for tiles whose range holds points
+        cur.init(I.start, I.bin_begin, I.nbx,
+                 tile_bins(I.cs, I.reach, I.inv_binw, I.nbx, I.nby, itm.tm, itm.tn));
       for (int st = 0; ok && st < itm.nst; st += kGroup) {
         const int ng = min(kGroup, itm.nst - st);
         float4 P[kGroup][2];
@@ -337,7 +328,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
     const uint32_t accempty_leader = map_to_rank(smem_u32(accempty), 0);
     uint32_t dc = 0;
     bool ok = true;
-    for (int it = cluster; ok && it < n_items; it += n_clusters) {
+    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const int nx = I.nx, ny = I.ny, CS = I.chunk_stages;
@@ -416,7 +408,8 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
     for (int s = 0; s < C::kStages; ++s) full_leader[s] = map_to_rank(smem_u32(&full[s]), 0);
     uint32_t g = 0;
     bool ok = true;
-    for (int it = cluster; ok && it < n_items; it += n_clusters) {
+    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       float gv;
