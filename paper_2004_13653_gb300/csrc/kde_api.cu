@@ -181,7 +181,7 @@ struct InstPlan {
   int path;
   int splits;
   int64_t n_pad, prep_begin;
-  size_t off_gxt, off_gyt, off_part;
+  size_t off_gxt, off_gyt, off_part, off_run;  // off_run: SIMT running sums
   // tensor-core path
   int tiles_m, tiles_n, items;
   int64_t per_split;
@@ -214,7 +214,8 @@ struct BatchPlan {
   bool host_pts = false, host_w = false, host_out = false;
   size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
   size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
-      off_co_spts, off_co_sw, off_hxy, off_hw, off_hout, total;
+      off_co_spts, off_co_sw, off_co_order, off_co_totals, off_co_ocount, off_hxy, off_hw,
+      off_hout, total;
 };
 
 int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory, BatchPlan* P) {
@@ -419,6 +420,8 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     I.off_gxt = take(sizeof(float2) * (size_t)A[k].nx);
     I.off_gyt = take(sizeof(float2) * (size_t)A[k].ny);
     I.off_part = I.splits > 1 ? take(sizeof(float) * (size_t)A[k].nx * A[k].ny * I.splits) : 0;
+    I.off_run = I.path == KDE_PATH_SIMT_FP32 ? take(simt_scratch_bytes(A[k].nx, A[k].ny, I.splits))
+                                             : 0;
   }
   if (P->n_cut || P->sparse) {
     const size_t u = sizeof(uint32_t);
@@ -432,6 +435,9 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     P->off_co_start = take(u * ((size_t)P->total_bins + 1));
     P->off_co_spts = take(sizeof(float4) * (size_t)P->cut_m);
     P->off_co_sw = take(sizeof(float) * (size_t)P->cut_m);
+    P->off_co_order = take(u * (size_t)std::max<int64_t>(P->cut_bins, 1));
+    P->off_co_totals = take(u * (size_t)std::max<int64_t>(P->cut_bins, 1));
+    P->off_co_ocount = take(u * 2 * kCutOrderKeys);
   }
   if (P->sparse) {
     const size_t u = sizeof(uint32_t);
@@ -688,6 +694,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     cs.start = reinterpret_cast<uint32_t*>(base + P.off_co_start);
     cs.spts = reinterpret_cast<float4*>(base + P.off_co_spts);
     cs.sw = reinterpret_cast<float*>(base + P.off_co_sw);
+    cs.order = reinterpret_cast<uint32_t*>(base + P.off_co_order);
+    cs.totals = reinterpret_cast<uint32_t*>(base + P.off_co_totals);
+    cs.ocount = reinterpret_cast<uint32_t*>(base + P.off_co_ocount);
     KDE_CUDA(launch_bin_sort(d_cut, (int)cut.size(), P.cut_m, P.total_bins, pts, wts, P.cz, cs, s),
              "bin sort");
   }
@@ -717,7 +726,8 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     const InstPlan& I = P.in[k];
     if (I.path != KDE_PATH_SIMT_FP32) continue;
     KDE_CUDA(launch_simt(kid_of(&A[k]), prep[k].pts, prep[k].wts, I.n_pad, prep[k].gxt,
-                         prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k), part_of(k), s),
+                         prep[k].gyt, A[k].nx, A[k].ny, I.splits, compact_scale(k),
+                         reinterpret_cast<float2*>(base + I.off_run), part_of(k), s),
              "SIMT direct sum");
   }
   if (P.n_cut)

@@ -9,8 +9,8 @@
 // in sorted order, a batch of 64 at a time: for each batch a point group
 // tabulates the x and y kernel factors of its 16 columns and 16 rows in shared
 // memory, and each thread adds the outer products into its four cells.
-// Nothing is accumulated with atomics, and the order of every sum is fixed,
-// so results are reproducible bit for bit.  The same sort, with 32-cell bins
+// The blocks run heaviest first.  Nothing is accumulated with atomics, and
+// the order of every sum is fixed, so results are reproducible bit for bit.  The same sort, with 32-cell bins
 // and a wider reach, orders the points of the block-sparse tensor-core path.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
@@ -208,6 +208,87 @@ __device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float 
   }
 }
 
+// The sort bins whose points can reach output block (bx, by): a millionth of
+// a bandwidth wider than the support, so the points left out have |u| or |v|
+// above 1 in FP32 too and their factors are exactly zero.
+__device__ __forceinline__ BinRange output_block_bins(const CutInst& I, int bx, int by) {
+  return block_bins(I.cs, I.reach + 1e-6, I.inv_binw, I.nbx, I.nby, bx * kBin, by * kBin, kBin);
+}
+
+// The instance of global output block blk, and the block's position in it.
+__device__ __forceinline__ const CutInst& output_block(const CutInst* __restrict__ tab, int ninst,
+                                                       int blk, int& bx, int& by) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].out_begin <= blk) lo = mid; else hi = mid - 1;
+  }
+  const CutInst& I = tab[lo];
+  const int local = blk - I.out_begin;
+  bx = local % I.obx;
+  by = local / I.obx;
+  return I;
+}
+
+// Weight class of a block from the points within its reach (larger is
+// heavier): two classes per power of two.
+__device__ __forceinline__ int weight_key(uint32_t total) {
+  if (total == 0) return 0;
+  const int b = 31 - __clz(total);
+  return 1 + 2 * b + (b >= 1 ? (int)((total >> (b - 1)) & 1u) : 0);
+}
+
+// Points within reach of each output block, and the count of blocks per
+// weight class.  The rows' runs are read two at a time so their loads overlap.
+__global__ void k_cut_block_totals(const CutInst* __restrict__ tab, int ninst,
+                                   const uint32_t* __restrict__ start, int nblocks,
+                                   uint32_t* __restrict__ totals, uint32_t* __restrict__ ocount) {
+  const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= nblocks) return;
+  int bx, by;
+  const CutInst& I = output_block(tab, ninst, blk, bx, by);
+  const BinRange br = output_block_bins(I, bx, by);
+  uint32_t total = 0;
+  if (!range_empty(br)) {
+    int r = br.lo_by;
+    for (; r + 1 <= br.hi_by; r += 2) {
+      const uint32_t* a = start + I.bin_begin + r * I.nbx;
+      const uint32_t* b = a + I.nbx;
+      const uint32_t a0 = __ldg(a + br.lo_bx), a1 = __ldg(a + br.hi_bx + 1);
+      const uint32_t b0 = __ldg(b + br.lo_bx), b1 = __ldg(b + br.hi_bx + 1);
+      total += (a1 - a0) + (b1 - b0);
+    }
+    if (r <= br.hi_by) {
+      const uint32_t* a = start + I.bin_begin + r * I.nbx;
+      total += __ldg(a + br.hi_bx + 1) - __ldg(a + br.lo_bx);
+    }
+  }
+  totals[blk] = total;
+  atomicAdd(&ocount[weight_key(total)], 1u);
+}
+
+// The output blocks in decreasing weight class (a counting sort; within a
+// class the order is whatever the atomics give).  Each block computes only its
+// own cells, so the order changes the schedule, never a result: the heaviest
+// blocks (dense clusters) start first instead of wherever raster order puts
+// them.
+__global__ void k_cut_order_scatter(const uint32_t* __restrict__ totals, int nblocks,
+                                    uint32_t* __restrict__ ocount, uint32_t* __restrict__ order) {
+  __shared__ uint32_t first[kCutOrderKeys];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int k = kCutOrderKeys - 1; k >= 0; --k) {
+      first[k] = acc;
+      acc += ocount[k];
+    }
+  }
+  __syncthreads();
+  const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= nblocks) return;
+  const int key = weight_key(__ldg(totals + blk));
+  order[first[key] + atomicAdd(&ocount[kCutOrderKeys + key], 1u)] = (uint32_t)blk;
+}
+
 // Shared-memory tables of one point group.
 struct GroupTables {
   float4 P[kBatch];
@@ -225,7 +306,8 @@ template <int KID, bool RADIAL>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
-                                             int g, int tg, GroupTables& T, float2 (&run)[4]) {
+                                             int64_t total, int g, int tg, GroupTables& T,
+                                             float2 (&run)[4]) {
   const int nx = I.nx, ny = I.ny;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
@@ -236,11 +318,8 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   const int ej = tg % kBin, eq0 = (tg / kBin) * kEvalPts;
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
-  // (a millionth of a bandwidth wider than the support: the points left out
-  // have |u| or |v| above 1 in FP32 too, so their factors are exactly zero)
-  const BinRange br = block_bins(I.cs, I.reach + 1e-6, I.inv_binw, I.nbx, I.nby, x0, y0, kBin);
-  if (range_empty(br)) return;
-  const int64_t total = range_total(start, I.bin_begin, I.nbx, br);
+  if (total == 0) return;
+  const BinRange br = output_block_bins(I, bx, by);
   RunCursor cur;
   cur.init(start, I.bin_begin, I.nbx, br);
   constexpr int64_t kStride = (int64_t)kGroups * kBatch;
@@ -298,17 +377,14 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
 // close to those its cells' supports actually reach.
 __global__ void __launch_bounds__(kGroups * kGroupThreads)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
-             const float* __restrict__ W, const uint32_t* __restrict__ start) {
+             const float* __restrict__ W, const uint32_t* __restrict__ start,
+             const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals) {
   __shared__ GroupTables tables[kGroups];
   __shared__ float2 part[kGroups][kGroupThreads][4];
-  int lo = 0, hi = ninst - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tab[mid].out_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
-  const CutInst& I = tab[lo];
-  const int local = blockIdx.x - I.out_begin;
-  const int bx = local % I.obx, by = local / I.obx;
+  int bx, by;
+  const int blk = (int)__ldg(order + blockIdx.x);
+  const CutInst& I = output_block(tab, ninst, blk, bx, by);
+  const int64_t total = __ldg(totals + blk);
   const int g = threadIdx.x / kGroupThreads, tg = threadIdx.x % kGroupThreads;
   float2 run[4];
 #pragma unroll
@@ -317,10 +393,10 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
   switch (I.kid) {
 #define KDE_CUT(K)                                                                      \
   case K:                                                                               \
-    cutoff_group<K, false>(I, P, W, start, bx, by, g, tg, T, run);                      \
+    cutoff_group<K, false>(I, P, W, start, bx, by, total, g, tg, T, run);               \
     break;                                                                              \
   case kRadial + K:                                                                     \
-    cutoff_group<K, true>(I, P, W, start, bx, by, g, tg, T, run);                       \
+    cutoff_group<K, true>(I, P, W, start, bx, by, total, g, tg, T, run);                \
     break;
     KDE_CUT(KDE_UNIFORM)
     KDE_CUT(KDE_TRIANGULAR)
@@ -426,9 +502,15 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
 cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
                                const CutoffScratch& ws, cudaStream_t s) {
   if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
-  k_cutoff<<<(unsigned)cut_bins, kGroups * kGroupThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw,
-                                                                   ws.start);
-  note_launches(1);
+  if (cut_bins > 0x7fffffff) return cudaErrorInvalidValue;
+  const int nb = (int)cut_bins, grid = (nb + 255) / 256;
+  cudaError_t e = cudaMemsetAsync(ws.ocount, 0, sizeof(uint32_t) * 2 * kCutOrderKeys, s);
+  if (e != cudaSuccess) return e;
+  k_cut_block_totals<<<grid, 256, 0, s>>>(tab, ninst, ws.start, nb, ws.totals, ws.ocount);
+  k_cut_order_scatter<<<grid, 256, 0, s>>>(ws.totals, nb, ws.ocount, ws.order);
+  k_cutoff<<<(unsigned)nb, kGroups * kGroupThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw,
+                                                             ws.start, ws.order, ws.totals);
+  note_launches(3);
   return cudaGetLastError();
 }
 

@@ -171,16 +171,6 @@ struct RunCursor {
     return (int64_t)ra + (v - vr);
   }
 };
-// points in a non-empty range
-__device__ __forceinline__ int64_t range_total(const uint32_t* start, int row0, int nbx,
-                                               const BinRange& br) {
-  int64_t total = 0;
-  for (int by = br.lo_by; by <= br.hi_by; ++by) {
-    const int row = row0 + by * nbx;
-    total += __ldg(start + row + br.hi_bx + 1) - __ldg(start + row + br.lo_bx);
-  }
-  return total;
-}
 __host__ __device__ inline bool range_empty(const BinRange& br) {
   return br.lo_bx > br.hi_bx || br.lo_by > br.hi_by;
 }
@@ -247,9 +237,12 @@ cudaError_t launch_prepare(const PrepInst* tab, int ninst, int64_t total_pad, in
                            cudaStream_t s);
 
 // Path (a): FP32 SIMT direct sum into part[S][ny][nx] (scaled).
+// scratch: simt_scratch_bytes(nx, ny, splits) of device memory for the
+// running sums, or nullptr to keep them in shared memory (fewer CTAs per SM).
+size_t simt_scratch_bytes(int nx, int ny, int splits);
 cudaError_t launch_simt(int kid, const float4* pts, const float* wts, int64_t n_pad,
                         const float2* gxt, const float2* gyt, int nx, int ny, int splits,
-                        float scale, float* part, cudaStream_t s);
+                        float scale, float2* scratch, float* part, cudaStream_t s);
 
 // Sum each instance's S partial grids in fixed order (s = 0, 1, ...).
 cudaError_t launch_reduce(const ReduceInst* tab, int ninst, int64_t total_cells, cudaStream_t s);
@@ -285,7 +278,12 @@ struct CutoffScratch {
   uint32_t* start;  // [total bins + 1]
   float4* spts;     // points in bin order
   float* sw;
+  uint32_t* order;  // [cutoff output blocks] the blocks, heaviest first
+  uint32_t* totals; // [cutoff output blocks] points within reach of each block
+  uint32_t* ocount; // [2 * kCutOrderKeys] per-key block counts and cursors
 };
+// Weight classes of the cutoff path's output blocks (by points within reach).
+constexpr int kCutOrderKeys = 66;
 struct CutoffSizes {
   int nchunks, passes;
   size_t hist_words, scan_words;

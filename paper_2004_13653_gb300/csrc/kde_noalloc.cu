@@ -151,7 +151,7 @@ extern "C" int kde_grid_noalloc(const double* points, const float* weights, int6
     e = launch_prepare(reinterpret_cast<const PrepInst*>(base + off_tab), 1, n_pad,
                        nx > ny ? nx : ny, s);
   if (e == cudaSuccess)  // one point split: the kernel writes `out` directly
-    e = launch_simt(kernel_id, q.pts, q.wts, n_pad, q.gxt, q.gyt, nx, ny, 1, scale, out, s);
+    e = launch_simt(kernel_id, q.pts, q.wts, n_pad, q.gxt, q.gyt, nx, ny, 1, scale, nullptr, out, s);
   if (e != cudaSuccess) {
     char msg[256];
     snprintf(msg, sizeof(msg), "kde_grid_noalloc: %s", cudaGetErrorString(e));

@@ -9,10 +9,11 @@
 // double-buffered, so one barrier per batch separates a batch's tabulation
 // from its use; each point's table reads are issued while the previous
 // point's FMAs run, and the next batch's points are loaded into registers
-// while the current batch is accumulated.  Points arrive in tiles of 256; each thread sums one tile
-// in registers and adds that partial into a (hi, lo) running sum in shared
-// memory with an error-free two-sum, so the result does not degrade with the
-// number of points a cell sees.  The factors and the order of every sum are
+// while the current batch is accumulated.  Points arrive in tiles of 256;
+// each thread sums one tile in registers and adds that partial into a
+// (hi, lo) running sum (in global scratch, or in shared memory for callers
+// without scratch) with an error-free two-sum, so the result does not degrade
+// with the number of points a cell sees.  The factors and the order of every sum are
 // those of a thread that evaluates its own factors, so the result does not
 // depend on the tabulation.
 #include "kde_internal.cuh"
@@ -43,23 +44,48 @@ __device__ __forceinline__ TableRow table_row(const float* KX, const float* KY, 
   return r;
 }
 
-template <int KID>
-__global__ void __launch_bounds__(kThreads, 2)
+// GRUN: the (hi, lo) running sums live in global scratch (64 KB per CTA,
+// touched once per 256 points, so they stay in L2), which leaves shared
+// memory to the tables and three CTAs per SM; otherwise in shared memory (two
+// CTAs per SM, for callers that give no scratch).
+template <int KID, bool GRUN>
+__global__ void __launch_bounds__(kThreads, GRUN ? 3 : 2)
     k_simt(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n_pad,
            int64_t per_split, const float2* __restrict__ gxt, const float2* __restrict__ gyt,
-           int nx, int ny, float scale, float* __restrict__ part) {
+           int nx, int ny, float scale, float2* __restrict__ grun, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tables = reinterpret_cast<float*>(smem);                        // [2][kTable]
-  float2* run = reinterpret_cast<float2*>(tables + 2 * kTable);          // [64][kThreads]
   const int tid = threadIdx.x, lane = tid & 31;
   const int tx = tid & 15, ty = tid >> 4;
   const int cx0 = blockIdx.x * kTileX, cy0 = blockIdx.y * kTileY;
-#pragma unroll
-  for (int c = 0; c < 64; ++c) run[c * kThreads + tid] = make_float2(0.f, 0.f);
+  // running sum of cell c = b * 8 + a of this thread: run[c * kThreads]
+  float2* run;
+  if (GRUN) {
+    const int64_t cta = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    run = grun + cta * 64 * kThreads + tid;
+  } else {
+    run = reinterpret_cast<float2*>(tables + 2 * kTable) + tid;  // [64][kThreads]
+  }
+  float* dst = part + (int64_t)blockIdx.z * nx * ny;
+  auto cell = [&](int b, int a, int& x, int& y) {
+    y = cy0 + ty * 8 + b;
+    x = cx0 + (a < 4 ? tx * 4 + a : 64 + tx * 4 + a - 4);
+  };
 
   const int64_t p_begin = (int64_t)blockIdx.z * per_split;
   int64_t p_end = p_begin + per_split;
   if (p_end > n_pad) p_end = n_pad;
+  if (p_begin >= p_end) {  // no points in this split: a zero partial
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        int x, y;
+        cell(b, a, x, y);
+        if (x < nx && y < ny) dst[(int64_t)y * nx + x] = 0.f;
+      }
+    return;
+  }
   // factor roles: x column tid; y row frow for points fq0 .. fq0 + kBatch/2 - 1
   static_assert(kThreads == kTileX && kThreads == 2 * kTileY, "factor roles");
   static_assert(kPtsTile % kBatch == 0 && kBatch == 32, "one point per lane per batch");
@@ -126,60 +152,72 @@ __global__ void __launch_bounds__(kThreads, 2)
         cur = nxt;
       }
     }
+    // this tile's partials into the running sums; after the last tile the
+    // sums are the cells' results
+    const bool first = base == p_begin, last = base + kPtsTile >= p_end;
 #pragma unroll
     for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        float2 r = run[(b * 8 + a) * kThreads + tid];
+        float2 r = first ? make_float2(0.f, 0.f) : run[(b * 8 + a) * kThreads];
         two_sum_acc(r, acc[b][a]);
-        run[(b * 8 + a) * kThreads + tid] = r;
+        if (last) {
+          int x, y;
+          cell(b, a, x, y);
+          if (x < nx && y < ny) dst[(int64_t)y * nx + x] = (r.x + r.y) * scale;
+        } else {
+          run[(b * 8 + a) * kThreads] = r;
+        }
       }
-  }
-
-  float* dst = part + (int64_t)blockIdx.z * nx * ny;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int y = cy0 + ty * 8 + b;
-    if (y >= ny) continue;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int x = cx0 + (a < 4 ? tx * 4 + a : 64 + tx * 4 + a - 4);
-      if (x >= nx) continue;
-      const float2 r = run[(b * 8 + a) * kThreads + tid];
-      dst[(int64_t)y * nx + x] = (r.x + r.y) * scale;
-    }
   }
 }
 
-// 48 KB of tables + 64 KB of running sums: two CTAs per SM
-constexpr size_t kSmem = 2 * kTable * sizeof(float) + 64 * kThreads * sizeof(float2);
+// 48 KB of tables (+ 64 KB of running sums without global scratch)
+constexpr size_t kSmemTables = 2 * kTable * sizeof(float);
+constexpr size_t kSmemRun = 64 * kThreads * sizeof(float2);
 
-template <int KID>
+template <int KID, bool GRUN>
 cudaError_t launch_kid(const float4* pts, const float* wts, int64_t n_pad, const float2* gxt,
-                       const float2* gyt, int nx, int ny, int splits, float scale, float* part,
-                       cudaStream_t s) {
+                       const float2* gyt, int nx, int ny, int splits, float scale, float2* grun,
+                       float* part, cudaStream_t s) {
+  const size_t smem = GRUN ? kSmemTables : kSmemTables + kSmemRun;
   // per-device attribute; cheap, so set on every launch
-  cudaError_t e = cudaFuncSetAttribute(k_simt<KID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_simt<KID, GRUN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t per = (n_pad + splits - 1) / splits;
   per = (per + kPtsTile - 1) / kPtsTile * kPtsTile;
   if (per < kPtsTile) per = kPtsTile;
   dim3 grid((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY, splits);
-  k_simt<KID><<<grid, kThreads, kSmem, s>>>(pts, wts, n_pad, per, gxt, gyt, nx, ny, scale, part);
+  k_simt<KID, GRUN><<<grid, kThreads, smem, s>>>(pts, wts, n_pad, per, gxt, gyt, nx, ny, scale,
+                                                 grun, part);
   note_launches(1);
   return cudaGetLastError();
 }
 
+template <int KID>
+cudaError_t launch_kid(const float4* pts, const float* wts, int64_t n_pad, const float2* gxt,
+                       const float2* gyt, int nx, int ny, int splits, float scale, float2* grun,
+                       float* part, cudaStream_t s) {
+  return grun ? launch_kid<KID, true>(pts, wts, n_pad, gxt, gyt, nx, ny, splits, scale, grun,
+                                      part, s)
+              : launch_kid<KID, false>(pts, wts, n_pad, gxt, gyt, nx, ny, splits, scale, grun,
+                                       part, s);
+}
+
 }  // namespace
+
+size_t simt_scratch_bytes(int nx, int ny, int splits) {
+  return (size_t)((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY) * splits * kSmemRun;
+}
 
 cudaError_t launch_simt(int kid, const float4* pts, const float* wts, int64_t n_pad,
                         const float2* gxt, const float2* gyt, int nx, int ny, int splits,
-                        float scale, float* part, cudaStream_t s) {
+                        float scale, float2* scratch, float* part, cudaStream_t s) {
   switch (kid) {
 #define KDE_CASE(K) \
   case K:           \
-    return launch_kid<K>(pts, wts, n_pad, gxt, gyt, nx, ny, splits, scale, part, s);
+    return launch_kid<K>(pts, wts, n_pad, gxt, gyt, nx, ny, splits, scale, scratch, part, s);
     KDE_CASE(KDE_UNIFORM)
     KDE_CASE(KDE_TRIANGULAR)
     KDE_CASE(KDE_EPANECHNIKOV)

@@ -32,8 +32,9 @@ def run_gpu(wl, kid, path="cutoff", weights=True):
 
 @pytest.mark.parametrize("kid", COMPACT, ids=[oracle.KERNEL_NAMES[k] for k in COMPACT])
 def test_all_compact_kernels_ragged(kid):
-    """Ragged 32x32 bins on both axes, weights U(0.5, 2), points partly
-    outside the grid (some beyond reach, some within a bandwidth)."""
+    """Ragged 16x16 output blocks on both axes (4-cell sort bins), weights
+    U(0.5, 2), points partly outside the grid (some beyond reach, some within
+    a bandwidth)."""
     wl = workloads.random_points(500 + kid, 2500, 3000.0, 10.0, 300, 150, 35.0, kid)
     if kid == oracle.UNIFORM:
         wl = clear_of_support_edge(wl, radial=False)
@@ -44,8 +45,26 @@ def test_all_compact_kernels_ragged(kid):
 
 @pytest.mark.parametrize("kid", [oracle.EPANECHNIKOV, oracle.TRICUBE])
 def test_wide_bandwidth_many_bins_in_reach(kid):
-    """h = 70 cells: each point reaches three bins in every direction."""
+    """h = 70 cells (16-cell sort bins): each output block reads the points of
+    a 10 x 10 window of sort bins."""
     wl = workloads.random_points(510 + kid, 3000, 700.0, 5.0, 128, 96, 350.0, kid)
+    F = run_gpu(wl, kid)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("h_cells", [1.5, 5.0, 6.5, 12.0, 16.5, 30.0])
+@pytest.mark.parametrize("kid", [oracle.EPANECHNIKOV, oracle.RADIAL + oracle.QUARTIC],
+                         ids=["epanechnikov", "radial_quartic"])
+def test_every_sort_bin_side(h_cells, kid):
+    """Bandwidths on both sides of each change of sort-bin side (4 cells up
+    to 6 h/cell, 8 up to 16, 16 beyond), clustered points on a ragged grid:
+    the points an output block reads must include every point within a
+    bandwidth of its cells."""
+    cell = 10.0
+    wl = workloads.random_points(540 + int(h_cells * 10), 3000, 2400.0, cell, 230, 170,
+                                 h_cells * cell, kid % oracle.RADIAL)
+    wl.local[:1000] = wl.local[:1000] * 0.1 + 1100.0  # a dense cluster
     F = run_gpu(wl, kid)
     ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
     assert rel_linf(F, ref) <= TOL_FP32
