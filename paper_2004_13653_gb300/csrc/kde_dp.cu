@@ -15,15 +15,23 @@
 //                    (the label update of Eq. 11); segments with nothing
 //                    above eps are closed.  The per-segment slots of the next
 //                    iteration (double-buffered) are cleared here.
-// The loop ends when an iteration keeps no point.  The VED is evaluated with
+// The loop ends when an iteration keeps no point.  All iterations run in one
+// cooperative launch: the three steps are phases of a persistent kernel
+// separated by grid-wide barriers, and the count of points kept in an
+// iteration is read on the device, so no level costs a host round trip.
+// The VED is evaluated with
 // explicitly rounded FP64 operations in the order of Eq. 9, so every
 // comparison -- and therefore the kept set -- is identical to a sequential
 // FP64 evaluation.  The kept points are then compacted with the Sec. IV-A
 // exclusive scan.
+#include <cooperative_groups.h>
+
 #include "kde_internal.cuh"
 
 namespace kde {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr uint8_t kKept = 1, kDone = 2;
 constexpr uint32_t kNoArg = 0xffffffffu;
@@ -87,7 +95,7 @@ __global__ void k_dp_init(const double2* __restrict__ xy, int64_t n,
 // Step 1.  Lanes of a warp hold consecutive points, so equal segment starts
 // form runs of lanes: a shuffle scan takes each run's maximum and its last
 // lane issues the atomic.
-__global__ void k_dp_ved(const double2* __restrict__ xy, int64_t n, double eps,
+__device__ __forceinline__ void dp_ved(const double2* __restrict__ xy, int64_t n, double eps,
                          const int32_t* __restrict__ s, const int32_t* __restrict__ e,
                          const uint8_t* __restrict__ flag, double* __restrict__ dist,
                          unsigned long long* __restrict__ segmax) {
@@ -118,7 +126,7 @@ __global__ void k_dp_ved(const double2* __restrict__ xy, int64_t n, double eps,
 }
 
 // Step 2: the first point of each segment whose VED equals the maximum.
-__global__ void k_dp_arg(int64_t n, const int32_t* __restrict__ s,
+__device__ __forceinline__ void dp_arg(int64_t n, const int32_t* __restrict__ s,
                          const uint8_t* __restrict__ flag, const double* __restrict__ dist,
                          const unsigned long long* __restrict__ segmax,
                          uint32_t* __restrict__ segarg) {
@@ -134,11 +142,12 @@ __global__ void k_dp_arg(int64_t n, const int32_t* __restrict__ s,
 
 // Step 3: keep the split points, move the others' segment ends, close the
 // segments without a split, clear the next iteration's slots.
-__global__ void k_dp_split(int64_t n, int32_t* __restrict__ s, int32_t* __restrict__ e,
-                           uint8_t* __restrict__ flag, const uint32_t* __restrict__ segarg,
-                           unsigned long long* __restrict__ segmax_next,
-                           uint32_t* __restrict__ segarg_next,
-                           unsigned long long* __restrict__ kept_now) {
+__device__ __forceinline__ void dp_split(int64_t n, int32_t* __restrict__ s,
+                                         int32_t* __restrict__ e, uint8_t* __restrict__ flag,
+                                         const uint32_t* __restrict__ segarg,
+                                         unsigned long long* __restrict__ segmax_next,
+                                         uint32_t* __restrict__ segarg_next,
+                                         unsigned long long* __restrict__ kept_now) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long mine = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -161,6 +170,42 @@ __global__ void k_dp_split(int64_t n, int32_t* __restrict__ s, int32_t* __restri
     segarg_next[sp] = kNoArg;
   }
   if (mine) atomicAdd(kept_now, mine);
+}
+
+// Every iteration of the level loop in one cooperative launch (all CTAs
+// resident).  counter[it & 1] counts the points iteration `it` keeps; the
+// other slot is cleared after the first barrier of the iteration, when every
+// CTA has read the previous iteration's count.  Each CTA leaves the loop on
+// the same count, so all take the same barriers.  Every iteration keeps at
+// least one point or ends the loop, so n + 1 iterations bound it.
+__global__ void __launch_bounds__(256)
+    k_dp_levels(const double2* __restrict__ xy, int64_t n, double eps, int32_t* __restrict__ s,
+                int32_t* __restrict__ e, uint8_t* __restrict__ flag, double* __restrict__ dist,
+                unsigned long long* __restrict__ segmax, uint32_t* __restrict__ segarg,
+                unsigned long long* __restrict__ counter, int* __restrict__ iterations) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ unsigned long long kept;
+  int64_t it = 0;
+  for (; it <= n; ++it) {
+    const int b = (int)(it & 1);
+    dp_ved(xy, n, eps, s, e, flag, dist, segmax + b * n);
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) counter[b ^ 1] = 0ull;
+    dp_arg(n, s, flag, dist, segmax + b * n, segarg + b * n);
+    grid.sync();
+    dp_split(n, s, e, flag, segarg + b * n, segmax + (b ^ 1) * n, segarg + (b ^ 1) * n,
+             counter + b);
+    grid.sync();
+    if (threadIdx.x == 0) kept = __ldcg(counter + b);
+    __syncthreads();
+    const bool done = kept == 0ull;
+    __syncthreads();  // `kept` is rewritten in the next iteration
+    if (done) {
+      ++it;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *iterations = (int)it;
 }
 
 __global__ void k_dp_flags(const uint8_t* __restrict__ flag, int64_t n,
@@ -196,7 +241,7 @@ int grid_for(int64_t n) {
 
 size_t dp_workspace_bytes(int64_t n) {
   const size_t m = (size_t)n + 1;
-  return 256 * 12 + m * (4 + 4 + 1 + 16 + 8 + 8 + 4 + 4) + 4 * (scan_temp_words((int64_t)m, 2048) + 64);
+  return 256 * 13 + m * (4 + 4 + 1 + 16 + 8 + 8 + 4 + 4) + 4 * (scan_temp_words((int64_t)m, 2048) + 64);
 }
 
 cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t ntraj, double eps,
@@ -214,7 +259,8 @@ cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t n
   uint32_t* segarg = reinterpret_cast<uint32_t*>(take(8 * m));
   uint32_t* kept32 = reinterpret_cast<uint32_t*>(take(4 * m));
   uint32_t* pos = reinterpret_cast<uint32_t*>(take(4 * m));
-  unsigned long long* counter = reinterpret_cast<unsigned long long*>(take(8));
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(take(16));
+  int* iters_dev = reinterpret_cast<int*>(take(sizeof(int)));
   uint32_t* scan_temp = reinterpret_cast<uint32_t*>(take(4 * (scan_temp_words((int64_t)m, 2048) + 64)));
   const double2* P = reinterpret_cast<const double2*>(xy);
   const int g = grid_for(n);
@@ -224,26 +270,29 @@ cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t n
     k_dp_init<<<g, 256, 0, st>>>(P, n, off, ntraj, s, e, flag, segmax, segarg, scal);
     note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    unsigned long long kept_now = 0;
-    // every iteration keeps at least one point, so n iterations bound the loop
-    for (; it <= n; ++it) {
-      const int b = it & 1;
-      if ((err = cudaMemsetAsync(counter, 0, 8, st)) != cudaSuccess) break;
-      k_dp_ved<<<g, 256, 0, st>>>(P, n, eps, s, e, flag, dist, segmax + b * n);
-      k_dp_arg<<<g, 256, 0, st>>>(n, s, flag, dist, segmax + b * n, segarg + b * n);
-      k_dp_split<<<g, 256, 0, st>>>(n, s, e, flag, segarg + b * n, segmax + (b ^ 1) * n,
-                                    segarg + (b ^ 1) * n, counter);
-      note_launches(3);
-      if ((err = cudaGetLastError()) != cudaSuccess) break;
-      if ((err = cudaMemcpyAsync(&kept_now, counter, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        break;
-      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) break;
-      if (kept_now == 0) {
-        ++it;
-        break;
-      }
-    }
+    if ((err = cudaMemsetAsync(counter, 0, 16, st)) != cudaSuccess) return err;
+    // all CTAs of the cooperative launch must be resident at once
+    int dev = 0, per_sm = 0, sms = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dp_levels, 256, 0)) !=
+        cudaSuccess)
+      return err;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    // up to four CTAs per SM: enough warps for the memory phases, few CTAs
+    // at each barrier
+    const int gl = (int)std::min<int64_t>((int64_t)std::min(per_sm, 4) * sms, (n + 255) / 256);
+    void* args[] = {(void*)&P, (void*)&n, (void*)&eps, (void*)&s, (void*)&e, (void*)&flag,
+                    (void*)&dist, (void*)&segmax, (void*)&segarg, (void*)&counter,
+                    (void*)&iters_dev};
+    err = cudaLaunchCooperativeKernel((const void*)k_dp_levels, dim3(gl), dim3(256), args, 0, st);
+    note_launches(1);
     if (err != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(&it, iters_dev, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return err;
+    if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
   }
   if (iterations) *iterations = it;
   k_dp_flags<<<grid_for(n + 1), 256, 0, st>>>(flag, n, kept32, keep);
