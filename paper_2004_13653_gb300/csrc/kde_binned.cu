@@ -4,10 +4,12 @@
 // interpolation (Eq. InterX / InterY), and M_D is convolved with a
 // window x window stencil of a Table 1 kernel (Eq. 7).
 //
-// Counting: one thread per fix; the cell index is floor((x - o) / cell) in
-// FP64 and the interpolated cells are floor(i + (c/c_max) di + 1/2) with
-// c = 1..c_max-1, evaluated with explicitly rounded FP64 operations (no fused
-// multiply-add), so the counts are bit-identical to a CPU evaluation.
+// Counting: one thread per fix; the cell index is floor((x - o) / cell) with
+// the FP64 division correctly rounded (a multiply by 1/cell decides it except
+// within rounding distance of a cell edge), and the interpolated cells are
+// floor(i + (c/c_max) di + 1/2) with c = 1..c_max-1, evaluated with
+// explicitly rounded FP64 operations (no fused multiply-add), so the counts
+// are bit-identical to a CPU evaluation.
 // Integer atomics make the counts independent of scheduling.
 //
 // Convolution: the Table 1 kernels are products, so the 2-D stencil
@@ -23,21 +25,32 @@ namespace {
 
 constexpr int kMaxHalf = 127;  // window half-width limit (window <= 255)
 
-__device__ __forceinline__ int64_t cell_index(double v, double o, double d, int n) {
-  const double f = floor(__ddiv_rn(__dsub_rn(v, o), d));
+// floor((v - o) / d) with the FP64 division correctly rounded, or -1 outside
+// [0, n).  FP64 division is costly on this GPU, so the quotient is first
+// taken as (v - o) * inv_d (inv_d = 1/d rounded): that product is within
+// 3 ulp of the exact quotient, the rounded division within half an ulp, so
+// unless the product lies within 4e-15 relative of an integer both have the
+// same floor; only those rare cases divide.
+__device__ __forceinline__ int64_t cell_index(double v, double o, double d, double inv_d, int n) {
+  const double t = __dsub_rn(v, o);
+  const double q = __dmul_rn(t, inv_d);
+  double f = floor(q);
+  const double frac = q - f;  // exact for |q| < 2^52
+  if (!(fmin(frac, 1.0 - frac) > 4e-15 * fmax(fabs(q), 1.0)))
+    f = floor(__ddiv_rn(t, d));
   if (!(f >= 0.0) || f >= (double)n) return -1;
   return (int64_t)f;
 }
 
 __global__ void k_count(const double* __restrict__ xy, int64_t n,
                         const int64_t* __restrict__ off, int64_t ntraj, double ox, double oy,
-                        double cell, int nx, int ny, int interpolate, int* __restrict__ counts,
-                        unsigned long long* __restrict__ added) {
+                        double cell, double inv_cell, int nx, int ny, int interpolate,
+                        int* __restrict__ counts, unsigned long long* __restrict__ added) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long my_added = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const int64_t i = cell_index(xy[2 * p], ox, cell, nx);
-    const int64_t j = cell_index(xy[2 * p + 1], oy, cell, ny);
+    const int64_t i = cell_index(xy[2 * p], ox, cell, inv_cell, nx);
+    const int64_t j = cell_index(xy[2 * p + 1], oy, cell, inv_cell, ny);
     if (i < 0 || j < 0) continue;
     atomicAdd(&counts[j * nx + i], 1);
     if (!interpolate || p + 1 >= n) continue;
@@ -52,8 +65,8 @@ __global__ void k_count(const double* __restrict__ xy, int64_t n,
       next_start = off[lo + 1];
     }
     if (p + 1 >= next_start) continue;
-    const int64_t i1 = cell_index(xy[2 * p + 2], ox, cell, nx);
-    const int64_t j1 = cell_index(xy[2 * p + 3], oy, cell, ny);
+    const int64_t i1 = cell_index(xy[2 * p + 2], ox, cell, inv_cell, nx);
+    const int64_t j1 = cell_index(xy[2 * p + 3], oy, cell, inv_cell, ny);
     if (i1 < 0 || j1 < 0) continue;
     const int64_t di = i1 - i, dj = j1 - j;
     const int64_t adi = di < 0 ? -di : di, adj = dj < 0 ? -dj : dj;
@@ -165,8 +178,8 @@ cudaError_t launch_binned(const double* xy, int64_t n, const int64_t* off, int64
   if (n > 0) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_count<<<(int)blocks, 256, 0, s>>>(xy, n, off, ntraj, ox, oy, cell, nx, ny, interpolate,
-                                        counts, added);
+    k_count<<<(int)blocks, 256, 0, s>>>(xy, n, off, ntraj, ox, oy, cell, 1.0 / cell, nx, ny,
+                                        interpolate, counts, added);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

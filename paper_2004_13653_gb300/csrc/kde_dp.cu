@@ -4,17 +4,26 @@
 // textbook algorithm becomes a loop over tree levels.
 //
 // Each point carries the two ends (s, e) of the segment it lies in, which
-// plays the part of the paper's label set Lp.  One iteration:
-//   1. k_dp_ved    : the VED of every open point to its segment (Eq. 9); the
-//                    largest VED above eps per segment, by a segmented max over
-//                    each warp's lanes and one 64-bit atomicMax per run
-//                    (non-negative doubles order like their bit patterns);
-//   2. k_dp_arg    : the first point attaining that maximum (atomicMin), the
-//                    tie rule of the sequential algorithm;
-//   3. k_dp_split  : that point is kept; the others move their s or e to it
-//                    (the label update of Eq. 11); segments with nothing
-//                    above eps are closed.  The per-segment slots of the next
-//                    iteration (double-buffered) are cleared here.
+// plays the part of the paper's label set Lp, and each segment's length
+// |e - s| is kept at its start index.  Eq. 9's VED is |cross| / length, and for
+// one segment the correctly rounded quotient never decreases when the cross
+// product grows, so the steps work on the cross product and divide only where
+// the result could depend on it.  One iteration:
+//   1. ved   : the cross product of every open point with its segment; its
+//              maximum per segment by a segmented max over each warp's lanes
+//              and one 64-bit atomicMax per run (non-negative doubles order
+//              like their bit patterns);
+//   2. arg   : the segment's largest VED is the maximum cross product divided
+//              by the length; the points whose cross product is within 1e-15
+//              of the maximum (no other can tie after rounding) compute their
+//              VED exactly, and the first one equal to that largest VED, if it
+//              exceeds eps, is the split (atomicMin) -- the tie rule of the
+//              sequential algorithm;
+//   3. split : that point is kept and records the lengths of the two segments
+//              it starts and ends; the others move their s or e to it (the
+//              label update of Eq. 11); segments with nothing above eps are
+//              closed.  The per-segment slots of the next iteration
+//              (double-buffered) are cleared here.
 // The loop ends when an iteration keeps no point.  All iterations run in one
 // cooperative launch: the three steps are phases of a persistent kernel
 // separated by grid-wide barriers, and the count of points kept in an
@@ -36,13 +45,22 @@ namespace cg = cooperative_groups;
 constexpr uint8_t kKept = 1, kDone = 2;
 constexpr uint32_t kNoArg = 0xffffffffu;
 
-__device__ __forceinline__ double ved(double px, double py, double sx, double sy, double ex,
-                                      double ey) {
-  const double dx = __dsub_rn(ex, sx), dy = __dsub_rn(ey, sy);
-  const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-  const double vx = __dsub_rn(px, sx), vy = __dsub_rn(py, sy);
+// |e - s|, rounded as Eq. 9 is evaluated
+__device__ __forceinline__ double seg_len(double2 a, double2 b) {
+  const double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y);
+  return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+}
+// The numerator of Eq. 9, |(p - s) x (e - s)| -- or, for a segment of zero
+// length, the distance |p - s| itself (the VED then).
+__device__ __forceinline__ double ved_num(double2 q, double2 a, double2 b, double len) {
+  const double vx = __dsub_rn(q.x, a.x), vy = __dsub_rn(q.y, a.y);
   if (len == 0.0) return __dsqrt_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
-  return __ddiv_rn(fabs(__dsub_rn(__dmul_rn(vx, dy), __dmul_rn(vy, dx))), len);
+  const double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y);
+  return fabs(__dsub_rn(__dmul_rn(vx, dy), __dmul_rn(vy, dx)));
+}
+// The VED from its numerator.
+__device__ __forceinline__ double ved_of(double num, double len) {
+  return len == 0.0 ? num : __ddiv_rn(num, len);
 }
 
 // Trajectory bounds of point p: the last k with off[k] <= p; bounds clamped to
@@ -67,7 +85,7 @@ __global__ void k_dp_init(const double2* __restrict__ xy, int64_t n,
                           const int64_t* __restrict__ off, int64_t ntraj, int32_t* __restrict__ s,
                           int32_t* __restrict__ e, uint8_t* __restrict__ flag,
                           unsigned long long* __restrict__ segmax, uint32_t* __restrict__ segarg,
-                          CallScalars* __restrict__ scal) {
+                          double* __restrict__ seglen, CallScalars* __restrict__ scal) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     int64_t a, b;
@@ -82,6 +100,7 @@ __global__ void k_dp_init(const double2* __restrict__ xy, int64_t n,
     s[p] = (int32_t)a;
     e[p] = (int32_t)(b - 1);
     flag[p] = (p == a || p == b - 1 || bad) ? kKept : 0;
+    if (p == a) seglen[p] = seg_len(q, xy[b - 1]);
     segmax[p] = 0ull;
     segmax[n + p] = 0ull;
     segarg[p] = kNoArg;
@@ -95,10 +114,11 @@ __global__ void k_dp_init(const double2* __restrict__ xy, int64_t n,
 // Step 1.  Lanes of a warp hold consecutive points, so equal segment starts
 // form runs of lanes: a shuffle scan takes each run's maximum and its last
 // lane issues the atomic.
-__device__ __forceinline__ void dp_ved(const double2* __restrict__ xy, int64_t n, double eps,
-                         const int32_t* __restrict__ s, const int32_t* __restrict__ e,
-                         const uint8_t* __restrict__ flag, double* __restrict__ dist,
-                         unsigned long long* __restrict__ segmax) {
+__device__ __forceinline__ void dp_ved(const double2* __restrict__ xy, int64_t n,
+                                       const int32_t* __restrict__ s, const int32_t* __restrict__ e,
+                                       const uint8_t* __restrict__ flag,
+                                       const double* __restrict__ seglen, double* __restrict__ num,
+                                       unsigned long long* __restrict__ segmax) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -107,11 +127,10 @@ __device__ __forceinline__ void dp_ved(const double2* __restrict__ xy, int64_t n
     unsigned long long v = 0ull;
     if (p < n && !(flag[p] & (kKept | kDone))) {
       const int32_t sp = s[p], ep = e[p];
-      const double2 q = xy[p], a = xy[sp], b = xy[ep];
-      const double d = ved(q.x, q.y, a.x, a.y, b.x, b.y);
-      dist[p] = d;
+      const double c = ved_num(xy[p], xy[sp], xy[ep], seglen[sp]);
+      num[p] = c;
       key = sp;
-      if (d > eps) v = (unsigned long long)__double_as_longlong(d);
+      v = (unsigned long long)__double_as_longlong(c);
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -125,26 +144,37 @@ __device__ __forceinline__ void dp_ved(const double2* __restrict__ xy, int64_t n
   }
 }
 
-// Step 2: the first point of each segment whose VED equals the maximum.
-__device__ __forceinline__ void dp_arg(int64_t n, const int32_t* __restrict__ s,
-                         const uint8_t* __restrict__ flag, const double* __restrict__ dist,
-                         const unsigned long long* __restrict__ segmax,
-                         uint32_t* __restrict__ segarg) {
+// Step 2: the first point of each segment whose VED equals the segment's
+// largest, when that exceeds eps.  A cross product below (1 - 1e-15) times the
+// largest one gives a VED strictly below the largest after rounding (the
+// division is correctly rounded and monotone), so only the others divide.
+__device__ __forceinline__ void dp_arg(int64_t n, double eps, const int32_t* __restrict__ s,
+                                       const uint8_t* __restrict__ flag,
+                                       const double* __restrict__ seglen,
+                                       const double* __restrict__ num,
+                                       const unsigned long long* __restrict__ segmax,
+                                       uint32_t* __restrict__ segarg) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     if (flag[p] & (kKept | kDone)) continue;
     const int32_t sp = s[p];
-    const unsigned long long m = segmax[sp];
-    if (m != 0ull && (unsigned long long)__double_as_longlong(dist[p]) == m)
-      atomicMin(&segarg[sp], (uint32_t)p);
+    const double cmax = __longlong_as_double((long long)segmax[sp]);
+    const double c = num[p];
+    if (!(c >= __dmul_rn(cmax, 1.0 - 1e-15))) continue;
+    const double len = seglen[sp];
+    const double dmax = cmax == 0.0 ? 0.0 : ved_of(cmax, len);
+    const double d = c == cmax ? dmax : ved_of(c, len);
+    if (dmax > eps && d == dmax) atomicMin(&segarg[sp], (uint32_t)p);
   }
 }
 
 // Step 3: keep the split points, move the others' segment ends, close the
 // segments without a split, clear the next iteration's slots.
-__device__ __forceinline__ void dp_split(int64_t n, int32_t* __restrict__ s,
-                                         int32_t* __restrict__ e, uint8_t* __restrict__ flag,
+__device__ __forceinline__ void dp_split(const double2* __restrict__ xy, int64_t n,
+                                         int32_t* __restrict__ s, int32_t* __restrict__ e,
+                                         uint8_t* __restrict__ flag,
                                          const uint32_t* __restrict__ segarg,
+                                         double* __restrict__ seglen,
                                          unsigned long long* __restrict__ segmax_next,
                                          uint32_t* __restrict__ segarg_next,
                                          unsigned long long* __restrict__ kept_now) {
@@ -159,8 +189,11 @@ __device__ __forceinline__ void dp_split(int64_t n, int32_t* __restrict__ s,
       flag[p] = f | kDone;
       continue;
     }
-    if ((int64_t)k == p) {
+    if ((int64_t)k == p) {  // the lengths of the segments [s, p] and [p, e]
       flag[p] = kKept;
+      const double2 q = xy[p];
+      seglen[sp] = seg_len(xy[sp], q);
+      seglen[p] = seg_len(q, xy[e[p]]);
       ++mine;
       continue;
     }
@@ -180,21 +213,22 @@ __device__ __forceinline__ void dp_split(int64_t n, int32_t* __restrict__ s,
 // least one point or ends the loop, so n + 1 iterations bound it.
 __global__ void __launch_bounds__(256)
     k_dp_levels(const double2* __restrict__ xy, int64_t n, double eps, int32_t* __restrict__ s,
-                int32_t* __restrict__ e, uint8_t* __restrict__ flag, double* __restrict__ dist,
-                unsigned long long* __restrict__ segmax, uint32_t* __restrict__ segarg,
-                unsigned long long* __restrict__ counter, int* __restrict__ iterations) {
+                int32_t* __restrict__ e, uint8_t* __restrict__ flag, double* __restrict__ num,
+                double* __restrict__ seglen, unsigned long long* __restrict__ segmax,
+                uint32_t* __restrict__ segarg, unsigned long long* __restrict__ counter,
+                int* __restrict__ iterations) {
   cg::grid_group grid = cg::this_grid();
   __shared__ unsigned long long kept;
   int64_t it = 0;
   for (; it <= n; ++it) {
     const int b = (int)(it & 1);
-    dp_ved(xy, n, eps, s, e, flag, dist, segmax + b * n);
+    dp_ved(xy, n, s, e, flag, seglen, num, segmax + b * n);
     grid.sync();
     if (blockIdx.x == 0 && threadIdx.x == 0) counter[b ^ 1] = 0ull;
-    dp_arg(n, s, flag, dist, segmax + b * n, segarg + b * n);
+    dp_arg(n, eps, s, flag, seglen, num, segmax + b * n, segarg + b * n);
     grid.sync();
-    dp_split(n, s, e, flag, segarg + b * n, segmax + (b ^ 1) * n, segarg + (b ^ 1) * n,
-             counter + b);
+    dp_split(xy, n, s, e, flag, segarg + b * n, seglen, segmax + (b ^ 1) * n,
+             segarg + (b ^ 1) * n, counter + b);
     grid.sync();
     if (threadIdx.x == 0) kept = __ldcg(counter + b);
     __syncthreads();
@@ -241,7 +275,8 @@ int grid_for(int64_t n) {
 
 size_t dp_workspace_bytes(int64_t n) {
   const size_t m = (size_t)n + 1;
-  return 256 * 13 + m * (4 + 4 + 1 + 16 + 8 + 8 + 4 + 4) + 4 * (scan_temp_words((int64_t)m, 2048) + 64);
+  return 256 * 14 + m * (4 + 4 + 1 + 16 + 8 + 8 + 8 + 4 + 4) +
+         4 * (scan_temp_words((int64_t)m, 2048) + 64);
 }
 
 cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t ntraj, double eps,
@@ -255,7 +290,8 @@ cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t n
   int32_t* e = reinterpret_cast<int32_t*>(take(4 * m));
   uint8_t* flag = reinterpret_cast<uint8_t*>(take(m));
   unsigned long long* segmax = reinterpret_cast<unsigned long long*>(take(16 * m));
-  double* dist = reinterpret_cast<double*>(take(8 * m));
+  double* num = reinterpret_cast<double*>(take(8 * m));
+  double* seglen = reinterpret_cast<double*>(take(8 * m));
   uint32_t* segarg = reinterpret_cast<uint32_t*>(take(8 * m));
   uint32_t* kept32 = reinterpret_cast<uint32_t*>(take(4 * m));
   uint32_t* pos = reinterpret_cast<uint32_t*>(take(4 * m));
@@ -267,7 +303,7 @@ cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t n
   cudaError_t err = cudaSuccess;
   int it = 0;
   if (n > 0) {
-    k_dp_init<<<g, 256, 0, st>>>(P, n, off, ntraj, s, e, flag, segmax, segarg, scal);
+    k_dp_init<<<g, 256, 0, st>>>(P, n, off, ntraj, s, e, flag, segmax, segarg, seglen, scal);
     note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(counter, 0, 16, st)) != cudaSuccess) return err;
@@ -284,8 +320,8 @@ cudaError_t launch_dp(const double* xy, int64_t n, const int64_t* off, int64_t n
     // at each barrier
     const int gl = (int)std::min<int64_t>((int64_t)std::min(per_sm, 4) * sms, (n + 255) / 256);
     void* args[] = {(void*)&P, (void*)&n, (void*)&eps, (void*)&s, (void*)&e, (void*)&flag,
-                    (void*)&dist, (void*)&segmax, (void*)&segarg, (void*)&counter,
-                    (void*)&iters_dev};
+                    (void*)&num, (void*)&seglen, (void*)&segmax, (void*)&segarg,
+                    (void*)&counter, (void*)&iters_dev};
     err = cudaLaunchCooperativeKernel((const void*)k_dp_levels, dim3(gl), dim3(256), args, 0, st);
     note_launches(1);
     if (err != cudaSuccess) return err;

@@ -136,3 +136,23 @@ def test_binned_vs_direct_sum_on_dense_grid():
     err = rel_linf(F, D)
     print(f"binned vs direct sum: {err:.3e}")
     assert err < 0.1
+
+
+@pytest.mark.parametrize("cell", [10.0, 24.4140625, 7.3])
+def test_fixes_on_and_next_to_cell_edges(cell):
+    """Fixes exactly on cell edges (o + k cell in FP64) and one ulp either
+    side of them, along x and y, with an origin and a cell that are not
+    powers of two: the cell index must be the floor of the correctly rounded
+    FP64 division in every case (the kernel decides most cells with a
+    multiply and divides only next to an edge)."""
+    rng = np.random.default_rng(int(cell * 1000))
+    origin = (512_345.678, 4_401_234.5)
+    nx, ny = 300, 200
+    k = rng.integers(0, nx, 3000).astype(np.float64)
+    m = rng.integers(0, ny, 3000).astype(np.float64)
+    ex = origin[0] + k * cell
+    ey = origin[1] + m * cell
+    xs = np.concatenate([ex, np.nextafter(ex, -np.inf), np.nextafter(ex, np.inf), ex + 0.3 * cell])
+    ys = np.concatenate([ey + 0.5 * cell, ey, np.nextafter(ey, np.inf), np.nextafter(ey, -np.inf)])
+    xy = np.stack([xs, ys], axis=1)
+    check(xy, None, origin, cell, nx, ny, 3.0 * cell, oracle.EPANECHNIKOV, interpolate=False)
