@@ -22,7 +22,7 @@
  *     with linear interpolation of skipped cells (Sec. IV-B, Eq. InterX/
  *     InterY, Algorithm 3) and its discrete convolution (Eq. 7)
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - s and t in Table 1 are offsets divided by the bandwidth h, with support
  *     |s|,|t| <= 1 (every Table 1 factor then integrates to one);
  *   - Mercator uses the WGS84 ellipsoid, longitude in radians of the absolute
