@@ -19,12 +19,12 @@ namespace kde {
 namespace {
 
 constexpr int kBin = kCutoffBin;    // cells per output block side
-constexpr int kGroupThreads = kBin * kBin / 4;  // a point group: one thread per column, 4 rows
-constexpr int kGroups = 4;          // point groups per CTA (one bin)
+constexpr int kGroupThreads = 32;   // a point group is one warp: 8 cells per thread
+constexpr int kGroups = 8;          // point groups per CTA (one output block)
 constexpr int kSortThreads = 256;   // 8 warps
 constexpr int kSortRounds = 8;      // 32-element rounds per warp
 constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
-constexpr int kBatch = 64;          // points per shared-memory batch
+constexpr int kBatch = 32;          // points per shared-memory batch (one per lane)
 
 template <class T>
 __device__ __forceinline__ int find_by(const T* tab, int ninst, int64_t v, int64_t T::*field) {
@@ -164,46 +164,52 @@ __global__ void k_permute(const float4* __restrict__ pts, const float* __restric
 }
 
 
-// Accumulate one batch's outer products into a thread's four cells (column
-// cx, rows cy0..cy0+3): product kernels from tabulated factors, radial kernels
-// from tabulated squared offsets and the profile per pair.
+// Accumulate one batch's outer products into a thread's eight cells (columns
+// cx, cx+1, rows cy0..cy0+3; acc[2 r + c]): product kernels from tabulated
+// factors, radial kernels from tabulated squared offsets and the profile per
+// pair.  Per point one 8-byte and one 16-byte table read feed eight FMAs.
 template <int KID, bool RADIAL>
 __device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float (*KY)[kBin],
                                            const float* sW, int cnt, int cx, int cy0,
-                                           float (&acc)[4]) {
+                                           float (&acc)[8]) {
   int c = 0;
-  if (!RADIAL) {  // four points per step so their table reads are in flight together
-    for (; c + 4 <= cnt; c += 4) {
-      float kx[4];
-      float4 ky[4];
+  if (!RADIAL) {  // two points per step so their table reads are in flight together
+    for (; c + 2 <= cnt; c += 2) {
+      float2 kx[2];
+      float4 ky[2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        kx[u] = KX[c + u][cx];
+      for (int u = 0; u < 2; ++u) {
+        kx[u] = *reinterpret_cast<const float2*>(&KX[c + u][cx]);
         ky[u] = *reinterpret_cast<const float4*>(&KY[c + u][cy0]);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc[0] = fmaf(kx[u], ky[u].x, acc[0]);
-        acc[1] = fmaf(kx[u], ky[u].y, acc[1]);
-        acc[2] = fmaf(kx[u], ky[u].z, acc[2]);
-        acc[3] = fmaf(kx[u], ky[u].w, acc[3]);
+      for (int u = 0; u < 2; ++u) {
+        const float y[4] = {ky[u].x, ky[u].y, ky[u].z, ky[u].w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          acc[2 * r] = fmaf(kx[u].x, y[r], acc[2 * r]);
+          acc[2 * r + 1] = fmaf(kx[u].y, y[r], acc[2 * r + 1]);
+        }
       }
     }
   }
   for (; c < cnt; ++c) {
-    const float kx = KX[c][cx];
-    const float4 ky = *reinterpret_cast<const float4*>(&KY[c][cy0]);
+    const float2 kx = *reinterpret_cast<const float2*>(&KX[c][cx]);
+    const float4 ky4 = *reinterpret_cast<const float4*>(&KY[c][cy0]);
+    const float y[4] = {ky4.x, ky4.y, ky4.z, ky4.w};
     if (RADIAL) {
       const float w = sW[c];
-      acc[0] = fmaf(w, kradial<KID>(kx + ky.x), acc[0]);
-      acc[1] = fmaf(w, kradial<KID>(kx + ky.y), acc[1]);
-      acc[2] = fmaf(w, kradial<KID>(kx + ky.z), acc[2]);
-      acc[3] = fmaf(w, kradial<KID>(kx + ky.w), acc[3]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc[2 * r] = fmaf(w, kradial<KID>(kx.x + y[r]), acc[2 * r]);
+        acc[2 * r + 1] = fmaf(w, kradial<KID>(kx.y + y[r]), acc[2 * r + 1]);
+      }
     } else {
-      acc[0] = fmaf(kx, ky.x, acc[0]);
-      acc[1] = fmaf(kx, ky.y, acc[1]);
-      acc[2] = fmaf(kx, ky.z, acc[2]);
-      acc[3] = fmaf(kx, ky.w, acc[3]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc[2 * r] = fmaf(kx.x, y[r], acc[2 * r]);
+        acc[2 * r + 1] = fmaf(kx.y, y[r], acc[2 * r + 1]);
+      }
     }
   }
 }
@@ -299,23 +305,23 @@ struct GroupTables {
 
 // The block's work, for one kernel.  The points that can reach the block are
 // the runs of the sort bins in its range, one run per bin row; their
-// concatenation is cut into kBatch-point batches, and group g of the CTA takes
-// batches g, g+G, g+2G, ... (fetching the next while computing the current)
-// and ends with the two-sum of its four cells in run.
+// concatenation is cut into kBatch-point batches, and warp g of the CTA takes
+// batches g, g+G, g+2G, ... (fetching the next while computing the current;
+// the warp synchronises only itself) and ends with the two-sum of its eight
+// cells in run.
 template <int KID, bool RADIAL>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
-                                             int64_t total, int g, int tg, GroupTables& T,
-                                             float2 (&run)[4]) {
+                                             int64_t total, int g, int lane, GroupTables& T,
+                                             float2 (&run)[8]) {
   const int nx = I.nx, ny = I.ny;
   const int x0 = bx * kBin, y0 = by * kBin;
-  const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
-  // table role: column (and row) ej for points eq0 .. eq0 + kEvalPts - 1
+  const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
+  // table role: column (and row) ej for the points of one parity, c = 2k + half
   constexpr int kEvalPts = kBatch * kBin / kGroupThreads;
-  static_assert(kGroupThreads % kBin == 0 && kBatch * kBin % kGroupThreads == 0, "table roles");
-  static_assert(kGroupThreads == kBatch, "one point per thread per batch");
-  const int ej = tg % kBin, eq0 = (tg / kBin) * kEvalPts;
+  static_assert(kGroupThreads == 2 * kBin && kBatch == kGroupThreads, "table roles");
+  const int ej = lane & (kBin - 1), half = lane >> 4;
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
   if (total == 0) return;
@@ -323,8 +329,7 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   RunCursor cur;
   cur.init(start, I.bin_begin, I.nbx, br);
   constexpr int64_t kStride = (int64_t)kGroups * kBatch;
-  auto group_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads)); };
-  int64_t v = (int64_t)g * kBatch + tg;  // this thread's point of the group's current batch
+  int64_t v = (int64_t)g * kBatch + lane;  // this lane's point of the warp's current batch
   float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
   float wf = 0.f;
   if (v < total) {
@@ -334,21 +339,21 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   }
   for (int64_t b0 = (int64_t)g * kBatch; b0 < total; b0 += kStride, v += kStride) {
     const int cnt = (int)min((int64_t)kBatch, total - b0);
-    group_sync();  // the group's previous batch is consumed
-    if (tg < cnt) {
-      T.P[tg] = pf;
-      T.W[tg] = wf;
+    __syncwarp();  // the warp's previous batch is consumed
+    if (lane < cnt) {
+      T.P[lane] = pf;
+      T.W[lane] = wf;
     }
-    group_sync();
+    __syncwarp();
     if (v + kStride < total) {  // next batch, in flight
       const int64_t p = cur.map(v + kStride);
       pf = P[p];
       wf = W[p];
     }
-    // the lanes of a warp write consecutive words: conflict-free
+    // the two half-warps write rows 2k and 2k+1: conflict-free
 #pragma unroll 4
     for (int k = 0; k < kEvalPts; ++k) {
-      const int c = eq0 + k;
+      const int c = 2 * k + half;
       if (c < cnt) {
         const float4 p = T.P[c];
         const float u = (gxe.x - p.x) + (gxe.y - p.y), w = (gye.x - p.z) + (gye.y - p.w);
@@ -361,42 +366,47 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
         }
       }
     }
-    group_sync();
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    __syncwarp();
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     accumulate<KID, RADIAL>(T.KX, T.KY, T.W, cnt, cx, cy0, acc);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) two_sum_acc(run[r], acc[r]);
+    for (int r = 0; r < 8; ++r) two_sum_acc(run[r], acc[r]);
   }
 }
 
-// One CTA per 16x16-cell output block of some instance (blockIdx.x = global
-// block), kGroups point groups of 64 threads: a dense block's points are
-// shared out over the groups, whose (hi, lo) sums are added in group order at
-// the end, so results are reproducible.  Blocks of 16 cells spread a dense
-// region over many CTAs; the finer sort bins keep the points a block reads
-// close to those its cells' supports actually reach.
+// One CTA per 16x16-cell output block of some instance (the order list maps
+// CTAs to blocks, heaviest first), kGroups one-warp point groups: a dense
+// block's points are shared out over the groups, whose (hi, lo) sums are
+// added in group order at the end, so results are reproducible.  Blocks of 16
+// cells spread a dense region over many CTAs; the finer sort bins keep the
+// points a block reads close to those its cells' supports actually reach.
 __global__ void __launch_bounds__(kGroups * kGroupThreads)
     k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
              const float* __restrict__ W, const uint32_t* __restrict__ start,
              const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals) {
-  __shared__ GroupTables tables[kGroups];
-  __shared__ float2 part[kGroups][kGroupThreads][4];
+  // the groups' tables; after every group is done, their partial sums
+  constexpr size_t kTablesBytes = sizeof(GroupTables) * kGroups;
+  constexpr size_t kPartBytes = sizeof(float2) * kGroups * kGroupThreads * 8;
+  __shared__ __align__(16) unsigned char smem[kTablesBytes > kPartBytes ? kTablesBytes
+                                                                        : kPartBytes];
+  GroupTables* tables = reinterpret_cast<GroupTables*>(smem);
+  float2 (*part)[kGroupThreads][8] = reinterpret_cast<float2 (*)[kGroupThreads][8]>(smem);
   int bx, by;
   const int blk = (int)__ldg(order + blockIdx.x);
   const CutInst& I = output_block(tab, ninst, blk, bx, by);
   const int64_t total = __ldg(totals + blk);
-  const int g = threadIdx.x / kGroupThreads, tg = threadIdx.x % kGroupThreads;
-  float2 run[4];
+  const int g = threadIdx.x / kGroupThreads, lane = threadIdx.x % kGroupThreads;
+  float2 run[8];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) run[r] = make_float2(0.f, 0.f);
+  for (int r = 0; r < 8; ++r) run[r] = make_float2(0.f, 0.f);
   GroupTables& T = tables[g];
   switch (I.kid) {
 #define KDE_CUT(K)                                                                      \
   case K:                                                                               \
-    cutoff_group<K, false>(I, P, W, start, bx, by, total, g, tg, T, run);               \
+    cutoff_group<K, false>(I, P, W, start, bx, by, total, g, lane, T, run);             \
     break;                                                                              \
   case kRadial + K:                                                                     \
-    cutoff_group<K, true>(I, P, W, start, bx, by, total, g, tg, T, run);                \
+    cutoff_group<K, true>(I, P, W, start, bx, by, total, g, lane, T, run);              \
     break;
     KDE_CUT(KDE_UNIFORM)
     KDE_CUT(KDE_TRIANGULAR)
@@ -408,21 +418,21 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
 #undef KDE_CUT
     default: break;
   }
+  __syncthreads();  // every group is done with its tables
 #pragma unroll
-  for (int r = 0; r < 4; ++r) part[g][tg][r] = run[r];
+  for (int r = 0; r < 8; ++r) part[g][lane][r] = run[r];
   __syncthreads();
   if (g == 0) {
-    const int cx = tg % kBin, cy0 = (tg / kBin) * 4;
-    const int x = bx * kBin + cx;
+    const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      float2 sum = part[0][tg][r];
+    for (int r = 0; r < 8; ++r) {
+      float2 sum = part[0][lane][r];
       for (int h = 1; h < kGroups; ++h) {
-        const float2 o = part[h][tg][r];
+        const float2 o = part[h][lane][r];
         two_sum_acc(sum, o.x);
         sum.y += o.y;
       }
-      const int y = by * kBin + cy0 + r;
+      const int x = bx * kBin + cx + (r & 1), y = by * kBin + cy0 + (r >> 1);
       if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
     }
   }
