@@ -144,6 +144,8 @@ def parse():
     ap.add_argument("--split-k", type=int, default=0)
     ap.add_argument("--k-chunk", type=int, default=0)
     ap.add_argument("--tile-n", type=int, default=0)
+    ap.add_argument("--h-m", type=float, default=0.0,
+                    help="bandwidth in metres (default: the workload's 100 m)")
     return ap.parse_args()
 
 
@@ -244,6 +246,8 @@ def replica_value(world, evals, ms):
 def make_workload(args):
     import workloads
     wl = workloads.config3(n_traj=args.points, grid=args.grid)
+    if args.h_m > 0:
+        wl.h = args.h_m
     ll, corner, lat0 = wl.lonlat()
     return wl, ll, corner, lat0
 
