@@ -6,12 +6,13 @@
 // outside the grid are dropped), the (key, index) pairs are sorted with a
 // stable LSD radix sort, and each 16x16-cell output block is then computed by
 // one CTA that reads the points of the sort bins within reach of its cells,
-// in sorted order, a batch of 64 at a time: for each batch a point group
-// tabulates the x and y kernel factors of its 16 columns and 16 rows in shared
-// memory, and each thread adds the outer products into its four cells.
-// The blocks run heaviest first.  Nothing is accumulated with atomics, and
-// the order of every sum is fixed, so results are reproducible bit for bit.  The same sort, with 32-cell bins
-// and a wider reach, orders the points of the block-sparse tensor-core path.
+// in sorted order: its eight warps take 32-point batches in turn, tabulate
+// the x and y kernel factors of the block's 16 columns and 16 rows in shared
+// memory, and each thread adds the outer products into its eight cells.  The
+// blocks run heaviest first.  Nothing is accumulated with atomics, and the
+// order of every sum is fixed, so results are reproducible bit for bit.  The
+// same sort, with 32-cell bins and a wider reach, orders the points of the
+// block-sparse tensor-core path.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads, GRUN ? 3 : 2)
       __syncthreads();
       fetch(base + bb + kBatch);
       TableRow cur = table_row(KX, KY, 0, tx, ty);
-#pragma unroll 2
+#pragma unroll 4
       for (int q = 0; q < kBatch; ++q) {
         TableRow nxt = cur;
         if (q + 1 < kBatch) nxt = table_row(KX, KY, q + 1, tx, ty);
