@@ -46,8 +46,10 @@ def sparse_products(xy, origin, cell, nx, ny, h):
     of it (the library's binning, in FP64 here).  Times 65536 cells and 2 FLOP
     per product this is the contraction's algorithmic work."""
     import numpy as np
-    reach, sigma = 6.45, 1.0 / (h * 1.17741002251547469101)
+    sigma = 1.0 / (h * 1.17741002251547469101)
     cs = cell * sigma
+    # the library's ranges widen the reach by the FP32 rounding margin of its bin keys
+    reach = 6.45 + 1e-6 + 8.0 * 2.0 ** -24 * (max(nx, ny) * cs + 6.45)
     inv_binw = 1.0 / (32 * cs)
     nbx, nby = (nx + 31) // 32, (ny + 31) // 32
     X = (xy[:, 0] - origin[0]) * sigma
@@ -80,7 +82,8 @@ def cutoff_pairs(xy, origin, cell, nx, ny, h):
     S = 4 if rc <= 6.0 else 8 if rc <= 16.0 else 16
     while S < 64 and ((nx + S - 1) // S) * ((ny + S - 1) // S) > (1 << 24):
         S *= 2
-    B, cs, reach = 16, cell / h, 1.0 + 1e-6
+    B, cs = 16, cell / h
+    reach = 1.0 + 1e-6 + 8.0 * 2.0 ** -24 * (max(nx, ny) * cs + 1.0)  # as the library's ranges
     inv_binw = 1.0 / (S * cs)
     nbx, nby = (nx + S - 1) // S, (ny + S - 1) // S
     X = (xy[:, 0] - origin[0]) / h

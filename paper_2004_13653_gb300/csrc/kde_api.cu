@@ -581,7 +581,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
                                                  a->h * a->h))
                             : 0.0f;
     q.start = nullptr;
-    q.cs = q.reach = q.inv_binw = 0.0;
+    q.cs = q.reach = q.inv_binw = q.range_reach = 0.0;
     q.nbx = q.nby = q.bin_begin = q.tile_begin = 0;
     if (P.sparse) {  // points in bin order; the sparse reduce writes the output
       q.pts = reinterpret_cast<const float4*>(base + P.off_co_spts);
@@ -590,6 +590,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.start = reinterpret_cast<const uint32_t*>(base + P.off_co_start);
       q.cs = prep[k].cell_sigma;
       q.reach = kSparseReach;
+      q.range_reach = range_reach(kSparseReach, I.geo);
       q.inv_binw = I.geo.inv_binw;
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
@@ -614,6 +615,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.ext_x = I.geo.ext_x;
       q.ext_y = I.geo.ext_y;
       q.reach = 1.0;
+      q.range_reach = range_reach(1.0, I.geo);
       q.cs = A[k].cell / A[k].h;
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
@@ -653,6 +655,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.ext_x = I.geo.ext_x;
       q.ext_y = I.geo.ext_y;
       q.reach = kSparseReach;
+      q.range_reach = range_reach(kSparseReach, I.geo);
       q.cs = A[k].cell * kernel_sigma(KDE_GAUSSIAN, A[k].h);
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;

@@ -50,12 +50,17 @@ __global__ void k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m
     const int64_t p = g - I.cut_begin;
     uint32_t key = total_bins;
     if (p < I.n) {
+      // FP32 throughout (FP64 is slow here): the keys can be one bin off near
+      // a bin edge, which the ranges' widened reach covers
       const float4 q = prepared[I.prep_begin + p];
-      const double X = (double)q.x + (double)q.y, Y = (double)q.z + (double)q.w;
+      const float X = q.x + q.y, Y = q.z + q.w;
+      const float lo = (float)-I.range_reach, inv = (float)I.inv_binw;
+      const float hx = (float)(I.ext_x - I.reach + I.range_reach);
+      const float hy = (float)(I.ext_y - I.reach + I.range_reach);
       // a point reaches the grid only if it lies within the reach of it
-      if (X >= -I.reach && Y >= -I.reach && X <= I.ext_x && Y <= I.ext_y) {
-        const int bx = min(max((int)floor(X * I.inv_binw), 0), I.nbx - 1);
-        const int by = min(max((int)floor(Y * I.inv_binw), 0), I.nby - 1);
+      if (X >= lo && Y >= lo && X <= hx && Y <= hy) {
+        const int bx = min(max((int)floorf(X * inv), 0), I.nbx - 1);
+        const int by = min(max((int)floorf(Y * inv), 0), I.nby - 1);
         key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
       }
     }
@@ -215,11 +220,12 @@ __device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float 
   }
 }
 
-// The sort bins whose points can reach output block (bx, by): a millionth of
-// a bandwidth wider than the support, so the points left out have |u| or |v|
-// above 1 in FP32 too and their factors are exactly zero.
+// The sort bins whose points can reach output block (bx, by), with the
+// widened reach: the points left out have |u| or |v| above 1 in FP32 too, so
+// their factors are exactly zero, and those whose FP32 key put them a bin
+// further are still in.
 __device__ __forceinline__ BinRange output_block_bins(const CutInst& I, int bx, int by) {
-  return block_bins(I.cs, I.reach + 1e-6, I.inv_binw, I.nbx, I.nby, bx * kBin, by * kBin, kBin);
+  return block_bins(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby, bx * kBin, by * kBin, kBin);
 }
 
 // The instance of global output block blk, and the block's position in it.

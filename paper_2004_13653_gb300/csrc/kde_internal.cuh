@@ -105,6 +105,7 @@ struct TcInst {
   // block-sparse skipping (pts / wts then hold the points in bin order)
   const uint32_t* start;  // bin starts of the shared sort
   double cs, reach, inv_binw;  // cell and reach in prepared units, 1 / bin width
+  double range_reach;          // reach plus the bin keys' FP32 rounding margin (ranges use it)
   int nbx, nby, bin_begin, tile_begin;
 };
 
@@ -204,6 +205,11 @@ struct CutInst {
   float* out;
   int64_t n, n_pad, prep_begin, cut_begin;  // point ranges (prepared / cutoff spaces)
   double inv_binw, ext_x, ext_y, reach, cs; // reach: support radius, cs: cell side (prepared units)
+  // reach widened by more than the FP32 rounding of the bin keys: every range
+  // of bins (and the keys' reach test) uses it, so a point whose key landed
+  // one bin off is still read by every block it can reach; the extra points
+  // contribute exact zeros
+  double range_reach;
   int nbx, nby, bin_begin, nx, ny, kid;
   int obx, oby, out_begin;
   float scale;
@@ -265,6 +271,14 @@ constexpr int kSparseBin = 32;
 // Sort bins of `bin` cells; cs: cell side in prepared units; reach: support
 // radius in prepared units.
 CutoffGeom cutoff_geometry(int nx, int ny, double cs, double reach, int bin);
+// The reach the bin ranges use: the keys are computed in FP32 from the hi/lo
+// coordinates, within 3 units of 2^-24 of the coordinate's magnitude (at most
+// the geometry's extent) of the exact position; the margin is 8 such units
+// plus a millionth of a bandwidth.
+inline double range_reach(double reach, const CutoffGeom& g) {
+  const double ext = g.ext_x > g.ext_y ? g.ext_x : g.ext_y;
+  return reach + 1e-6 + 8.0 * 0x1p-24 * ext;
+}
 // The cutoff path's sort-bin side for a support of reach_cells cells: small
 // enough that an output block reads little beyond its support's reach, large
 // enough that the number of bins stays bounded.

@@ -48,7 +48,7 @@ __global__ void k_sparse_totals(const TcInst* __restrict__ tab, int ninst, Spars
   const TcInst& I = tab[inst_of_tile(tab, ninst, t)];
   const int local = t - I.tile_begin;
   const int tm = local % I.tiles_m, tn = local / I.tiles_m;
-  const BinRange br = tile_bins(I.cs, I.reach, I.inv_binw, I.nbx, I.nby, tm, tn);
+  const BinRange br = tile_bins(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby, tm, tn);
   uint64_t total = 0;
   for (int by = br.lo_by; br.lo_bx <= br.hi_bx && by <= br.hi_by; ++by) {
     const int row = I.bin_begin + by * I.nbx;

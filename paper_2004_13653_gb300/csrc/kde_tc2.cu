@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
       RunCursor cur;
       if (SPARSE)  // items exist only for tiles whose range holds points
         cur.init(I.start, I.bin_begin, I.nbx,
-                 tile_bins(I.cs, I.reach, I.inv_binw, I.nbx, I.nby, itm.tm, itm.tn));
+                 tile_bins(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby, itm.tm, itm.tn));
       for (int st = 0; ok && st < itm.nst; st += kGroup) {
         const int ng = min(kGroup, itm.nst - st);
         float4 P[kGroup][2];
