@@ -483,6 +483,15 @@ int acquire_workspace(const kde_opts* o, size_t need, cudaStream_t s, void** ws)
   return library_workspace(need, ws);
 }
 
+// The bin-key kernel's FP32 constants of a sort instance (set after its
+// geometry and reach).
+void set_key_constants(CutInst& q) {
+  q.key_lo = (float)-q.range_reach;
+  q.key_hx = (float)(q.ext_x - q.reach + q.range_reach);
+  q.key_hy = (float)(q.ext_y - q.reach + q.range_reach);
+  q.key_inv = (float)q.inv_binw;
+}
+
 // Plan, lay out, upload and launch every instance of a batch on one stream.
 int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) {
   for (int k = 0; k < count; ++k) {
@@ -616,6 +625,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.ext_y = I.geo.ext_y;
       q.reach = 1.0;
       q.range_reach = range_reach(1.0, I.geo);
+      set_key_constants(q);
       q.cs = A[k].cell / A[k].h;
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
@@ -657,6 +667,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
       q.reach = kSparseReach;
       q.range_reach = range_reach(kSparseReach, I.geo);
       q.cs = A[k].cell * kernel_sigma(KDE_GAUSSIAN, A[k].h);
+      set_key_constants(q);
       q.nbx = I.geo.nbx;
       q.nby = I.geo.nby;
       q.bin_begin = I.bin_begin;

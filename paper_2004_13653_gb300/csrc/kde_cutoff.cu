@@ -54,13 +54,10 @@ __global__ void k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m
       // a bin edge, which the ranges' widened reach covers
       const float4 q = prepared[I.prep_begin + p];
       const float X = q.x + q.y, Y = q.z + q.w;
-      const float lo = (float)-I.range_reach, inv = (float)I.inv_binw;
-      const float hx = (float)(I.ext_x - I.reach + I.range_reach);
-      const float hy = (float)(I.ext_y - I.reach + I.range_reach);
       // a point reaches the grid only if it lies within the reach of it
-      if (X >= lo && Y >= lo && X <= hx && Y <= hy) {
-        const int bx = min(max((int)floorf(X * inv), 0), I.nbx - 1);
-        const int by = min(max((int)floorf(Y * inv), 0), I.nby - 1);
+      if (X >= I.key_lo && Y >= I.key_lo && X <= I.key_hx && Y <= I.key_hy) {
+        const int bx = min(max((int)floorf(X * I.key_inv), 0), I.nbx - 1);
+        const int by = min(max((int)floorf(Y * I.key_inv), 0), I.nby - 1);
         key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
       }
     }

@@ -210,6 +210,9 @@ struct CutInst {
   // one bin off is still read by every block it can reach; the extra points
   // contribute exact zeros
   double range_reach;
+  // the keys' FP32 constants: accepted coordinates [key_lo, key_hx] x
+  // [key_lo, key_hy], 1 / bin width
+  float key_lo, key_hx, key_hy, key_inv;
   int nbx, nby, bin_begin, nx, ny, kid;
   int obx, oby, out_begin;
   float scale;
