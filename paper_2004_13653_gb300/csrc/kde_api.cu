@@ -77,6 +77,25 @@ int library_workspace(size_t need, void** out) {
   return KDE_OK;
 }
 
+// A second stream per device, at the lowest priority, for work that overlaps
+// the tensor-core contraction (created on first use, kept until release).
+cudaStream_t g_side[kMaxDevices] = {};
+
+int side_stream(cudaStream_t* out) {
+  int dev = 0;
+  KDE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(KDE_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  if (!g_side[dev]) {
+    int least = 0, greatest = 0;
+    KDE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priority range");
+    KDE_CUDA(cudaStreamCreateWithPriority(&g_side[dev], cudaStreamNonBlocking, least),
+             "create the side stream");
+  }
+  *out = g_side[dev];
+  return KDE_OK;
+}
+
 // 0: device or managed memory, 1: host memory (pinned or pageable)
 int memory_kind(const void* p) {
   cudaPointerAttributes at;
@@ -711,9 +730,31 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     cs.order = reinterpret_cast<uint32_t*>(base + P.off_co_order);
     cs.totals = reinterpret_cast<uint32_t*>(base + P.off_co_totals);
     cs.ocount = reinterpret_cast<uint32_t*>(base + P.off_co_ocount);
+  }
+  // The compact instances (sort and gather) overlap the tensor-core
+  // contraction on the side stream when no block-sparse instance needs the
+  // sort first: the contraction is enqueued first, its CTAs take every SM,
+  // the small sort kernels fit beside them and the gather fills the SMs its
+  // tail frees.  They write disjoint buffers, so results do not change.
+  const bool overlap = P.n_cut && P.n_tc && !P.sparse;
+  cudaStream_t s2 = s;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  struct EventGuard {
+    cudaEvent_t* e[2];
+    ~EventGuard() {
+      for (cudaEvent_t* x : e)
+        if (*x) cudaEventDestroy(*x);
+    }
+  } guard{{&fork, &join}};
+  if (overlap) {
+    if (int rc = side_stream(&s2)) return rc;
+    KDE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "create event");
+    KDE_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming), "create event");
+    KDE_CUDA(cudaEventRecord(fork, s), "fork to the side stream");
+  }
+  if ((P.n_cut || P.sparse) && !overlap)
     KDE_CUDA(launch_bin_sort(d_cut, (int)cut.size(), P.cut_m, P.total_bins, pts, wts, P.cz, cs, s),
              "bin sort");
-  }
   if (P.n_tc && P.sparse) {
     SparseCtl sp;
     sp.piece_begin = reinterpret_cast<const uint32_t*>(base + P.off_sp_pb);
@@ -744,8 +785,16 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
                          reinterpret_cast<float2*>(base + I.off_run), part_of(k), s),
              "SIMT direct sum");
   }
-  if (P.n_cut)
+  if (overlap) {
+    KDE_CUDA(cudaStreamWaitEvent(s2, fork, 0), "side stream waits for the prepared points");
+    KDE_CUDA(launch_bin_sort(d_cut, (int)cut.size(), P.cut_m, P.total_bins, pts, wts, P.cz, cs, s2),
+             "bin sort");
+    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, cs, s2), "cutoff evaluation");
+    KDE_CUDA(cudaEventRecord(join, s2), "join from the side stream");
+    KDE_CUDA(cudaStreamWaitEvent(s, join, 0), "join the side stream");
+  } else if (P.n_cut) {
     KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, cs, s), "cutoff evaluation");
+  }
   if (ev) KDE_CUDA(cudaEventRecord(ev[1], s), "record end event");
   if (P.n_reduce) KDE_CUDA(launch_reduce(d_red, P.n_reduce, P.reduce_cells, s), "split-K reduce");
   if (P.host_out)
@@ -1049,6 +1098,11 @@ int kde_release(void) {
       cudaFree(g_ws_ptr[d]);
       g_ws_ptr[d] = nullptr;
       g_ws_bytes[d] = 0;
+    }
+    if (g_side[d]) {
+      cudaSetDevice(d);
+      cudaStreamDestroy(g_side[d]);
+      g_side[d] = nullptr;
     }
   }
   cudaSetDevice(prev);
