@@ -138,3 +138,42 @@ def test_radial_gaussian_is_the_gaussian_and_simt_rejects_radial():
     np.testing.assert_array_equal(a, b)
     with pytest.raises(RuntimeError):
         run_gpu(wl, oracle.RADIAL + oracle.EPANECHNIKOV, path="simt")
+
+
+@pytest.mark.parametrize("kid", COMPACT, ids=[oracle.KERNEL_NAMES[k] for k in COMPACT])
+def test_all_compact_kernels_sort_bins_of_8(kid):
+    """h = 12 cells (8-cell sort bins) for every compact kernel, ragged grid."""
+    wl = workloads.random_points(560 + kid, 2000, 2600.0, 10.0, 230, 170, 120.0, kid)
+    if kid == oracle.UNIFORM:
+        wl = clear_of_support_edge(wl, radial=False)
+    F = run_gpu(wl, kid)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("kid", [oracle.EPANECHNIKOV, oracle.RADIAL + oracle.TRIWEIGHT],
+                         ids=["epanechnikov", "radial_triweight"])
+def test_points_on_sort_bin_edges_far_from_origin(kid):
+    """A 20,000-cell-wide grid (coordinates up to 10^4 bandwidths, where the
+    FP32 bin keys are coarsest) with points exactly on sort-bin edges, one
+    cell either side of them and at random, near the far end: the points a
+    block reads must still include every point within a bandwidth of its
+    cells."""
+    rng = np.random.default_rng(570 + kid)
+    cell, nx, ny, h = 10.0, 20000, 48, 20.0  # h = 2 cells: 4-cell sort bins
+    k = rng.integers(4900, 5000, 400).astype(np.float64)
+    edges = k * 4 * cell
+    xs = np.concatenate([edges, edges + cell, edges - cell, rng.uniform(19_500 * cell, nx * cell, 400)])
+    ys = rng.uniform(0.0, ny * cell, xs.size)
+    wl = workloads.random_points(571, xs.size, 1.0, cell, nx, ny, h, kid % oracle.RADIAL)
+    wl.local[:] = np.stack([xs, ys], axis=1)
+    F = run_gpu(wl, kid)
+    # the cells around the first 300 edge points (and their neighbours one cell off)
+    ci = np.floor(xs[:300] / cell).astype(np.int64)
+    cj = np.floor(ys[:300] / cell).astype(np.int64)
+    cells = np.unique(np.concatenate([
+        np.clip(cj + dj, 0, ny - 1) * nx + np.clip(ci + di, 0, nx - 1)
+        for di in range(-3, 4) for dj in (-1, 0, 1)]))
+    ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
+    assert np.max(ref) > 0
+    assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
