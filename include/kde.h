@@ -247,9 +247,12 @@ int kde_grid_binned(const double* points, const int64_t* traj_offsets, int64_t n
  * metres; keep: device [n] (1 = kept); out_points: device [2n] or NULL,
  * receives the kept points in order; out_offsets: device [ntraj+1] or NULL,
  * the trajectories' bounds in out_points; n_kept, iterations: host, optional.
- * Synchronous (the loop ends when an iteration keeps no point; one host read
- * per iteration).  Errors: KDE_EINVAL (n, eps, pointers, alignment, offsets
- * that do not rise from 0 to n), KDE_EDATA (non-finite coordinate).
+ * Synchronous: every iteration runs inside one cooperative launch (the loop
+ * ends on the device when an iteration keeps no point), and the call reads
+ * the iteration count and the kept count back once.  Errors: KDE_EINVAL (n,
+ * eps, pointers, alignment, offsets that do not rise from 0 to n), KDE_EDATA
+ * (non-finite coordinate), KDE_ECUDA (the device cannot hold the cooperative
+ * launch's CTAs at once).
  */
 int kde_dp_simplify(const double* points, const int64_t* traj_offsets, int64_t ntraj,
                     int64_t n, double eps, uint8_t* keep, double* out_points,
