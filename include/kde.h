@@ -172,7 +172,11 @@ int kde_project_mercator(const double* lonlat_deg, int64_t n, double lat0_deg,
  * compact kernels: binned cutoff path) unless opts->path forces
  * KDE_PATH_SIMT_FP32.  Asynchronous on opts->stream unless KDE_FLAG_SYNC;
  * graph-capturable when the workspace is already large enough (call once
- * outside capture, or pass opts->workspace).
+ * outside capture, or pass opts->workspace).  When a batch holds both
+ * Gaussian and compact instances (and no block-sparse ones), the compact
+ * instances run on a library-owned low-priority stream forked from and joined
+ * back to opts->stream by events, so they overlap the tensor-core
+ * contraction; the call stays ordered on opts->stream as a whole.
  */
 int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts);
 
