@@ -588,12 +588,13 @@ def extra_workloads(dev):
     G = torch.rand((raw.ny, raw.nx), device=dev, generator=torch.Generator(dev).manual_seed(5))
     args5 = (thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0)
     fwd_ms = _time(lambda: kde.grid(*args5, "gaussian"), reps=5)
+    fwd_sparse_ms = _time(lambda: kde.grid(*args5, "gaussian", flags=kde.FLAG_SKIP_ZERO), reps=5)
     bwd_ms = _time(lambda: kde.grid_backward(*args5, G), reps=5)
     F5 = kde.grid(*args5, "gaussian")
     lscv_ms = _time(lambda: kde.lscv_grid(F5, *args5), reps=5)
     out["forward_adjoint_lscv_1024sq"] = {
-        "points": int(thin.shape[0]), "forward_ms": fwd_ms, "adjoint_ms": bwd_ms,
-        "lscv_ms": lscv_ms,
+        "points": int(thin.shape[0]), "forward_ms": fwd_ms,
+        "forward_block_sparse_ms": fwd_sparse_ms, "adjoint_ms": bwd_ms, "lscv_ms": lscv_ms,
         "note": "adjoint: one warp per point over its +-8h window (dL/dw, dL/dpoints, dL/dh)"}
     torch.cuda.synchronize()
     t0 = time.perf_counter()

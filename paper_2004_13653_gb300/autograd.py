@@ -1,8 +1,9 @@
 """torch.autograd wrappers over the library's density, adjoint and LSCV kernels.
 
 KDEGridFn: F = density(points, w, h) on the grid (Gaussian, split-FP16
-tensor-core path by default); backward runs kde_grid_backward (dL/dpoints,
-dL/dw, dL/dh recomputed from the exponentials, nothing stored).
+tensor-core path with block-sparse skipping by default); backward runs
+kde_grid_backward (dL/dpoints, dL/dw, dL/dh recomputed from the exponentials,
+nothing stored).
 LSCVFn: L = the grid least-squares cross-validation loss of F (kde_lscv_grid);
 backward returns dL/dF and the loss's direct partials.
 fit_bandwidth: Adam on (log h, weight logits) minimising the LSCV loss, the
@@ -16,15 +17,19 @@ import os
 
 import torch
 
-from . import grid, grid_backward, lscv_grid
+from . import FLAG_SKIP_ZERO, grid, grid_backward, lscv_grid
 
 
 class KDEGridFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, points, weights, h, origin, cell, nx, ny, path="tc_split16"):
         hv = float(h)
+        # on the tensor paths, skip the (tile, point) pairs whose products are
+        # exactly zero in FP16: the same density, far fewer products at the
+        # bandwidths a fit explores
+        flags = FLAG_SKIP_ZERO if path in ("tc_split16", "tc_fp16") else 0
         F = grid(points.detach().contiguous(), weights.detach().contiguous(), origin, cell, nx, ny,
-                 hv, "gaussian", path=path)
+                 hv, "gaussian", path=path, flags=flags)
         ctx.save_for_backward(points, weights)
         ctx.hv, ctx.geom = hv, (origin, cell, nx, ny)
         ctx.h_like = h
