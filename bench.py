@@ -595,7 +595,8 @@ def extra_workloads(dev):
     out["forward_adjoint_lscv_1024sq"] = {
         "points": int(thin.shape[0]), "forward_ms": fwd_ms,
         "forward_block_sparse_ms": fwd_sparse_ms, "adjoint_ms": bwd_ms, "lscv_ms": lscv_ms,
-        "note": "adjoint: one warp per point over its +-8h window (dL/dw, dL/dpoints, dL/dh)"}
+        "note": "adjoint: a warp per 32 points, each over its +-8h window in turn "
+                "(dL/dw, dL/dpoints, dL/dh)"}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h, _, losses = kag.fit_bandwidth(thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,

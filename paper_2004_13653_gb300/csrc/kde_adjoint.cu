@@ -10,9 +10,12 @@
 //   dL/dh   = -(2/h) sum_ij G_ij F_ij + c/h sum_p w_p sum_ij G_ij (s^2 + t^2) A B
 // and sum_ij G_ij F_ij = sum_p w_p dL/dw_p, so F itself is not needed.
 //
-// One warp per point: lanes take the columns of the point's window, the rows
-// are walked in order, and the four sums are reduced across the warp in a
-// fixed order (reproducible).  The window spans +-8 bandwidths (clamped to the
+// One warp per point in turn, over batches of 32 points: lanes take the
+// columns of the point's window, the rows are walked in order, and the four
+// sums are reduced across the warp in a fixed order (reproducible).  The
+// window itself (FP64, slow on this part) is found once per point, by the
+// lane that later writes the point's results; the batch's points, windows
+// and sums pass between the lanes through shared memory.  The window spans +-8 bandwidths (clamped to the
 // grid): beyond it every term is below exp(-32) of the largest, far under the
 // accuracy of the FP32 sums.
 #include "kde_internal.cuh"
@@ -27,70 +30,96 @@ __device__ __forceinline__ float gauss(float s) { return ex2_approx(-0.5f * kLog
 
 // COLS: window columns a lane keeps in registers per block of 32 * COLS
 // columns (the host picks the smallest power of two that covers the window).
+// A window of at most 16 columns takes 2^sub_log2 >= its width lanes per row
+// and 32 / 2^sub_log2 rows at a time (sub_log2 = 5 otherwise).
 template <int COLS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, COLS == 1 ? 6 : 1)  // COLS = 1: 40 registers
     k_adjoint_gauss(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n,
                     const float* __restrict__ G, const float2* __restrict__ gxt,
                     const float2* __restrict__ gyt, int nx, int ny, double cell_s, int R,
-                    float c, float inv_h, float* __restrict__ grad_xy,
+                    int sub_log2, float c, float inv_h, float* __restrict__ grad_xy,
                     float* __restrict__ grad_w, double* __restrict__ hterm,
                     double* __restrict__ lterm) {
-  const int lane = threadIdx.x & 31;
+  // per warp: the batch's points, windows and reduced sums (one slot per point)
+  __shared__ float4 sP[8][32];
+  __shared__ int4 sWin[8][32];
+  __shared__ float4 sSum[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // lanes in groups of 2^sub_log2 over the columns; group g takes rows g, g + ng, ...
+  const int ci = lane & ((1 << sub_log2) - 1), rg = lane >> sub_log2, ng = 32 >> sub_log2;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
-    const float4 P = pts[p];
-    const float w = wts[p];
-    // window of cells within R of the point's cell (X, Y in bandwidths)
-    const double X = (double)P.x + (double)P.y, Y = (double)P.z + (double)P.w;
-    const int ic = (int)floor(X / cell_s), jc = (int)floor(Y / cell_s);
-    const int i0 = max(ic - R, 0), i1 = min(ic + R, nx - 1);
-    const int j0 = max(jc - R, 0), j1 = min(jc + R, ny - 1);
-    float aw = 0.f, ax = 0.f, ay = 0.f, ah = 0.f;
-    if (i0 <= i1 && j0 <= j1) {
-      for (int ib = i0; ib <= i1; ib += 32 * COLS) {
-        float A[COLS], S[COLS];
-        int col[COLS];
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          const int i = ib + lane + 32 * k;
-          col[k] = i <= i1 ? i : -1;
-          const float2 g = gxt[min(i, nx - 1)];
-          S[k] = (g.x - P.x) + (g.y - P.y);
-          A[k] = col[k] >= 0 ? gauss(S[k]) : 0.f;
-        }
-        // rows in order, four per iteration so their loads are in flight together
-#pragma unroll 4
-        for (int j = j0; j <= j1; ++j) {
-          const float2 g = gyt[j];
-          const float t = (g.x - P.z) + (g.y - P.w);
-          const float B = gauss(t);
-          const float* Grow = G + (int64_t)j * nx;
+  for (int64_t pb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; pb < n;
+       pb += warps * 32) {
+    // Lane l prepares point pb + l: its window of cells within R of its cell
+    // (X, Y in bandwidths).  This is the FP64 part, so it runs once per point
+    // instead of once per lane of the warp.
+    const int64_t pl = pb + lane;
+    if (pl < n) {
+      const float4 P = pts[pl];
+      const double X = (double)P.x + (double)P.y, Y = (double)P.z + (double)P.w;
+      const int ic = (int)floor(X / cell_s), jc = (int)floor(Y / cell_s);
+      sP[wib][lane] = P;
+      sWin[wib][lane] = make_int4(max(ic - R, 0), min(ic + R, nx - 1), max(jc - R, 0),
+                                  min(jc + R, ny - 1));
+    }
+    __syncwarp();
+    const int cnt = n - pb < 32 ? (int)(n - pb) : 32;
+    for (int q = 0; q < cnt; ++q) {
+      const float4 P = sP[wib][q];
+      const int4 win = sWin[wib][q];
+      const int i0 = win.x, i1 = win.y, j0 = win.z, j1 = win.w;
+      float aw = 0.f, ax = 0.f, ay = 0.f, ah = 0.f;
+      if (i0 <= i1 && j0 <= j1) {
+        for (int ib = i0; ib <= i1; ib += 32 * COLS) {
+          float A[COLS], S[COLS];
+          int col[COLS];
 #pragma unroll
           for (int k = 0; k < COLS; ++k) {
-            const float Gv = col[k] >= 0 ? __ldg(Grow + col[k]) : 0.f;
-            const float q = Gv * B * A[k];
-            aw += q;
-            ax = fmaf(S[k], q, ax);
-            ay = fmaf(t, q, ay);
-            ah = fmaf(fmaf(S[k], S[k], t * t), q, ah);
+            const int i = ib + ci + 32 * k;
+            col[k] = i <= i1 ? i : -1;
+            const float2 g = gxt[min(i, nx - 1)];
+            S[k] = (g.x - P.x) + (g.y - P.y);
+            A[k] = col[k] >= 0 ? gauss(S[k]) : 0.f;
+          }
+          // rows in order, four per iteration so their loads are in flight together
+#pragma unroll 4
+          for (int j = j0 + rg; j <= j1; j += ng) {
+            const float2 g = gyt[j];
+            const float t = (g.x - P.z) + (g.y - P.w);
+            const float B = gauss(t);
+            const float* Grow = G + (int64_t)j * nx;
+#pragma unroll
+            for (int k = 0; k < COLS; ++k) {
+              const float Gv = col[k] >= 0 ? __ldg(Grow + col[k]) : 0.f;
+              const float v = Gv * B * A[k];
+              aw += v;
+              ax = fmaf(S[k], v, ax);
+              ay = fmaf(t, v, ay);
+              ah = fmaf(fmaf(S[k], S[k], t * t), v, ah);
+            }
           }
         }
       }
+      for (int o = 16; o > 0; o >>= 1) {
+        aw += __shfl_xor_sync(0xffffffffu, aw, o);
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        ah += __shfl_xor_sync(0xffffffffu, ah, o);
+      }
+      if (lane == 0) sSum[wib][q] = make_float4(aw, ax, ay, ah);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      aw += __shfl_xor_sync(0xffffffffu, aw, o);
-      ax += __shfl_xor_sync(0xffffffffu, ax, o);
-      ay += __shfl_xor_sync(0xffffffffu, ay, o);
-      ah += __shfl_xor_sync(0xffffffffu, ah, o);
+    __syncwarp();
+    if (pl < n) {
+      const float w = wts[pl];
+      const float4 r = sSum[wib][lane];
+      const float gw = c * r.x;
+      if (grad_w) grad_w[pl] = gw;
+      grad_xy[2 * pl] = c * w * inv_h * r.y;
+      grad_xy[2 * pl + 1] = c * w * inv_h * r.z;
+      hterm[pl] = (double)c * w * inv_h * r.w;
+      lterm[pl] = (double)w * gw;
     }
-    if (lane == 0) {
-      const float gw = c * aw;
-      if (grad_w) grad_w[p] = gw;
-      grad_xy[2 * p] = c * w * inv_h * ax;
-      grad_xy[2 * p + 1] = c * w * inv_h * ay;
-      hterm[p] = (double)c * w * inv_h * ah;
-      lterm[p] = (double)w * gw;
-    }
+    __syncwarp();
   }
 }
 
@@ -222,10 +251,13 @@ cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n,
   const int R = (int)ceil(8.0 * h / cell) + 1;
   const float c = (float)(1.0 / (2.0 * 3.14159265358979323846 * (double)n * h * h));
   const int width = 2 * R + 1;
-  const int blocks = grid_blocks(n * 32, 256, 152 * 64);
+  const int blocks = grid_blocks((n + 31) / 32 * 32, 256, 152 * 64);  // a warp per 32 points
+  int sub_log2 = 0;
+  while ((1 << sub_log2) < width && sub_log2 < 5) ++sub_log2;
 #define KDE_ADJ(C)                                                                          \
-  k_adjoint_gauss<C><<<blocks, 256, 0, s>>>(pts, wts, n, G, gxt, gyt, nx, ny, cell / h, R, c, \
-                                            (float)(1.0 / h), grad_xy, grad_w, hterm, lterm)
+  k_adjoint_gauss<C><<<blocks, 256, 0, s>>>(pts, wts, n, G, gxt, gyt, nx, ny, cell / h, R,    \
+                                            C == 1 ? sub_log2 : 5, c, (float)(1.0 / h),     \
+                                            grad_xy, grad_w, hterm, lterm)
   if (width <= 32) KDE_ADJ(1);
   else if (width <= 64) KDE_ADJ(2);
   else if (width <= 128) KDE_ADJ(4);

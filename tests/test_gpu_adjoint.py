@@ -57,6 +57,23 @@ def test_adjoint_wide_bandwidth_whole_grid_window():
     assert gh == pytest.approx(rh, rel=TOL_GRAD)
 
 
+@pytest.mark.parametrize("h_cells,n", [(0.1, 7), (0.3, 300), (0.7, 333), (1.2, 65), (1.7, 301)])
+def test_adjoint_narrow_windows(h_cells, n):
+    """Windows of 5, 9, 15, 23 and 31 columns: at most 16 columns take 32 / 2^k
+    rows at a time (2^k >= width lanes per row); batches of 32 points per warp
+    end ragged (7, 333, 65 and 301 points; the seeds keep the h-term's
+    cancellation below 100x)."""
+    wl = workloads.random_points(902 + n, n, 600.0, 10.0, 60, 50, 10.0 * h_cells,
+                                 oracle.GAUSSIAN)
+    G = np.random.default_rng(902).normal(0, 1, (50, 60))
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, 60, 50, wl.h, _dev(G, torch.float32))
+    rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, 60, 50, wl.h, G)
+    assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
+    assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    assert gh == pytest.approx(rh, rel=TOL_GRAD)
+
+
 def test_lscv_loss_cotangent_and_direct_terms_match_oracle():
     wl, _ = _case(902, 400)
     F = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
