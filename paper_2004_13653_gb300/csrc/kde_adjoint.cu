@@ -33,7 +33,8 @@ __device__ __forceinline__ float gauss(float s) { return ex2_approx(-0.5f * kLog
 // A window of at most 16 columns takes 2^sub_log2 >= its width lanes per row
 // and 32 / 2^sub_log2 rows at a time (sub_log2 = 5 otherwise).
 template <int COLS>
-__global__ void __launch_bounds__(256, COLS == 1 ? 6 : 1)  // COLS = 1: 40 registers
+// (the blocks per SM each COLS fits without spilling registers)
+__global__ void __launch_bounds__(256, COLS == 1 ? 5 : (COLS == 2 ? 4 : (COLS == 4 ? 3 : 1)))
     k_adjoint_gauss(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n,
                     const float* __restrict__ G, const float2* __restrict__ gxt,
                     const float2* __restrict__ gyt, int nx, int ny, double cell_s, int R,
@@ -71,32 +72,42 @@ __global__ void __launch_bounds__(256, COLS == 1 ? 6 : 1)  // COLS = 1: 40 regis
       float aw = 0.f, ax = 0.f, ay = 0.f, ah = 0.f;
       if (i0 <= i1 && j0 <= j1) {
         for (int ib = i0; ib <= i1; ib += 32 * COLS) {
-          float A[COLS], S[COLS];
+          // per column: A, s A and s^2 A (zero outside the window)
+          float A[COLS], SA[COLS], S2A[COLS];
           int col[COLS];
 #pragma unroll
           for (int k = 0; k < COLS; ++k) {
             const int i = ib + ci + 32 * k;
             col[k] = i <= i1 ? i : -1;
             const float2 g = gxt[min(i, nx - 1)];
-            S[k] = (g.x - P.x) + (g.y - P.y);
-            A[k] = col[k] >= 0 ? gauss(S[k]) : 0.f;
+            const float S = (g.x - P.x) + (g.y - P.y);
+            A[k] = col[k] >= 0 ? gauss(S) : 0.f;
+            SA[k] = S * A[k];
+            S2A[k] = S * SA[k];
           }
-          // rows in order, four per iteration so their loads are in flight together
+          // Rows in order, four per iteration so their loads are in flight
+          // together.  The window sum is separable: with the lane's row sums
+          // u = sum G A, v = sum G s A, x = sum G s^2 A,
+          //   w += B u,  x_p += B v,  y_p += t B u,  h += B x + t^2 B u.
 #pragma unroll 4
           for (int j = j0 + rg; j <= j1; j += ng) {
             const float2 g = gyt[j];
             const float t = (g.x - P.z) + (g.y - P.w);
             const float B = gauss(t);
             const float* Grow = G + (int64_t)j * nx;
+            float u = 0.f, v = 0.f, x = 0.f;
 #pragma unroll
             for (int k = 0; k < COLS; ++k) {
               const float Gv = col[k] >= 0 ? __ldg(Grow + col[k]) : 0.f;
-              const float v = Gv * B * A[k];
-              aw += v;
-              ax = fmaf(S[k], v, ax);
-              ay = fmaf(t, v, ay);
-              ah = fmaf(fmaf(S[k], S[k], t * t), v, ah);
+              u = fmaf(Gv, A[k], u);
+              v = fmaf(Gv, SA[k], v);
+              x = fmaf(Gv, S2A[k], x);
             }
+            const float Bu = B * u;
+            aw += Bu;
+            ax = fmaf(B, v, ax);
+            ay = fmaf(t, Bu, ay);
+            ah = fmaf(B, x, fmaf(t * t, Bu, ah));
           }
         }
       }
