@@ -23,6 +23,11 @@
  *   - Streams: kde_grid_ex and friends enqueue on opts->stream (a
  *     cudaStream_t; NULL = the legacy default stream) and return without
  *     waiting unless KDE_FLAG_SYNC is set.  kde_grid() always waits.
+ *     Calls that use the library's workspace are ordered only by their
+ *     streams: calls in flight at the same time on different streams of one
+ *     device (from one host thread or several) must each pass their own
+ *     workspace in kde_opts; on one stream, or on streams the caller orders
+ *     with events, the library's workspace is safe.
  *   - Layout: points are interleaved (x0, y0, x1, y1, ...) FP64 metres;
  *     weights are FP32 (NULL = all ones); out is FP32 row-major [ny][nx]
  *     with out[j*nx + i] and is overwritten.
