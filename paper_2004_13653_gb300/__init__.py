@@ -5,6 +5,11 @@ marshals arguments (torch tensors or numpy arrays, device or host) to the
 library, whose kernels do every step of the computation.  There is no CPU
 fallback: importing the binding on a machine where ``libkde_gb300.so`` is
 missing raises.
+
+Calls run on the torch current stream (or ``stream=``) and share the
+library's device workspace, which only stream order protects: calls in
+flight at the same time on different streams of one device each pass their
+own ``workspace=`` (a device buffer of ``workspace_size(...)`` bytes).
 """
 from __future__ import annotations
 
