@@ -11,13 +11,16 @@
 // and sum_ij G_ij F_ij = sum_p w_p dL/dw_p, so F itself is not needed.
 //
 // One warp per point in turn, over batches of 32 points: lanes take the
-// columns of the point's window, the rows are walked in order, and the four
-// sums are reduced across the warp in a fixed order (reproducible).  The
-// window itself (FP64, slow on this part) is found once per point, by the
-// lane that later writes the point's results; the batch's points, windows
-// and sums pass between the lanes through shared memory.  The window spans +-8 bandwidths (clamped to the
-// grid): beyond it every term is below exp(-32) of the largest, far under the
-// accuracy of the FP32 sums.
+// columns of the point's window (for a window of at most 16 columns, groups
+// of lanes take alternate rows), the rows are walked in order, and the four
+// sums are reduced across the warp in a fixed order (reproducible).  The sum
+// over a window is separable: per row, three FMAs per cell form sum G A,
+// sum G s A and sum G s^2 A, which the row's B and t then weight.  The window
+// itself (FP64) is found once per point, by the lane that later writes the
+// point's results; the batch's points, windows and sums pass between the
+// lanes through shared memory.  The window spans +-8 bandwidths (clamped to
+// the grid): beyond it every term is below exp(-32) of the largest, far under
+// the accuracy of the FP32 sums.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
 
@@ -31,9 +34,9 @@ __device__ __forceinline__ float gauss(float s) { return ex2_approx(-0.5f * kLog
 // COLS: window columns a lane keeps in registers per block of 32 * COLS
 // columns (the host picks the smallest power of two that covers the window).
 // A window of at most 16 columns takes 2^sub_log2 >= its width lanes per row
-// and 32 / 2^sub_log2 rows at a time (sub_log2 = 5 otherwise).
+// and 32 / 2^sub_log2 rows at a time (sub_log2 = 5 otherwise).  The launch
+// bounds are the blocks per SM each COLS fits without spilling registers.
 template <int COLS>
-// (the blocks per SM each COLS fits without spilling registers)
 __global__ void __launch_bounds__(256, COLS == 1 ? 5 : (COLS == 2 ? 4 : (COLS == 4 ? 3 : 1)))
     k_adjoint_gauss(const float4* __restrict__ pts, const float* __restrict__ wts, int64_t n,
                     const float* __restrict__ G, const float2* __restrict__ gxt,
