@@ -702,6 +702,8 @@ def cpu_baseline(args, wl, origin, ll, lat0, out_dev):
     return {"value": len(cells) * wl.n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(cells)} cells (GPU argmax 8x8 neighbourhood, corners, random) x "
                       f"all {wl.n} points, FP64, {dt:.1f} s",
+            # the sample's time scaled to every cell of the grid (not measured)
+            "extrapolated_full_grid_s": dt * wl.nx * wl.ny / len(cells),
             "gpu_err_rel_linf_on_sample": err}, (cells, ref)
 
 
@@ -739,7 +741,8 @@ def run_reference(args):
         "config": {"workload": f"{wl.n} AIS-like pts, {wl.nx}x{wl.ny} grid, cell {wl.cell} m, "
                                f"h={wl.h} m, gaussian", "path": "oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} random cells x all {wl.n} points per step"},
+                         "sample": f"{per_step} random cells x all {wl.n} points per step",
+                         "extrapolated_full_grid_s": step_s * wl.nx * wl.ny / per_step},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
