@@ -214,30 +214,41 @@ def lscv_value_and_grad(xy, w, origin, cell, nx, ny, h, threads=0):
     L = lscv_loss(F, xy, wv, origin, cell, nx, ny, h)
     G = lscv_cotangent(F, xy, wv, origin, cell, nx, ny)
     gw, gxy, gh = kde_vjp_gauss(xy, wv, origin, cell, nx, ny, h, G, None, threads)
-    # direct terms of -(2/N) sum_p w_p [bilerp(F, x_p) - w_p K0/(N h^2)]
-    k0 = 1.0 / (2.0 * np.pi)
+    # direct terms of -(2/N) sum_p w_p bilerp(F - F_p, x_p): through the
+    # bilinear weights (x_p), the weight w_p (twice: the factor and F_p) and
+    # F_p's own dependence on x_p and h; F_p(g) = w_p S(g), S = exp(-r^2/2h^2)/(2 pi N h^2)
     ox, oy = float(origin[0]), float(origin[1])
     for p in range(n):
         fx = (xy[p, 0] - ox) / cell - 0.5
         fy = (xy[p, 1] - oy) / cell - 0.5
         i0, j0 = int(np.floor(fx)), int(np.floor(fy))
         ax, ay = fx - i0, fy - j0
-        v = dvx = dvy = 0.0
+        v = s = dvx = dvy = dsx = dsy = sh = 0.0
         for b in (0, 1):
             for a in (0, 1):
                 ii, jj = i0 + a, j0 + b
                 if ii < 0 or jj < 0 or ii >= nx or jj >= ny:
                     continue
+                dx = ox + (ii + 0.5) * cell - xy[p, 0]
+                dy = oy + (jj + 0.5) * cell - xy[p, 1]
+                r2 = dx * dx + dy * dy
+                S = np.exp(-0.5 * r2 / (h * h)) / (2.0 * np.pi * n * h * h)
                 f = F[jj, ii]
                 wx = ax if a else 1.0 - ax
                 wy = ay if b else 1.0 - ay
+                ex = (1.0 if a else -1.0) / cell * wy  # d(wx wy)/dx_p
+                ey = (1.0 if b else -1.0) / cell * wx
                 v += wx * wy * f
-                dvx += (1.0 if a else -1.0) / cell * wy * f
-                dvy += (1.0 if b else -1.0) / cell * wx * f
-        gw[p] += -2.0 / n * (v - 2.0 * wv[p] * k0 / (n * h * h))
-        gxy[p, 0] += -2.0 / n * wv[p] * dvx
-        gxy[p, 1] += -2.0 / n * wv[p] * dvy
-    gh += -2.0 / n * float(np.sum(wv * wv)) * k0 * 2.0 / (n * h ** 3)
+                s += wx * wy * S
+                dvx += ex * f
+                dvy += ey * f
+                dsx += ex * S + wx * wy * S * dx / (h * h)
+                dsy += ey * S + wx * wy * S * dy / (h * h)
+                sh += wx * wy * S * (r2 / h ** 3 - 2.0 / h)
+        gw[p] += -2.0 / n * (v - 2.0 * wv[p] * s)
+        gxy[p, 0] += -2.0 / n * wv[p] * (dvx - wv[p] * dsx)
+        gxy[p, 1] += -2.0 / n * wv[p] * (dvy - wv[p] * dsy)
+        gh += 2.0 / n * wv[p] * wv[p] * sh
     return L, gw, gxy, gh
 
 

@@ -358,11 +358,13 @@ static int bilerp_taps(double x, double y, double ox, double oy, double cell,
 }
 
 /* Least-squares cross-validation on the grid (Gaussian kernel):
- *   L = cell^2 sum_ij F_ij^2
- *       - (2/N) sum_p w_p [ bilerp(F, x_p) - w_p K(0) / (N h^2) ]
- * where F is the density above on the grid, bilerp samples it at x_p and the
- * bracket is the leave-one-out density at x_p (K(0) = 1/(2 pi) removes the
- * point's own term).  F is passed in (computed by oracle_kde_cells). */
+ *   L = cell^2 sum_ij F_ij^2 - (2/N) sum_p w_p bilerp(F - F_p, x_p)
+ * where F is the density above on the grid, F_p = w_p K(|g - x_p|/h)/(N h^2)
+ * is point p's own term at each cell centre g (K(u) = exp(-u^2/2)/(2 pi)), and
+ * bilerp samples a grid at x_p.  bilerp(F - F_p, x_p) is the interpolated
+ * density of the other points, the leave-one-out density at x_p; the first
+ * term approximates the integral of the squared density.  F is passed in
+ * (computed by oracle_kde_grid). */
 double oracle_lscv_loss(const double* F, const double* xy, const double* w,
                         int64_t n, double ox, double oy, double cell, int nx,
                         int ny, double h) {
@@ -373,12 +375,18 @@ double oracle_lscv_loss(const double* F, const double* xy, const double* w,
   for (int64_t p = 0; p < n; ++p) {
     int64_t idx[4];
     double wt[4];
-    const int m = bilerp_taps(xy[2 * p], xy[2 * p + 1], ox, oy, cell, nx, ny,
-                              idx, wt);
-    double v = 0.0;
-    for (int t = 0; t < m; ++t) v += wt[t] * F[idx[t]];
+    const double x = xy[2 * p], y = xy[2 * p + 1];
+    const int m = bilerp_taps(x, y, ox, oy, cell, nx, ny, idx, wt);
     const double wp = w ? w[p] : 1.0;
-    loo += wp * (v - wp * k0 / ((double)n * h * h));
+    double v = 0.0;
+    for (int t = 0; t < m; ++t) {
+      const double gx = ox + ((double)(idx[t] % nx) + 0.5) * cell;
+      const double gy = oy + ((double)(idx[t] / nx) + 0.5) * cell;
+      const double dx = (gx - x) / h, dy = (gy - y) / h;
+      const double own = wp * k0 * exp(-0.5 * (dx * dx + dy * dy)) / ((double)n * h * h);
+      v += wt[t] * (F[idx[t]] - own);
+    }
+    loo += wp * v;
   }
   return cell * cell * sq - 2.0 / (double)n * loo;
 }
