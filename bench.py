@@ -3,16 +3,19 @@
 
 Workload: 20M AIS-like points (40,000 synthetic trajectories: 70% lane traffic,
 20% port clusters, 10% uniform) over a 100 km box, 4096 x 4096 grid of
-24.4140625 m cells, Gaussian kernel, h = 100 m.  One step = Mercator
-projection of the (lon, lat) inputs (FP64) -> centring / hi-lo split ->
-density on the tensor cores (split-FP16 by default) -> split-K reduce.
+24.4140625 m cells, Gaussian kernel, h = 100 m.  One step = one kde_grid_ex
+call on the (lon, lat) inputs: Mercator projection (FP64) fused with the
+centring / hi-lo split -> density on the tensor cores (split-FP16 by default)
+-> split-K reduce.
 
 Metric: point.cell evaluations per second (N * nx * ny per step), in
 Gpoint.cell/s, for the whole job.  Inputs are resident in HBM when the timed
 region starts (they exceed the 129 MB L2: 320 MB of lon/lat), and `e2e`
-repeats the step through the public API with pinned host buffers, the
-host->device copy of the inputs and the device->host copy of the grid inside
-the timed region.  `--impl reference` times the FP64 CPU oracle instead.
+repeats the step through the same call with pinned host buffers: the library
+copies the inputs in and the grid out on the call's stream inside the timed
+region (asynchronous host mode, two streams and two workspaces so one step's
+copies overlap the other's kernels).  `--impl reference` times the FP64 CPU
+oracle instead.
 """
 from __future__ import annotations
 
@@ -138,8 +141,10 @@ def parse():
                     help="also measure the batched, cutoff and LSCV workloads (slower)")
     ap.add_argument("--grid", type=int, default=4096, help="grid side (default: the 4096^2 workload)")
     ap.add_argument("--points", type=int, default=40_000, help="trajectories of 500 fixes")
-    ap.add_argument("--simt-grid", type=int, default=512,
-                    help="grid side for the FP32 SIMT comparison (same points)")
+    ap.add_argument("--simt-grid", type=int, default=4096,
+                    help="grid side for the FP32 SIMT comparison (same points; 0 = skip)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batch leg")
+    ap.add_argument("--no-lscv", action="store_true", help="skip the LSCV bandwidth-fit leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sparse", action="store_true", help="skip the block-sparse leg")
@@ -270,17 +275,19 @@ def run_ours(args):
     n, nx, ny = wl.n, wl.nx, wl.ny
     lonlat_dev = torch.as_tensor(ll, dtype=torch.float64, device=dev)
     w_dev = torch.as_tensor(wl.w, dtype=torch.float32, device=dev)
-    xy_dev = torch.empty_like(lonlat_dev)
     out_dev = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     corner_dev = torch.tensor([corner], dtype=torch.float64, device=dev)
     origin = kde.project_mercator(corner_dev, lat0).cpu().numpy()[0]
+    # projected fixes for the host-side work counts and the oracle (not timed)
+    xy_dev = kde.project_mercator(lonlat_dev, lat0)
     stream = torch.cuda.current_stream(dev)
     tiling = dict(split_k=args.split_k, k_chunk=args.k_chunk, tile_n=args.tile_n)
 
     def step(events=None, path=args.path, out=out_dev, gx=nx, gy=ny, flags=args.flags):
-        kde.project_mercator(lonlat_dev, lat0, out=xy_dev, stream=stream)
-        kde.grid(xy_dev, w_dev, origin, wl.cell, gx, gy, wl.h, args.kernel, out=out, path=path,
-                 flags=flags, stream=stream, timing_events=events, **tiling)
+        # one call: Eq. 1-4 fused into the centring, then the density
+        kde.grid(lonlat_dev, w_dev, origin, wl.cell, gx, gy, wl.h, args.kernel, out=out,
+                 path=path, flags=flags | kde.FLAG_LONLAT, lat0_deg=lat0, stream=stream,
+                 timing_events=events, **tiling)
 
     def new_pair():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -324,7 +331,7 @@ def run_ours(args):
         # (the cutoff path is charged the same per evaluated pair)
         clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_pairs = sms * clk_hz * min(128 / 1.14, 16 / (6144 / (32 * 8192)))
+        peak_pairs = alu_peak_pairs(peaks, sms)
         pairs = evals
         if args.path == "cutoff":  # only the pairs of the bins within reach are evaluated
             pairs = cutoff_pairs(xy_dev.cpu().numpy().reshape(-1, 2), origin, wl.cell, nx, ny,
@@ -366,89 +373,63 @@ def run_ours(args):
         "clocks": clk,
     }
 
+    simt_out = None
     if rank == 0 and args.path not in ("simt", "cutoff") and args.simt_grid > 0:
+        # the FP32 SIMT path on the same fixes: one warm-up call on a small grid
+        # (the kernel is the same at every grid size), then one timed step on
+        # the stated grid
         sg = args.simt_grid
-        out_s = torch.empty((sg, sg), dtype=torch.float32, device=dev)
-        step(path="simt", out=out_s, gx=sg, gy=sg)
+        small = torch.empty((512, 512), dtype=torch.float32, device=dev)
+        step(path="simt", out=small, gx=512, gy=512)
+        simt_out = torch.empty((sg, sg), dtype=torch.float32, device=dev)
         torch.cuda.synchronize()
         a, b = new_pair()
+        simt_clocks = ClockSampler(local)
+        simt_clocks.start()
+        time.sleep(0.3)
         a.record(stream)
-        step(path="simt", out=out_s, gx=sg, gy=sg)
+        step(path="simt", out=simt_out, gx=sg, gy=sg)
         b.record(stream)
         torch.cuda.synchronize()
-        simt = float(n) * sg * sg / (a.elapsed_time(b) * 1e-3) / 1e9
-        result["simt_fp32"] = {"value": simt, "unit": UNIT, "grid": [sg, sg],
-                               "note": "FP32 SIMT path, same points, smaller grid (the path is "
-                                       "compute-bound, its rate does not depend on grid size)"}
+        simt_ms = a.elapsed_time(b)
+        simt = float(n) * sg * sg / (simt_ms * 1e-3) / 1e9
+        result["simt_fp32"] = {"value": simt, "unit": UNIT, "grid": [sg, sg], "ms_per_step": simt_ms,
+                               "steps": 1, "clocks": simt_clocks.stop(),
+                               "note": "FP32 SIMT path, same fixes, one timed step (after a "
+                                       "warm-up call on a 512^2 grid)"}
         result["tensor_vs_simt"] = value / world / simt
+        if sg != nx:
+            simt_out = None
 
     if not args.no_e2e:
-        # End to end: every step copies its inputs from pinned host memory and
-        # reads its result back.  The copies run on a second stream into
-        # double-buffered device arrays, so step k+1's inputs arrive while step
-        # k computes and step k's result leaves while step k+1 computes; each
-        # step's copies are still inside the timed region.
-        lonlat_host = torch.empty_like(lonlat_dev, device="cpu").pin_memory()
+        # End to end through the same call with host buffers: pinned (lon, lat)
+        # and weights in, the pinned grid out; the library copies them on the
+        # call's stream.  FLAG_HOST_ASYNC lets a call return once queued, so
+        # steps alternate between two streams (each with its own workspace and
+        # output buffer) and one step's copies overlap the other's kernels.
+        lonlat_host = torch.empty(tuple(lonlat_dev.shape), dtype=torch.float64, pin_memory=True)
         lonlat_host.copy_(torch.as_tensor(ll))
-        w_host = torch.as_tensor(wl.w).pin_memory()
-        out_host = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
-        bufs = [(lonlat_dev, w_dev, out_dev),
-                (torch.empty_like(lonlat_dev), torch.empty_like(w_dev), torch.empty_like(out_dev))]
-        cs = torch.cuda.Stream(dev)
+        w_host = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        w_host.copy_(torch.as_tensor(wl.w))
+        outs_host = [torch.empty((ny, nx), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        flags_e2e = args.flags | kde.FLAG_LONLAT | kde.FLAG_HOST_ASYNC
+        wsb = kde.workspace_size(lonlat_host, w_host, origin, wl.cell, nx, ny, wl.h, args.kernel,
+                                 outs_host[0], path=args.path, flags=flags_e2e,
+                                 lat0_deg=lat0, **tiling)
+        ws = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(2)]
+        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
 
-        def compute(b, events=None):
-            lon_b, w_b, out_b = bufs[b]
-            kde.project_mercator(lon_b, lat0, out=xy_dev, stream=stream)
-            kde.grid(xy_dev, w_b, origin, wl.cell, nx, ny, wl.h, args.kernel, out=out_b,
-                     path=args.path, flags=args.flags, stream=stream, timing_events=events,
-                     **tiling)
+        def e2e_step(k, events=None):
+            b = k % 2
+            kde.grid(lonlat_host, w_host, origin, wl.cell, nx, ny, wl.h, args.kernel,
+                     out=outs_host[b], path=args.path, flags=flags_e2e, lat0_deg=lat0,
+                     stream=streams[b], workspace=ws[b], timing_events=events, **tiling)
 
-        def pipeline(nsteps, pairs=None, h2d_ev=None, d2h_ev=None):
-            ev = lambda: torch.cuda.Event()
-            in_ready, in_free = [ev(), ev()], [ev(), ev()]
-            out_ready, out_free = [ev(), ev()], [ev(), ev()]
-
-            def h2d(k):
-                b = k % 2
-                with torch.cuda.stream(cs):
-                    if k >= 2:
-                        cs.wait_event(in_free[b])
-                    if h2d_ev:
-                        h2d_ev[k][0].record(cs)
-                    bufs[b][0].copy_(lonlat_host, non_blocking=True)
-                    bufs[b][1].copy_(w_host, non_blocking=True)
-                    if h2d_ev:
-                        h2d_ev[k][1].record(cs)
-                    in_ready[b].record(cs)
-
-            cs.wait_stream(stream)
-            h2d(0)
-            for k in range(nsteps):
-                b = k % 2
-                if k + 1 < nsteps:
-                    h2d(k + 1)
-                stream.wait_event(in_ready[b])
-                if k >= 2:
-                    stream.wait_event(out_free[b])
-                compute(b, kde.event_pair(*pairs[k]) if pairs else None)
-                in_free[b].record(stream)
-                out_ready[b].record(stream)
-                with torch.cuda.stream(cs):
-                    cs.wait_event(out_ready[b])
-                    if d2h_ev:
-                        d2h_ev[k][0].record(cs)
-                    out_host.copy_(bufs[b][2], non_blocking=True)
-                    if d2h_ev:
-                        d2h_ev[k][1].record(cs)
-                    out_free[b].record(cs)
-            stream.wait_stream(cs)
-
-        pipeline(2)
+        torch.cuda.synchronize()
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
         e2e_pairs = [new_pair() for _ in range(args.steps)]
-        h2d_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                  for _ in range(args.steps)]
-        d2h_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                  for _ in range(args.steps)]
         torch.cuda.synchronize()
         barrier(world)
         e2e_clocks = ClockSampler(local)
@@ -456,31 +437,38 @@ def run_ours(args):
         time.sleep(0.3)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pipeline(args.steps, e2e_pairs, h2d_ev, d2h_ev)
-        e1.record(stream)
+        e0.record(streams[0])
+        streams[1].wait_event(e0)
+        for k in range(args.steps):
+            e2e_step(k, kde.event_pair(*e2e_pairs[k]))
+        streams[0].wait_stream(streams[1])
+        e1.record(streams[0])
         torch.cuda.synchronize()
         barrier(world)
         ems = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
         h2d_bytes = int(lonlat_host.numel() * 8 + w_host.numel() * 4)
-        h2d_ms = statistics.mean(a.elapsed_time(b) for a, b in h2d_ev)
         result["e2e"] = {"value": replica_value(world, evals, ems), "unit": UNIT,
                          "ms_per_step": ems,
                          "h2d_bytes_per_step": h2d_bytes,
-                         "d2h_bytes_per_step": int(out_host.numel() * 4),
-                         "copies": "second stream, double-buffered: step k+1's inputs and step "
-                                   "k's result move while step k computes",
-                         # the dominant kernel's own time inside this loop and the
-                         # clocks seen meanwhile
+                         "d2h_bytes_per_step": int(outs_host[0].numel() * 4),
+                         "copies": "inside kde_grid_ex: host (lon, lat) and weights in, grid out, "
+                                   "on the call's stream (KDE_FLAG_HOST_ASYNC; two streams, two "
+                                   "workspaces)",
+                         # the dominant kernel's own time inside this loop
                          "kernel_ms": statistics.mean(a.elapsed_time(b) for a, b in e2e_pairs),
-                         # the copies' own time on their stream
-                         "h2d_ms": h2d_ms, "h2d_gbs": h2d_bytes / h2d_ms / 1e6,
-                         "d2h_ms": statistics.mean(a.elapsed_time(b) for a, b in d2h_ev),
                          "clocks": e2e_clocks.stop()}
+        del ws
 
     sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"], sample = cpu_baseline(args, wl, origin, ll, lat0, out_dev)
+        if simt_out is not None and "simt_fp32" in result:
+            import numpy as np
+            cells, ref = sample
+            Fs = simt_out.cpu().numpy().reshape(-1)[cells]
+            result["simt_fp32"]["rel_linf_vs_oracle_on_sample"] = float(
+                np.max(np.abs(Fs - ref)) / np.max(np.abs(ref)))
+    del simt_out
 
     if rank == 0 and args.path in ("tc_split16", "tc_fp16") and not args.flags \
             and not args.no_sparse:
@@ -500,9 +488,16 @@ def run_ours(args):
 
     if rank == 0 and args.extra:
         result["binned_estimator"] = binned_leg(dev, wl, xy_dev, origin, out_dev)
+    if rank == 0 and not (args.no_batched and args.no_lscv and not args.extra):
         del lonlat_dev, xy_dev, out_dev
         torch.cuda.empty_cache()
-        result["extra"] = extra_workloads(dev)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        if not args.no_batched:
+            result["batched"] = batched_leg(dev, peaks, sms, local)
+        if not args.no_lscv:
+            result["lscv_fit"] = lscv_leg(dev, local)
+        if args.extra:
+            result["extra"] = extra_workloads(dev)
 
     if rank == 0:
         print(json.dumps(result))
@@ -523,16 +518,14 @@ def _time(fn, reps=3):
 
 def extra_workloads(dev):
     """The other rows of the hot path on their own workloads: the binned
-    cutoff path (1M lane points, 1024^2, Epanechnikov), the batched persistent
-    launch (256 instances, 1e4..2e6 points each), the GPU Douglas-Peucker on
-    the 2M raw lane fixes (eps = 10 m) and the LSCV bandwidth fit (1024^2,
-    200 Adam steps) on its output."""
+    cutoff path (1M lane points, 1024^2, Epanechnikov), the GPU
+    Douglas-Peucker on the 2M raw lane fixes (eps = 10 m), and one forward,
+    adjoint and LSCV evaluation on its output (1024^2, h = 150 m)."""
     import numpy as np
     import torch
 
     import paper_2004_13653_gb300 as kde
     import workloads
-    from paper_2004_13653_gb300 import autograd as kag
     out = {}
     wl = workloads.config2(kernel=2)
     pts = torch.as_tensor(wl.xy, dtype=torch.float64, device=dev)
@@ -548,29 +541,6 @@ def extra_workloads(dev):
     out["cutoff_radial_epanechnikov_1M_1024sq"] = {
         "ms": ms, "Gpoint_cell_per_s": wl.n * wl.nx * wl.ny / ms / 1e6,
         "note": "the radial variant K(|u|) on the unit disk, same points and grid"}
-    inst = workloads.config4_instances()
-    insts = [dict(points=torch.as_tensor(x.xy, dtype=torch.float64, device=dev),
-                  weights=torch.as_tensor(x.w, device=dev), origin=x.origin, cell=x.cell,
-                  nx=x.nx, ny=x.ny, h=x.h, kernel=x.kernel) for x in inst]
-    outs = [torch.empty((x.ny, x.nx), device=dev) for x in inst]
-    for d, o in zip(insts, outs):
-        d["out"] = o
-    ms = _time(lambda: kde.grid_batched(insts), reps=2)
-    g = torch.cuda.CUDAGraph()
-    st = torch.cuda.Stream()
-    st.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(st):
-        with torch.cuda.graph(g, stream=st):
-            kde.grid_batched(insts, stream=st)
-    torch.cuda.synchronize()
-    gms = _time(g.replay, reps=2)
-    pairs = float(sum(x.n * x.nx * x.ny for x in inst))
-    out["batched_256_instances"] = {
-        "points": int(sum(x.n for x in inst)), "ms": ms, "graph_replay_ms": gms,
-        "Gpoint_cell_per_s": pairs / gms / 1e6,
-        "kernels": {"gaussian": sum(x.kernel == 6 for x in inst),
-                    "epanechnikov": sum(x.kernel == 2 for x in inst)}}
-    del insts, outs, g
     raw = workloads.config5_raw()
     xy = torch.as_tensor(raw.xy, dtype=torch.float64, device=dev)
     off = torch.as_tensor(raw.offsets, device=dev)
@@ -597,17 +567,141 @@ def extra_workloads(dev):
         "forward_block_sparse_ms": fwd_sparse_ms, "adjoint_ms": bwd_ms, "lscv_ms": lscv_ms,
         "note": "adjoint: a warp per 32 points, each over its +-8h window in turn "
                 "(dL/dw, dL/dpoints, dL/dh)"}
+    return out
+
+
+def alu_peak_pairs(peaks, sms):
+    """ALU roofline of the SIMT and cutoff paths in pair evaluations per second:
+    1.14 FP32 instructions per pair (one FMA plus the factor tabulation) at
+    128 FP32 lanes per SM per clock."""
+    clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return sms * clk_hz * min(128 / 1.14, 16 / (6144 / (32 * 8192)))
+
+
+def batched_leg(dev, peaks, sms, local):
+    """The 256-instance batch (point counts log-uniform 1e4..2e6, grid sides
+    2^7..2^11, h in 50..800 m, Gaussian and Epanechnikov half and half) in one
+    kde_grid_batched call, captured in a CUDA graph and replayed; parity on
+    sampled cells of a few instances of each kernel; roofline = the time the
+    instances would take at their own rooflines (tensor peak for the Gaussian
+    contractions, ALU peak for the cutoff pairs) over the measured time."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2004_13653_gb300 as kde
+    import workloads
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from kde_testutil import sample_cells
+    inst = workloads.config4_instances()
+    insts = [dict(points=torch.as_tensor(x.xy, dtype=torch.float64, device=dev),
+                  weights=torch.as_tensor(x.w, device=dev), origin=x.origin, cell=x.cell,
+                  nx=x.nx, ny=x.ny, h=x.h, kernel=x.kernel) for x in inst]
+    outs = [torch.empty((x.ny, x.nx), device=dev) for x in inst]
+    for d, o in zip(insts, outs):
+        d["out"] = o
+    ms = _time(lambda: kde.grid_batched(insts), reps=2)
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            kde.grid_batched(insts, stream=st)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    gms = _time(g.replay, reps=3)
+    clk = clocks.stop()
+    # parity: the largest instances of each kernel, 64 sampled cells each
+    errs = {}
+    for kid, name in ((6, "gaussian"), (2, "epanechnikov")):
+        idx = sorted((k for k, x in enumerate(inst) if x.kernel == kid),
+                     key=lambda k: -inst[k].n)[:3]
+        worst = 0.0
+        for k in idx:
+            x = inst[k]
+            F = outs[k].cpu().numpy()
+            cells = sample_cells(F, 64, seed=k)
+            ref = oracle.kde_cells(x.xy, x.w, x.origin, x.cell, x.nx, x.ny, x.h, x.kernel, cells,
+                                   threads=os.cpu_count() or 1)
+            worst = max(worst, float(np.max(np.abs(F.reshape(-1)[cells] - ref)) /
+                                     np.max(np.abs(ref))))
+        errs[name] = {"instances": idx, "rel_linf_vs_oracle_on_sample": worst}
+    t_roof = 0.0
+    peak_t = peaks["bf16_tflops_sustained"] * 1e12
+    peak_a = alu_peak_pairs(peaks, sms)
+    for x in inst:
+        if x.kernel == 6:
+            t_roof += 6.0 * x.n * x.nx * x.ny / peak_t
+        else:
+            t_roof += cutoff_pairs(x.xy, x.origin, x.cell, x.nx, x.ny, x.h) / peak_a
+    pairs = float(sum(x.n * x.nx * x.ny for x in inst))
+    del insts, outs, g
+    torch.cuda.empty_cache()
+    return {"instances": len(inst), "points": int(sum(x.n for x in inst)), "ms": ms,
+            "graph_replay_ms": gms, "value": pairs / gms / 1e6, "unit": UNIT,
+            "kernels": {"gaussian": sum(x.kernel == 6 for x in inst),
+                        "epanechnikov": sum(x.kernel == 2 for x in inst)},
+            "roofline": {"bound": "tensor+alu", "roofline_ms": t_roof * 1e3,
+                         "frac": t_roof * 1e3 / gms,
+                         "note": "sum over instances of work / peak (tensor: measured sustained "
+                                 "bf16 for the split-FP16 contractions; ALU: FP32 issue for the "
+                                 "evaluated cutoff pairs) over the measured replay time"},
+            "parity": errs, "clocks": clk}
+
+
+def lscv_leg(dev, local):
+    """Config 5: the 2M raw lane fixes thinned by the GPU Douglas-Peucker at
+    eps = 10 m, then 200 Adam steps of the grid LSCV loss over (log h, weight
+    logits) on 1024^2 (forward, adjoint and loss kernels every step)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2004_13653_gb300 as kde
+    import workloads
+    from paper_2004_13653_gb300 import autograd as kag
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from kde_testutil import sample_cells
+    raw = workloads.config5_raw()
+    xy = torch.as_tensor(raw.xy, dtype=torch.float64, device=dev)
+    off = torch.as_tensor(raw.offsets, device=dev)
+    keep, thin, _, its = kde.dp_simplify(xy, off, 10.0)
+    idx = np.flatnonzero(keep.cpu().numpy())
+    rep = np.diff(np.append(idx, raw.n)).astype(np.float32)
+    w0 = torch.as_tensor(rep, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h, _, losses = kag.fit_bandwidth(thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,
+    h, w, losses = kag.fit_bandwidth(thin, w0, raw.origin, raw.cell, raw.nx, raw.ny, 150.0,
                                      steps=200, lr=0.05)
     torch.cuda.synchronize()
-    out["lscv_fit_200_steps"] = {"points": int(thin.shape[0]), "raw_points": int(raw.n),
-                                 "seconds": time.perf_counter() - t0, "h_final_m": h,
-                                 "loss_first": losses[0], "loss_last": losses[-1],
-                                 "input": "the GPU Douglas-Peucker output at eps = 10 m, weights "
-                                          "= raw fixes each kept fix stands for"}
-    return out
+    secs = time.perf_counter() - t0
+    clk = clocks.stop()
+    # parity at the fitted bandwidth: the density on sampled cells, and the
+    # loss of the GPU grid recomputed by the oracle's loss function
+    F = kde.grid(thin, w, raw.origin, raw.cell, raw.nx, raw.ny, h, "gaussian",
+                 flags=kde.FLAG_SYNC)
+    Fh = F.cpu().numpy()
+    xyh = thin.cpu().numpy()
+    wh = w.cpu().numpy().astype(np.float64)
+    cells = sample_cells(Fh, 64, seed=9)
+    ref = oracle.kde_cells(xyh, wh, raw.origin, raw.cell, raw.nx, raw.ny, h, oracle.GAUSSIAN, cells,
+                           threads=os.cpu_count() or 1)
+    loss_gpu = kde.lscv_grid(F, thin, w, raw.origin, raw.cell, raw.nx, raw.ny, h)[0]
+    loss_or = oracle.lscv_loss(Fh, xyh, wh, raw.origin, raw.cell, raw.nx, raw.ny, h)
+    return {"raw_points": int(raw.n), "points": int(thin.shape[0]), "dp_iterations": its,
+            "steps": 200, "seconds": secs, "ms_per_step": secs * 1e3 / 200, "h0_m": 150.0,
+            "h_final_m": h, "loss_first": losses[0], "loss_last": losses[-1],
+            "parity": {"density_rel_linf_vs_oracle_on_sample":
+                       float(np.max(np.abs(Fh.reshape(-1)[cells] - ref)) / np.max(np.abs(ref))),
+                       "loss_rel_vs_oracle_same_grid": abs(loss_gpu - loss_or) / abs(loss_or)},
+            "clocks": clk,
+            "input": "GPU Douglas-Peucker output at eps = 10 m, initial weights = raw fixes each "
+                     "kept fix stands for"}
 
 
 def sparse_leg(step, stream, out_dense, new_pair, dense_kernel_ms, evals, sample):

@@ -97,6 +97,20 @@ typedef enum {
                                  /* (tcgen05 cta_group::2); the default for     */
                                  /* split-FP16 with 256-wide tiles              */
 #define KDE_FLAG_ONE_CTA 8u      /* TC paths: 128xN tiles on single CTAs        */
+#define KDE_FLAG_LONLAT 16u      /* points are (lon, lat) in degrees: the call  */
+                                 /* projects them with Eq. 1-4 (as            */
+                                 /* kde_project_mercator at opts->lat0_deg)    */
+                                 /* while centring them; origin, cell and h    */
+                                 /* stay in projected metres                   */
+#define KDE_FLAG_HOST_ASYNC 32u  /* with host buffers: return once the copies  */
+                                 /* and kernels are queued on opts->stream     */
+                                 /* instead of waiting for the result. The     */
+                                 /* host buffers must stay valid and unchanged */
+                                 /* until the stream has passed the call (and  */
+                                 /* be pinned for the copies to overlap other  */
+                                 /* work); out is valid after the caller       */
+                                 /* synchronises the stream; device-side data  */
+                                 /* errors are then not reported               */
 
 typedef struct kde_args {
   const double* points; /* [2n] interleaved x,y metres (device or host)      */
@@ -125,6 +139,8 @@ typedef struct kde_opts {
                           /* right before / after the dominant kernel       */
   int32_t stage_points;   /* TC paths: 32 or 64 points per pipeline stage,  */
                           /* 0 = automatic                                  */
+  double lat0_deg;        /* KDE_FLAG_LONLAT: standard latitude phi0 of     */
+                          /* Eq. 1-4, in (-90, 90) degrees                  */
 } kde_opts;
 
 /* Fill *o with the defaults (AUTO path, legacy stream, library workspace). */
@@ -185,6 +201,32 @@ int kde_project_mercator(const double* lonlat_deg, int64_t n, double lat0_deg,
  */
 int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts);
 
+/* Per-instance tiling of a tensor-core density in kde_grid_batched_tiled
+ * (every field 0 = the call's own choice, as in kde_opts). */
+typedef struct kde_tiling {
+  int32_t tile_n;       /* 128 or 256 grid rows (y) per tile                 */
+  int32_t k_chunk;      /* points per accumulator drain (multiple of 32, at  */
+                        /* least twice the stage)                            */
+  int32_t split_k;      /* point-range splits, 0..1024                       */
+  int32_t stage_points; /* 32 or 64 points per pipeline stage                */
+  uint32_t flags;       /* KDE_FLAG_CTA_PAIR (256 x 256 tiles on CTA pairs), */
+                        /* KDE_FLAG_ONE_CTA (128 x tile_n tiles), or 0       */
+} kde_tiling;
+
+/*
+ * kde_grid_batched_tiled — kde_grid_batched with a tiling per instance
+ * (tiles[k] for inst[k]; NULL = kde_grid_batched), for instance the one an
+ * autotuner measured best for that instance's class.  Tensor-core instances
+ * that end up with the same tile shape and stage form one family; each family
+ * is one persistent launch over its instances' work items (all in stream
+ * order, still one call and capturable the same way).  The tiling is ignored
+ * for non-tensor-core instances.  Errors as kde_grid_batched, plus KDE_EINVAL
+ * for an invalid tiling and KDE_ENOTSUP for a one-CTA tiling with
+ * KDE_FLAG_SKIP_ZERO.
+ */
+int kde_grid_batched_tiled(const kde_args* inst, const kde_tiling* tiles, int count,
+                           const kde_opts* opts);
+
 /*
  * kde_grid_backward — adjoint of the Gaussian density (Sec. III-C, Eq. 7
  * with the Gaussian row of Table 1).  Given G = dL/dF (device, [ny*nx]
@@ -205,9 +247,11 @@ int kde_grid_backward(const kde_args* a, const float* grad_out,
  * kde_lscv_grid — least-squares cross-validation loss of the Gaussian
  * density on the grid (the paper chooses the bandwidth by eye, Sec. V-D;
  * this is its quantitative counterpart):
- *   L = cell^2 sum F^2 - (2/N) sum_p w_p [bilerp(F, x_p) - w_p K(0)/(N h^2)],
- * K(0) = 1/(2 pi), bilerp = bilinear interpolation of F between cell
- * centres with zero outside the grid.  F: device [ny*nx] (as computed by
+ *   L = cell^2 sum F^2 - (2/N) sum_p w_p bilerp(F - F_p, x_p),
+ * F_p = w_p K(|g - x_p|/h)/(N h^2) point p's own term at the cell centres g
+ * (K(u) = exp(-u^2/2)/(2 pi)), bilerp = bilinear interpolation between cell
+ * centres with zero outside the grid; bilerp(F - F_p, x_p) is the
+ * leave-one-out density at x_p interpolated from the grid.  F: device [ny*nx] (as computed by
  * kde_grid_ex for the same arguments).  Writes the loss to *loss (host),
  * dL/dF to grad_F (device [ny*nx], FP32), and the loss's direct partial
  * derivatives w.r.t. w_p and x_p (not through F) to grad_w_direct (device
@@ -277,13 +321,17 @@ int kde_dp_simplify(const double* points, const int64_t* traj_offsets, int64_t n
  * memory budget).  Its scratch is one static device array of 8 MiB per GPU,
  * reserved while the library is loaded; inputs needing more scratch (about
  * 400,000 points on a small grid; 20 bytes per point plus 8 per grid row and
- * column) are rejected with KDE_EINVAL.  points, weights (or NULL) and out
- * are device memory, laid out as for kde_grid.  Asynchronous on `stream`
- * (a cudaStream_t, NULL = legacy default stream); non-finite inputs are not
+ * column) are rejected with KDE_EINVAL before anything is launched.
+ * kernel_id: a Table 1 kernel (0..7) or the radial Gaussian (14, the same
+ * density as KDE_GAUSSIAN).  points, weights (or NULL) and out are device
+ * memory, laid out as for kde_grid.  Asynchronous on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); non-finite inputs are not
  * reported.  Every call on a device shares the scratch and it keeps the last
  * call's contents: calls that overlap on the GPU race.  The first call on a
- * device looks up the scratch's device address; make it before any stream
- * capture.  Errors: KDE_EINVAL, KDE_ECUDA.
+ * device looks up the scratch's device address and keeps it for the life of
+ * the process; make that call before any stream capture.  A device reset
+ * (cudaDeviceReset) or a non-primary driver context invalidates the kept
+ * address and is not supported.  Errors: KDE_EINVAL, KDE_ECUDA.
  */
 int kde_grid_noalloc(const double* points, const float* weights, int64_t n,
                      const double grid_origin[2], double cell, int nx, int ny, double h,

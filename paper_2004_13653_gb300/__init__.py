@@ -24,6 +24,7 @@ RADIAL = 8  # radial variant of Table 1 kernel k: RADIAL + k ("radial_<name>")
 KERNELS.update({"radial_" + k: RADIAL + v for k, v in list(KERNELS.items())})
 PATHS = {"auto": 0, "simt": 1, "tc_fp16": 2, "tc_split16": 3, "cutoff": 4}
 FLAG_SYNC, FLAG_SKIP_ZERO, FLAG_CTA_PAIR, FLAG_ONE_CTA = 1, 2, 4, 8
+FLAG_LONLAT, FLAG_HOST_ASYNC = 16, 32
 
 KDE_OK, KDE_EINVAL, KDE_ENOMEM, KDE_ECUDA, KDE_ETIMEOUT, KDE_ENOTSUP, KDE_EDATA = 0, -1, -2, -3, -4, -5, -6
 _ERRNAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EDATA"}
@@ -47,11 +48,19 @@ class KdeOpts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("split_k", ctypes.c_int32), ("k_chunk", ctypes.c_int32),
                 ("tile_n", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("timing_events", ctypes.c_void_p), ("stage_points", ctypes.c_int32)]
+                ("timing_events", ctypes.c_void_p), ("stage_points", ctypes.c_int32),
+                ("lat0_deg", ctypes.c_double)]
+
+
+class KdeTiling(ctypes.Structure):
+    _fields_ = [("tile_n", ctypes.c_int32), ("k_chunk", ctypes.c_int32),
+                ("split_k", ctypes.c_int32), ("stage_points", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
 
 
 EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
-           "kde_project_mercator", "kde_grid_batched", "kde_grid_backward", "kde_lscv_grid",
+           "kde_project_mercator", "kde_grid_batched", "kde_grid_batched_tiled",
+           "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
            "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
            "kde_grid_binned", "kde_dp_simplify")
@@ -88,6 +97,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_project_mercator.restype = i32
     lib.kde_grid_batched.argtypes = [P(KdeArgs), i32, P(KdeOpts)]
     lib.kde_grid_batched.restype = i32
+    lib.kde_grid_batched_tiled.argtypes = [P(KdeArgs), P(KdeTiling), i32, P(KdeOpts)]
+    lib.kde_grid_batched_tiled.restype = i32
     lib.kde_grid_backward.argtypes = [P(KdeArgs), vp, vp, vp, P(ctypes.c_double), P(KdeOpts)]
     lib.kde_grid_backward.restype = i32
     lib.kde_lscv_grid.argtypes = [P(KdeArgs), vp, P(ctypes.c_double), vp, vp, vp,
@@ -168,7 +179,8 @@ def make_args(points, weights, origin, cell, nx, ny, h, kernel, out) -> KdeArgs:
 
 
 def make_opts(path="auto", flags=0, stream=None, workspace=None, split_k=0, k_chunk=0,
-              tile_n=0, max_ctas=0, timing_events=None, stage_points=0) -> KdeOpts:
+              tile_n=0, max_ctas=0, timing_events=None, stage_points=0,
+              lat0_deg=0.0) -> KdeOpts:
     o = KdeOpts()
     load().kde_default_opts(ctypes.byref(o))
     o.path = PATHS[path] if isinstance(path, str) else int(path)
@@ -180,6 +192,7 @@ def make_opts(path="auto", flags=0, stream=None, workspace=None, split_k=0, k_ch
         o.workspace_bytes = _count(workspace) * workspace.element_size()
     o.split_k, o.k_chunk, o.tile_n, o.max_ctas = int(split_k), int(k_chunk), int(tile_n), int(max_ctas)
     o.stage_points = int(stage_points)
+    o.lat0_deg = float(lat0_deg)
     if timing_events is not None:
         # keep the array alive as long as the options object
         o._events = timing_events
@@ -207,10 +220,13 @@ def grid(points, weights, origin, cell, nx, ny, h, kernel="gaussian", out=None, 
          flags=0, stream=None, **tiling):
     """Density on the nx x ny grid (kde_grid_ex).  See include/kde.h.
 
-    points: [n,2] float64 metres (torch cuda/cpu tensor or numpy array);
-    weights: [n] float32 or None; returns out ([ny, nx] float32), allocated
-    like points when not given.  Runs on the torch current stream of the
-    points' device unless `stream` is given; host buffers make it synchronous.
+    points: [n,2] float64 metres (torch cuda/cpu tensor or numpy array), or
+    (lon, lat) degrees with flags=FLAG_LONLAT and lat0_deg= the standard
+    latitude; weights: [n] float32 or None; returns out ([ny, nx] float32),
+    allocated like points when not given.  Runs on the torch current stream of
+    the points' device unless `stream` is given; host buffers make it
+    synchronous unless flags has FLAG_HOST_ASYNC.  Tiling keywords, workspace=,
+    timing_events= and lat0_deg= go to kde_opts.
     """
     import torch
     if out is None:
@@ -244,11 +260,15 @@ def workspace_size(points, weights, origin, cell, nx, ny, h, kernel, out, **opts
     return int(b.value)
 
 
-def grid_batched(instances, path="auto", flags=0, stream=None, **tiling):
+def grid_batched(instances, path="auto", flags=0, stream=None, tilings=None, **tiling):
     """kde_grid_batched: many densities, one persistent launch per path family.
 
     instances: sequence of dicts with keys points, weights, origin, cell, nx,
-    ny, h, kernel and optionally out (device tensors).  Returns the outputs.
+    ny, h, kernel and optionally out (device tensors).  tilings: optional
+    sequence (one per instance) of dicts with keys of kde_tiling (tile_n,
+    k_chunk, split_k, stage_points, flags) or None, e.g. from
+    autotune.tune_batch; then kde_grid_batched_tiled runs the batch.  Returns
+    the outputs.
     """
     import torch
     args = (KdeArgs * max(len(instances), 1))()
@@ -264,7 +284,16 @@ def grid_batched(instances, path="auto", flags=0, stream=None, **tiling):
     if stream is None and outs:
         stream = _current_stream(outs[0].device)
     o = make_opts(path, flags, stream, **tiling)
-    check(load().kde_grid_batched(args, len(instances), ctypes.byref(o)))
+    if tilings is None:
+        check(load().kde_grid_batched(args, len(instances), ctypes.byref(o)))
+        return outs
+    if len(tilings) != len(instances):
+        raise ValueError("one tiling per instance")
+    tl = (KdeTiling * max(len(instances), 1))()
+    for k, d in enumerate(tilings):
+        for key, v in (d or {}).items():
+            setattr(tl[k], key, int(v))
+    check(load().kde_grid_batched_tiled(args, tl, len(instances), ctypes.byref(o)))
     return outs
 
 

@@ -176,24 +176,28 @@ __global__ void k_lscv_grid(const float* __restrict__ F, int64_t cells, double t
   if (threadIdx.x == 0) sq_part[blockIdx.x] = sh[0];
 }
 
-// Per point: bilinear sample of F between cell centres (zero outside), the
-// leave-one-out term, the loss's direct partials, and the scatter of
-// -(2/N) w_p beta into the FP64 cotangent (atomic adds; in FP64 their order
-// does not show in the FP32 result).
+// Per point: the leave-one-out term w_p bilerp(F - F_p, x_p) (the bilinear
+// sample of F between cell centres, zero outside, minus the same sample of
+// the point's own term F_p = w_p S, S = exp(-r^2/2h^2)/(2 pi N h^2)), the
+// loss's direct partials (through the bilinear weights, w_p and F_p), and the
+// scatter of -(2/N) w_p beta into the FP64 cotangent (atomic adds; in FP64
+// their order does not show in the FP32 result).  FP64 throughout.
 __global__ void k_lscv_points(const float4* __restrict__ pts, const float* __restrict__ wts,
                               int64_t n, const float* __restrict__ F, int nx, int ny,
-                              double cells_per_h, float inv_cell, double inv_N, double self_term,
-                              double* __restrict__ G, float* __restrict__ gw_direct,
-                              float* __restrict__ gxy_direct, double* __restrict__ loo) {
+                              double cells_per_h, double cell_h, double inv_cell, double inv_h,
+                              double inv_N, double self_term, double* __restrict__ G,
+                              float* __restrict__ gw_direct, float* __restrict__ gxy_direct,
+                              double* __restrict__ loo, double* __restrict__ hdir) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const float4 P = pts[p];
     const double w = wts[p];
-    const double fx = ((double)P.x + (double)P.y) * cells_per_h - 0.5;
-    const double fy = ((double)P.z + (double)P.w) * cells_per_h - 0.5;
+    const double X = (double)P.x + (double)P.y, Y = (double)P.z + (double)P.w;  // in h
+    const double fx = X * cells_per_h - 0.5;
+    const double fy = Y * cells_per_h - 0.5;
     const double fi = floor(fx), fj = floor(fy);
     const double ax = fx - fi, ay = fy - fj;
-    double v = 0.0, dvx = 0.0, dvy = 0.0;
+    double v = 0.0, sv = 0.0, dvx = 0.0, dvy = 0.0, dsx = 0.0, dsy = 0.0, sh = 0.0;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -201,19 +205,29 @@ __global__ void k_lscv_points(const float4* __restrict__ pts, const float* __res
         const double ii = fi + a, jj = fj + b;
         if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
         const int64_t q = (int64_t)jj * nx + (int64_t)ii;
-        const double wx = a ? ax : 1.0 - ax, wy = b ? ay : 1.0 - ay;
+        const double wx = a ? ax : 1.0 - ax, wy = b ? ay : 1.0 - ay, ww = wx * wy;
+        const double ex = (a ? 1.0 : -1.0) * wy * inv_cell;  // d(wx wy)/dx_p
+        const double ey = (b ? 1.0 : -1.0) * wx * inv_cell;
+        const double dx = (ii + 0.5) * cell_h - X, dy = (jj + 0.5) * cell_h - Y;  // in h
+        const double r2 = dx * dx + dy * dy;
+        const double S = self_term * exp(-0.5 * r2);
         const double f = F[q];
-        v += wx * wy * f;
-        dvx += (a ? 1.0 : -1.0) * wy * f;
-        dvy += (b ? 1.0 : -1.0) * wx * f;
-        if (G) atomicAdd(&G[q], -2.0 * inv_N * w * wx * wy);
+        v += ww * f;
+        sv += ww * S;
+        dvx += ex * f;
+        dvy += ey * f;
+        dsx += ex * S + ww * S * dx * inv_h;
+        dsy += ey * S + ww * S * dy * inv_h;
+        sh += ww * S * (r2 - 2.0) * inv_h;
+        if (G) atomicAdd(&G[q], -2.0 * inv_N * w * ww);
       }
-    if (gw_direct) gw_direct[p] = (float)(-2.0 * inv_N * (v - 2.0 * w * self_term));
+    if (gw_direct) gw_direct[p] = (float)(-2.0 * inv_N * (v - 2.0 * w * sv));
     if (gxy_direct) {
-      gxy_direct[2 * p] = (float)(-2.0 * inv_N * w * dvx * inv_cell);
-      gxy_direct[2 * p + 1] = (float)(-2.0 * inv_N * w * dvy * inv_cell);
+      gxy_direct[2 * p] = (float)(-2.0 * inv_N * w * (dvx - w * dsx));
+      gxy_direct[2 * p + 1] = (float)(-2.0 * inv_N * w * (dvy - w * dsy));
     }
-    loo[p] = w * (v - w * self_term);
+    loo[p] = w * (v - w * sv);
+    hdir[p] = w * w * sh;
   }
 }
 
@@ -223,24 +237,12 @@ __global__ void k_to_float(const double* __restrict__ src, int64_t n, float* __r
     dst[q] = (float)src[q];
 }
 
-__global__ void k_square(const float* __restrict__ w, int64_t n, double* __restrict__ w2) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
-    w2[p] = (double)w[p] * w[p];
-}
-
 int grid_blocks(int64_t n, int threads, int cap) {
   const int64_t b = (n + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
 }  // namespace
-
-cudaError_t launch_square_weights(const float* w, int64_t n, double* w2, cudaStream_t s) {
-  k_square<<<grid_blocks(n, 256, 152 * 16), 256, 0, s>>>(w, n, w2);
-  note_launches(1);
-  return cudaGetLastError();
-}
 
 size_t sum_partials(int64_t n) { return (size_t)((n + 65535) / 65536) + 1; }
 
@@ -284,7 +286,7 @@ cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n,
 cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const float* F, int nx,
                         int ny, double cell, double h, double* Gd, float* G, float* gw_direct,
                         float* gxy_direct, double* sq_part, int sq_blocks, double* loo,
-                        cudaStream_t s) {
+                        double* hdir, cudaStream_t s) {
   const int64_t cells = (int64_t)nx * ny;
   k_lscv_grid<<<sq_blocks, 256, 0, s>>>(F, cells, 2.0 * cell * cell, Gd, sq_part);
   note_launches(1);
@@ -293,8 +295,8 @@ cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const fl
   if (n > 0) {
     const double self = 1.0 / (2.0 * 3.14159265358979323846) / ((double)n * h * h);
     k_lscv_points<<<grid_blocks(n, 256, 152 * 16), 256, 0, s>>>(
-        pts, wts, n, F, nx, ny, h / cell, (float)(1.0 / cell), 1.0 / (double)n, self, Gd,
-        gw_direct, gxy_direct, loo);
+        pts, wts, n, F, nx, ny, h / cell, cell / h, 1.0 / cell, 1.0 / h, 1.0 / (double)n, self,
+        Gd, gw_direct, gxy_direct, loo, hdir);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -156,6 +156,8 @@ int validate(const kde_args* a, const kde_opts* o) {
     if (o->max_ctas < 0) return fail(KDE_EINVAL, "max_ctas must be >= 0");
     if (o->workspace && o->workspace_bytes == 0)
       return fail(KDE_EINVAL, "workspace given with zero size");
+    if ((o->flags & KDE_FLAG_LONLAT) && !(fabs(o->lat0_deg) < 90.0))
+      return fail(KDE_EINVAL, "KDE_FLAG_LONLAT needs a standard latitude in (-90, 90)");
   }
   return KDE_OK;
 }
@@ -201,7 +203,8 @@ struct InstPlan {
   int splits;
   int64_t n_pad, prep_begin;
   size_t off_gxt, off_gyt, off_part, off_run;  // off_run: SIMT running sums
-  // tensor-core path
+  // tensor-core path: the instance's tile family and accumulator chunk
+  int fam, k_chunk, split_req;
   int tiles_m, tiles_n, items;
   int64_t per_split;
   // cutoff path, and the bin sort of block-sparse tensor-core instances
@@ -218,11 +221,21 @@ struct InstPlan {
 // the FP32 rounding of the offsets and of ex2.approx.
 constexpr double kSparseReach = 6.45;
 
+// Tensor-core instances that share a tile shape and pipeline stage: one
+// persistent launch over their work items.
+struct TcFamily {
+  TcPlan plan;
+  std::vector<int> order;  // instances, most expensive items first
+  int items = 0;
+  int tab_begin = 0;       // first entry of the family in the TC table
+};
+
 struct BatchPlan {
   int count;
   std::vector<InstPlan> in;
-  TcPlan tc;
-  std::vector<int> tc_order;  // TC instances, most expensive items first
+  TcPlan tc;                  // the call's default plan (and the block-sparse one)
+  std::vector<TcFamily> fam;  // tensor-core families, in launch order
+  std::vector<int> tc_order;  // TC instances: the families' orders concatenated
   int n_tc = 0, n_cut = 0, n_simt = 0, n_reduce = 0, tc_items = 0, max_side = 1;
   int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0, cut_bins = 0;
   bool sparse = false;  // block-sparse tensor-core instances
@@ -237,7 +250,8 @@ struct BatchPlan {
       off_hout, total;
 };
 
-int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory, BatchPlan* P) {
+int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling* tiles,
+              bool probe_memory, BatchPlan* P) {
   P->count = count;
   P->in.assign(count, InstPlan());
   const int sms = sm_count();
@@ -311,23 +325,78 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
     return fail(KDE_EINVAL, "k_chunk %d must be a multiple of, and at least twice, the %d-point stage",
                 t.k_chunk, t.stage_points);
 
+  // tile families: the call's plan, changed per instance by its tiling; the
+  // instances of one family share a persistent launch
+  for (int k = 0; k < count; ++k) {
+    InstPlan& I = P->in[k];
+    I.fam = -1;
+    I.split_req = o ? o->split_k : 0;
+    if (!is_tc(I.path)) continue;
+    TcPlan f = t;
+    int kc = t.k_chunk;
+    if (tiles) {
+      const kde_tiling& ti = tiles[k];
+      if ((ti.tile_n != 0 && ti.tile_n != 128 && ti.tile_n != 256) ||
+          (ti.stage_points != 0 && ti.stage_points != 32 && ti.stage_points != 64) ||
+          ti.k_chunk < 0 || (ti.k_chunk % 32) != 0 || ti.split_k < 0 || ti.split_k > 1024 ||
+          (ti.flags & ~(KDE_FLAG_CTA_PAIR | KDE_FLAG_ONE_CTA)) ||
+          ((ti.flags & KDE_FLAG_CTA_PAIR) && (ti.flags & KDE_FLAG_ONE_CTA)))
+        return fail(KDE_EINVAL, "instance %d: invalid tiling", k);
+      if (P->sparse) {
+        if ((ti.flags & KDE_FLAG_ONE_CTA) || (ti.tile_n && ti.tile_n != 256) ||
+            (ti.stage_points && ti.stage_points != 64))
+          return fail(KDE_ENOTSUP, "instance %d: block-sparse skipping runs on 256 x 256 CTA-pair "
+                      "tiles with 64-point stages", k);
+      } else {
+        if (ti.tile_n) f.tile_n = ti.tile_n;
+        if (ti.stage_points) f.stage_points = ti.stage_points;
+        const bool can_pair = f.tile_n == 256 && f.stage_points == 64 && ctas >= 2;
+        if (ti.flags & KDE_FLAG_CTA_PAIR) {
+          if (!can_pair)
+            return fail(KDE_EINVAL, "instance %d: CTA-pair tiles need tile_n 256, 64-point stages "
+                        "and two CTAs", k);
+          f.pair = 1;
+        } else if (ti.flags & KDE_FLAG_ONE_CTA) {
+          f.pair = 0;
+        } else {
+          f.pair = t.pair && can_pair ? 1 : 0;
+        }
+      }
+      if (ti.k_chunk) kc = ti.k_chunk;
+      if (ti.split_k) I.split_req = ti.split_k;
+      if (kc % f.stage_points || kc < 2 * f.stage_points)
+        return fail(KDE_EINVAL, "instance %d: k_chunk %d must be a multiple of, and at least "
+                    "twice, the %d-point stage", k, kc, f.stage_points);
+    }
+    I.k_chunk = kc;
+    for (int q = 0; q < (int)P->fam.size() && I.fam < 0; ++q) {
+      const TcPlan& g = P->fam[q].plan;
+      if (g.pair == f.pair && g.tile_n == f.tile_n && g.stage_points == f.stage_points) I.fam = q;
+    }
+    if (I.fam < 0) {
+      I.fam = (int)P->fam.size();
+      P->fam.push_back(TcFamily());
+      P->fam.back().plan = f;
+    }
+  }
+
   // per-path work decomposition
-  double tc_cost = 0.0;
+  std::vector<double> fam_cost(P->fam.size(), 0.0);
   for (int k = 0; k < count; ++k) {
     const kde_args* a = &A[k];
     InstPlan& I = P->in[k];
     if (is_tc(I.path)) {
-      const int tile_m = t.pair ? 256 : 128;
+      const TcPlan& f = P->fam[I.fam].plan;
+      const int tile_m = f.pair ? 256 : 128;
       I.tiles_m = (a->nx + tile_m - 1) / tile_m;
-      I.tiles_n = (a->ny + t.tile_n - 1) / t.tile_n;
-      tc_cost += (double)I.tiles_m * I.tiles_n * (double)I.n_pad;
+      I.tiles_n = (a->ny + f.tile_n - 1) / f.tile_n;
+      fam_cost[I.fam] += (double)I.tiles_m * I.tiles_n * (double)I.n_pad;
     }
   }
-  const double target_item = tc_cost / (double)(t.pair ? ctas / 2 : ctas) / 6.0;
   for (int k = 0; k < count; ++k) {
     const kde_args* a = &A[k];
     InstPlan& I = P->in[k];
-    int splits = o ? o->split_k : 0;
+    int splits = I.split_req;
     if (I.path == KDE_PATH_SIMT_FP32) {
       if (splits == 0) {
         const int64_t tiles = (int64_t)((a->nx + 127) / 128) * ((a->ny + 63) / 64);
@@ -341,22 +410,26 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       splits = 1;
       I.per_split = I.n_pad;
       I.items = 0;
-      P->tc_order.push_back(k);
+      P->fam[I.fam].order.push_back(k);
       ++P->n_tc;
     } else if (is_tc(I.path)) {
+      const TcPlan& f = P->fam[I.fam].plan;
+      const int units = f.pair ? ctas / 2 : ctas;
       const int64_t tiles = (int64_t)I.tiles_m * I.tiles_n;
       if (splits == 0) {
         if (count == 1) {
-          splits = choose_tc_splits(tiles, t.pair ? ctas / 2 : ctas, I.n_pad);
+          splits = choose_tc_splits(tiles, units, I.n_pad);
         } else {
+          // items of about a sixth of each CTA's (pair's) share of the family
+          const double target_item = fam_cost[I.fam] / (double)units / 6.0;
           const double want = std::ceil((double)I.n_pad / std::max(target_item, 1.0));
           splits = (int)std::max(1.0, std::min({want, 64.0, (double)(I.n_pad / 256)}));
         }
       }
-      const int64_t ks = t.stage_points;
+      const int64_t ks = f.stage_points;
       I.per_split = ((I.n_pad + splits - 1) / splits + ks - 1) / ks * ks;
       I.items = (int)(tiles * splits);
-      P->tc_order.push_back(k);
+      P->fam[I.fam].order.push_back(k);
       ++P->n_tc;
     } else {  // cutoff
       splits = 1;
@@ -378,10 +451,18 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
       P->reduce_cells += (int64_t)a->nx * a->ny;
     }
   }
-  // most expensive work items first, so round-robin CTAs balance
-  std::stable_sort(P->tc_order.begin(), P->tc_order.end(), [&](int x, int y) {
-    return P->in[x].per_split > P->in[y].per_split;
-  });
+  // most expensive work items first within each family, so round-robin CTAs
+  // balance; the TC table holds the families one after the other
+  for (TcFamily& f : P->fam) {
+    std::stable_sort(f.order.begin(), f.order.end(), [&](int x, int y) {
+      return P->in[x].per_split > P->in[y].per_split;
+    });
+    f.tab_begin = (int)P->tc_order.size();
+    for (int k : f.order) {
+      P->tc_order.push_back(k);
+      f.items += P->in[k].items;
+    }
+  }
   if (P->sparse) {
     // bins of the block-sparse instances follow the cutoff bins in the sort
     double est = 0.0;
@@ -423,6 +504,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, bool probe_memory
   if (P->cut_m >= ((int64_t)1 << 32)) return fail(KDE_EINVAL, "too many points to sort in one batch");
   for (int k : P->tc_order) P->tc_items += P->in[k].items;
   if ((int64_t)P->tc_items > 0x7fffffff) return fail(KDE_EINVAL, "too many work items");
+  if (P->sparse && P->fam.size() > 1) return fail(KDE_EINVAL, "block-sparse batch with two tilings");
   P->cz = cutoff_sizes(P->cut_m, P->total_bins);
 
   size_t off = 0;
@@ -512,16 +594,20 @@ void set_key_constants(CutInst& q) {
 }
 
 // Plan, lay out, upload and launch every instance of a batch on one stream.
-int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) {
+int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling* tiles,
+              bool force_sync) {
   for (int k = 0; k < count; ++k) {
     int rc = validate(&A[k], o);
     if (rc) return rc;
   }
   BatchPlan P;
-  int rc = make_plan(A, count, o, true, &P);
+  int rc = make_plan(A, count, o, tiles, true, &P);
   if (rc) return rc;
   cudaStream_t s = stream_of(o);
-  const bool sync = force_sync || (o && (o->flags & KDE_FLAG_SYNC)) || P.host_out;
+  // host output makes the call wait for its copy back, unless the caller
+  // asked for the asynchronous host mode (and then synchronises the stream)
+  const bool host_async = o && (o->flags & KDE_FLAG_HOST_ASYNC);
+  const bool sync = force_sync || (o && (o->flags & KDE_FLAG_SYNC)) || (P.host_out && !host_async);
   void* wsv = nullptr;
   rc = acquire_workspace(o, P.total, s, &wsv);
   if (rc) return rc;
@@ -548,7 +634,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   }
 
   // ---- tables
-  std::vector<PrepInst> prep(count);
+  std::vector<PrepInst> prep(count, PrepInst{});
+  const bool lonlat = o && (o->flags & KDE_FLAG_LONLAT);
+  const MercParams merc = lonlat ? mercator_params(o->lat0_deg) : MercParams{};
   std::vector<TcInst> tct;
   std::vector<CutInst> cut;
   std::vector<ReduceInst> red;
@@ -574,6 +662,8 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     q.cell_sigma = a->cell * q.sigma;
     q.nx = a->nx;
     q.ny = a->ny;
+    q.lonlat = lonlat ? 1 : 0;
+    q.merc = merc;
   }
   auto part_of = [&](int k) {
     return P.in[k].splits > 1 ? reinterpret_cast<float*>(base + P.in[k].off_part) : out_dev[k];
@@ -588,6 +678,8 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
   for (int k : P.tc_order) {
     const kde_args* a = &A[k];
     const InstPlan& I = P.in[k];
+    const TcFamily& fam = P.fam[I.fam];
+    if (k == fam.order.front()) item_begin = 0;  // each family numbers its own items
     TcInst q;
     q.pts = prep[k].pts;
     q.wts = prep[k].wts;
@@ -603,7 +695,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
     q.tiles_n = I.tiles_n;
     q.splits = I.splits;
     q.item_begin = item_begin;
-    q.chunk_stages = P.tc.k_chunk / P.tc.stage_points;
+    q.chunk_stages = I.k_chunk / fam.plan.stage_points;
     // c = 2^-30 / (2 pi N h^2); the kernel multiplies by max |w|
     q.base_scale = a->n > 0 ? (float)(0x1p-30 / (2.0 * 3.14159265358979323846 * (double)a->n *
                                                  a->h * a->h))
@@ -769,13 +861,18 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
                                 reinterpret_cast<uint32_t*>(base + P.off_sp_nf),
                                 reinterpret_cast<uint32_t*>(base + P.off_sp_temp), batch_scal, s),
              "block-sparse work list");
-    KDE_CUDA(launch_tc_pair(P.tc, d_tc, P.n_tc, 0, &sp, batch_scal, s),
+    KDE_CUDA(launch_tc_pair(P.fam[0].plan, d_tc, P.n_tc, 0, &sp, batch_scal, s),
              "block-sparse tensor-core contraction");
     KDE_CUDA(launch_sparse_reduce(d_tc, P.n_tc, sp, s), "block-sparse reduce");
   } else if (P.n_tc) {
-    KDE_CUDA(P.tc.pair ? launch_tc_pair(P.tc, d_tc, P.n_tc, P.tc_items, nullptr, batch_scal, s)
-                       : launch_tc(P.tc, d_tc, P.n_tc, P.tc_items, batch_scal, s),
-             "tensor-core contraction");
+    for (const TcFamily& f : P.fam) {  // one persistent launch per tile family
+      if (f.items < 1) continue;
+      const int nf = (int)f.order.size();
+      KDE_CUDA(f.plan.pair
+                   ? launch_tc_pair(f.plan, d_tc + f.tab_begin, nf, f.items, nullptr, batch_scal, s)
+                   : launch_tc(f.plan, d_tc + f.tab_begin, nf, f.items, batch_scal, s),
+               "tensor-core contraction");
+    }
   }
   for (int k = 0; k < count; ++k) {
     const InstPlan& I = P.in[k];
@@ -813,8 +910,6 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, bool force_sync) 
         return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs[k].timeout_where);
       if (err & kErrNonFinite)
         return fail(KDE_EDATA, "instance %d: non-finite coordinate or weight", k);
-      if (err & kErrNegWeight)
-        return fail(KDE_EDATA, "the tensor-core paths need non-negative weights");
       if (err) return fail(KDE_ECUDA, "device error word 0x%x", err);
     }
   }
@@ -855,12 +950,12 @@ int kde_grid(const double* points, const float* weights, int64_t n, const double
   a.out = out;
   kde_opts o;
   kde_default_opts(&o);
-  return run_batch(&a, 1, &o, true);
+  return run_batch(&a, 1, &o, nullptr, true);
 }
 
 int kde_grid_ex(const kde_args* a, const kde_opts* opts) {
   if (!a) return fail(KDE_EINVAL, "args is NULL");
-  return run_batch(a, 1, opts, false);
+  return run_batch(a, 1, opts, nullptr, false);
 }
 
 int kde_workspace_size(const kde_args* a, const kde_opts* opts, size_t* bytes) {
@@ -868,7 +963,7 @@ int kde_workspace_size(const kde_args* a, const kde_opts* opts, size_t* bytes) {
   int rc = validate(a, opts);
   if (rc) return rc;
   BatchPlan pl;
-  rc = make_plan(a, 1, opts, true, &pl);
+  rc = make_plan(a, 1, opts, nullptr, true, &pl);
   if (rc) return rc;
   *bytes = pl.total;
   return KDE_OK;
@@ -894,7 +989,19 @@ int kde_grid_batched(const kde_args* inst, int count, const kde_opts* opts) {
   if (!inst || count < 0) return fail(KDE_EINVAL, "inst is NULL or count < 0");
   for (int b = 0; b < count; b += kMaxBatch) {
     const int c = std::min(kMaxBatch, count - b);
-    const int rc = run_batch(inst + b, c, opts, false);
+    const int rc = run_batch(inst + b, c, opts, nullptr, false);
+    if (rc) return rc;
+  }
+  if (opts && (opts->flags & KDE_FLAG_SYNC) && count == 0) g_err[0] = 0;
+  return KDE_OK;
+}
+
+int kde_grid_batched_tiled(const kde_args* inst, const kde_tiling* tiles, int count,
+                           const kde_opts* opts) {
+  if (!inst || count < 0) return fail(KDE_EINVAL, "inst is NULL or count < 0");
+  for (int b = 0; b < count; b += kMaxBatch) {
+    const int c = std::min(kMaxBatch, count - b);
+    const int rc = run_batch(inst + b, c, opts, tiles ? tiles + b : nullptr, false);
     if (rc) return rc;
   }
   if (opts && (opts->flags & KDE_FLAG_SYNC) && count == 0) g_err[0] = 0;
@@ -939,7 +1046,7 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
   rc = acquire_workspace(opts, off, s, &wsv);
   if (rc) return rc;
   char* base = static_cast<char*>(wsv);
-  PrepInst q;
+  PrepInst q = {};
   q.xy = a->points;
   q.w = a->weights;
   q.pts = reinterpret_cast<float4*>(base + o_pts);
@@ -1020,7 +1127,7 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
   const size_t o_gxt = take(sizeof(float2) * a->nx);
   const size_t o_gyt = take(sizeof(float2) * a->ny);
   const size_t o_loo = take(sizeof(double) * std::max<int64_t>(n, 1));
-  const size_t o_w2 = take(sizeof(double) * std::max<int64_t>(n, 1));
+  const size_t o_hd = take(sizeof(double) * std::max<int64_t>(n, 1));
   const size_t o_sq = take(sizeof(double) * sq_blocks);
   const size_t o_gd = take(grad_F ? sizeof(double) * (size_t)a->nx * a->ny : 0);
   const size_t o_part = take(sizeof(double) * 3 * (sum_partials(std::max<int64_t>(n, sq_blocks)) + 1));
@@ -1029,7 +1136,7 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
   rc = acquire_workspace(opts, off, s, &wsv);
   if (rc) return rc;
   char* base = static_cast<char*>(wsv);
-  PrepInst q;
+  PrepInst q = {};
   q.xy = a->points;
   q.w = a->weights;
   q.pts = reinterpret_cast<float4*>(base + o_pts);
@@ -1047,7 +1154,7 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
   q.nx = a->nx;
   q.ny = a->ny;
   double* loo = reinterpret_cast<double*>(base + o_loo);
-  double* w2 = reinterpret_cast<double*>(base + o_w2);
+  double* hd = reinterpret_cast<double*>(base + o_hd);
   double* sq = reinterpret_cast<double*>(base + o_sq);
   double* part = reinterpret_cast<double*>(base + o_part);
   double* res = reinterpret_cast<double*>(base + o_res);
@@ -1060,13 +1167,12 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
            "prepare points");
   KDE_CUDA(launch_lscv(q.pts, q.wts, n, F, a->nx, a->ny, a->cell, a->h,
                        grad_F ? reinterpret_cast<double*>(base + o_gd) : nullptr, grad_F,
-                       grad_w_direct, grad_points_direct, sq, sq_blocks, loo, s),
+                       grad_w_direct, grad_points_direct, sq, sq_blocks, loo, hd, s),
            "LSCV");
   KDE_CUDA(launch_sum(sq, sq_blocks, part, res, s), "sum");
   if (n > 0) {
-    KDE_CUDA(launch_square_weights(q.wts, n, w2, s), "squares");
     KDE_CUDA(launch_sum(loo, n, part + np, res + 1, s), "sum");
-    KDE_CUDA(launch_sum(w2, n, part + 2 * np, res + 2, s), "sum");
+    KDE_CUDA(launch_sum(hd, n, part + 2 * np, res + 2, s), "sum");
   }
   double hres[4];
   int err = 0;
@@ -1076,12 +1182,10 @@ int kde_lscv_grid(const kde_args* a, const float* F, double* loss, float* grad_F
   KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
   if (err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
   const double N = (double)std::max<int64_t>(n, 1);
-  // L = cell^2 sum F^2 - (2/N) sum_p w_p [bilerp - w_p K0/(N h^2)]
+  // L = cell^2 sum F^2 - (2/N) sum_p w_p bilerp(F - F_p, x_p)
   *loss = a->cell * a->cell * hres[0] - 2.0 / N * hres[1];
-  if (grad_h_direct) {
-    const double k0 = 1.0 / (2.0 * 3.14159265358979323846);
-    *grad_h_direct += -4.0 * k0 * hres[2] / (N * N * a->h * a->h * a->h);
-  }
+  // the direct dependence on h is through each point's own term F_p
+  if (grad_h_direct) *grad_h_direct += 2.0 / N * hres[2];
   g_err[0] = 0;
   return KDE_OK;
 }

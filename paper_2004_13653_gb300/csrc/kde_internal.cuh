@@ -22,13 +22,13 @@ namespace kde {
 constexpr int kErrTimeout = 1;    // a bounded device-side wait gave up
 constexpr int kErrNonFinite = 2;  // non-finite coordinate or weight
 constexpr int kErrBadArg = 4;     // a kernel saw an impossible argument
-constexpr int kErrNegWeight = 8;  // negative weight on a tensor-core path
 
 struct CallScalars {
   int err;            // OR of kErr* bits
   unsigned wmax_bits; // bit pattern of max |w| (non-negative floats order as ints)
   int timeout_where;  // role id of the first wait that gave up
-  int pad[61];        // keep the struct 256 bytes
+  int negw;           // nonzero when some weight is negative
+  int pad[60];        // keep the struct 256 bytes
 };
 
 // One factor k(s) of each Table 1 kernel without its constant; the constant
@@ -79,8 +79,19 @@ inline double kernel_sigma(int kid, double h) {
 
 constexpr int kMaxBatch = 256;  // instances per batched launch
 
+// Eq. 1-4 at one standard latitude phi0, set up on the host (kde_prep.cu):
+// x = lambda r0, y = r0 q(phi); near phi0 (|phi - phi0| <= range) y is the
+// Taylor series of q about phi0 (y0 + c1 d + c2 d^2 in FP64, orders 3..7 in
+// FP32), elsewhere the closed form with eccentricity e.
+struct MercParams {
+  double r0, kx, phi0, y0, c1, c2, range, e;
+  float c[5];
+};
+// Parameters of the projection at standard latitude lat0_deg (|lat0| < 90).
+MercParams mercator_params(double lat0_deg);
+
 struct PrepInst {
-  const double* xy;  // caller's points (device)
+  const double* xy;  // caller's points (device): metres, or (lon, lat) degrees when lonlat
   const float* w;    // caller's weights (device) or null
   float4* pts;       // prepared points, n_pad entries
   float* wts;
@@ -90,6 +101,8 @@ struct PrepInst {
   int64_t n, n_pad, begin;  // begin: offset in the flattened n_pad space
   double ox, oy, sigma, cell_sigma;
   int nx, ny;
+  int lonlat;       // 1: xy holds (lon, lat) degrees, projected here with merc
+  MercParams merc;
 };
 
 struct TcInst {
@@ -322,12 +335,12 @@ cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n,
                                  const float2* gxt, const float2* gyt, int nx, int ny,
                                  double cell, double h, float* grad_xy, float* grad_w,
                                  double* hterm, double* lterm, cudaStream_t s);
-// Gd: FP64 scratch for the cotangent (cells), G: FP32 cotangent out.
+// Gd: FP64 scratch for the cotangent (cells), G: FP32 cotangent out; loo and
+// hdir: per-point leave-one-out terms and direct dL/dh terms (sum hdir * 2/N).
 cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const float* F, int nx,
                         int ny, double cell, double h, double* Gd, float* G, float* gw_direct,
                         float* gxy_direct, double* sq_part, int sq_blocks, double* loo,
-                        cudaStream_t s);
-cudaError_t launch_square_weights(const float* w, int64_t n, double* w2, cudaStream_t s);
+                        double* hdir, cudaStream_t s);
 // Fixed-order sum of n doubles into *result (device); partial needs
 // sum_partials(n) doubles.
 size_t sum_partials(int64_t n);

@@ -12,14 +12,17 @@
 //
 // Limits and rules:
 //   * the scratch holds kNoAllocScratchBytes; inputs needing more are rejected
-//     with KDE_EINVAL (the message gives the bytes needed);
+//     with KDE_EINVAL before any launch (the point count is checked before any
+//     size is computed from it, so no size can wrap around);
 //   * every call on a device shares the array and it keeps the last call's
 //     contents: the status words are cleared at the start of each call, and
 //     calls that overlap on the GPU (different streams, or host threads that
 //     do not serialise) race on it;
-//   * the array's device address is looked up once per device, on the first
-//     call made with that device current; make that first call before any
-//     stream capture.
+//   * the array's device address is looked up once per device ordinal, on the
+//     first call made with that device current, and kept for the life of the
+//     process; make that first call before any stream capture.  A device
+//     reset (cudaDeviceReset) or a non-primary driver context invalidates the
+//     kept address, so neither is supported.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -44,6 +47,32 @@ int noalloc_fail(int code, const char* msg) {
 }
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Where each part of one call lives in the scratch.
+struct NoAllocLayout {
+  int64_t n_pad;
+  size_t off_scal, off_tab, off_pts, off_wts, off_gxt, off_gyt, need;
+};
+
+// Most points the scratch can hold (20 bytes each: a float4 and a weight).
+constexpr int64_t kNoAllocMaxPoints = (int64_t)(kNoAllocScratchBytes / 20);
+
+// The scratch layout for n points on an nx x ny grid (host only).  Returns
+// false, without forming any offset, when n alone exceeds the scratch, so no
+// size computed here can wrap around; otherwise L->need says whether the
+// whole layout fits.
+bool noalloc_layout(int64_t n, int nx, int ny, NoAllocLayout* L) {
+  if (n < 0 || n > kNoAllocMaxPoints || nx <= 0 || ny <= 0) return false;
+  L->n_pad = n < 512 ? 512 : (n + 511) / 512 * 512;
+  L->off_scal = 0;
+  L->off_tab = up256(L->off_scal + sizeof(CallScalars));
+  L->off_pts = up256(L->off_tab + sizeof(PrepInst));
+  L->off_wts = up256(L->off_pts + sizeof(float4) * (size_t)L->n_pad);
+  L->off_gxt = up256(L->off_wts + sizeof(float) * (size_t)L->n_pad);
+  L->off_gyt = up256(L->off_gxt + sizeof(float2) * (size_t)nx);
+  L->need = up256(L->off_gyt + sizeof(float2) * (size_t)ny);
+  return true;
+}
 
 bool device_pointer(const void* p) {
   cudaPointerAttributes at;
@@ -92,39 +121,39 @@ extern "C" int kde_grid_noalloc(const double* points, const float* weights, int6
       !isfinite(grid_origin[1]))
     return noalloc_fail(KDE_EINVAL, "kde_grid_noalloc: cell, h and origin must be finite, "
                                     "cell and h positive");
+  // the radial Gaussian is the product Gaussian; the radial compact kernels
+  // need the cutoff path, which this entry point does not run
+  if (kernel_id == kRadial + KDE_GAUSSIAN) kernel_id = KDE_GAUSSIAN;
   if (kernel_id < 0 || kernel_id > 7)
-    return noalloc_fail(KDE_EINVAL, "kde_grid_noalloc: kernel_id is not a Table 1 kernel");
+    return noalloc_fail(KDE_EINVAL, "kde_grid_noalloc: kernel_id is not a Table 1 kernel "
+                                    "(0..7) or the radial Gaussian (14)");
   if ((points && (reinterpret_cast<uintptr_t>(points) & 15)) ||
       (weights && (reinterpret_cast<uintptr_t>(weights) & 3)) ||
       (reinterpret_cast<uintptr_t>(out) & 3))
     return noalloc_fail(KDE_EINVAL, "kde_grid_noalloc: misaligned pointer");
+  NoAllocLayout L;
+  if (!noalloc_layout(n, nx, ny, &L) || L.need > kNoAllocScratchBytes) {
+    char msg[256];
+    snprintf(msg, sizeof(msg),
+             "kde_grid_noalloc: %lld points on a %d x %d grid exceed the static maximum of %zu "
+             "bytes of scratch (at most %lld points, fewer on large grids)",
+             (long long)n, nx, ny, kNoAllocScratchBytes, (long long)kNoAllocMaxPoints);
+    return noalloc_fail(KDE_EINVAL, msg);
+  }
   if ((n > 0 && !device_pointer(points)) || (n > 0 && weights && !device_pointer(weights)) ||
       !device_pointer(out))
     return noalloc_fail(KDE_EINVAL, "kde_grid_noalloc: points, weights and out must be device memory");
 
-  const int64_t n_pad = n < 512 ? 512 : (n + 511) / 512 * 512;
-  const size_t off_scal = 0;
-  const size_t off_tab = up256(off_scal + sizeof(CallScalars));
-  const size_t off_pts = up256(off_tab + sizeof(PrepInst));
-  const size_t off_wts = up256(off_pts + sizeof(float4) * (size_t)n_pad);
-  const size_t off_gxt = up256(off_wts + sizeof(float) * (size_t)n_pad);
-  const size_t off_gyt = up256(off_gxt + sizeof(float2) * (size_t)nx);
-  const size_t need = up256(off_gyt + sizeof(float2) * (size_t)ny);
-  if (need > kNoAllocScratchBytes) {
-    char msg[256];
-    snprintf(msg, sizeof(msg),
-             "kde_grid_noalloc: these inputs need %zu bytes of scratch; the static maximum is "
-             "%zu bytes (about %zu points on a small grid)",
-             need, kNoAllocScratchBytes, kNoAllocScratchBytes / 20);
-    return noalloc_fail(KDE_EINVAL, msg);
-  }
+  const int64_t n_pad = L.n_pad;
+  const size_t off_scal = L.off_scal, off_tab = L.off_tab, off_pts = L.off_pts,
+               off_wts = L.off_wts, off_gxt = L.off_gxt, off_gyt = L.off_gyt;
   void* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc) return rc;
   char* base = static_cast<char*>(scratch);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  PrepInst q;
+  PrepInst q = {};
   q.xy = points;
   q.w = weights;
   q.pts = reinterpret_cast<float4*>(base + off_pts);

@@ -24,35 +24,36 @@ constexpr double kWgs84E2 = 0.00669437999014;
 // FP64, the terms of order 3..7 (a few metres at most) in FP32.  Elsewhere the
 // closed form is evaluated in FP64.  GB300's FP64 rate makes the closed form
 // (two logarithms, a tangent and a sine per point) the slow part.
-struct MercSeries {
-  double r0, kx, phi0, y0, c1, c2;  // kx = r0 pi/180; y0 = r0 q(phi0); c_k = r0 q^(k)(phi0)/k!
-  double range;                     // |phi - phi0| up to which the series is used
-  float c[5];                       // c3 .. c7
-};
+// MercParams: kx = r0 pi/180; y0 = r0 q(phi0); c_k = r0 q^(k)(phi0)/k!
+// (c[] holds c3 .. c7); range: |phi - phi0| up to which the series is used.
+using MercSeries = MercParams;
 
-__global__ void k_mercator(const double* __restrict__ lonlat, int64_t n, double e,
-                           const __grid_constant__ MercSeries m, double* __restrict__ xy) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const double2 ll = reinterpret_cast<const double2*>(lonlat)[p];
-    const double phi = ll.y * (kPi / 180.0);
-    const double d = phi - m.phi0;
-    double y;
-    if (fabs(d) <= m.range) {
-      const float df = (float)d;
-      float t = m.c[4];
-      t = fmaf(t, df, m.c[3]);
-      t = fmaf(t, df, m.c[2]);
-      t = fmaf(t, df, m.c[1]);
-      t = fmaf(t, df, m.c[0]);
-      y = fma(m.c2, d * d, fma(m.c1, d, m.y0)) + (double)(t * (df * df * df));
-    } else {
-      const double es = e * sin(phi);
-      const double q = log(tan(0.25 * kPi + 0.5 * phi)) + 0.5 * e * log((1.0 - es) / (1.0 + es));
-      y = q * m.r0;
-    }
-    reinterpret_cast<double2*>(xy)[p] = make_double2(ll.x * m.kx, y);
+__device__ __forceinline__ double2 mercator_xy(double2 ll, const MercParams& m) {
+  const double phi = ll.y * (kPi / 180.0);
+  const double d = phi - m.phi0;
+  double y;
+  if (fabs(d) <= m.range) {
+    const float df = (float)d;
+    float t = m.c[4];
+    t = fmaf(t, df, m.c[3]);
+    t = fmaf(t, df, m.c[2]);
+    t = fmaf(t, df, m.c[1]);
+    t = fmaf(t, df, m.c[0]);
+    y = fma(m.c2, d * d, fma(m.c1, d, m.y0)) + (double)(t * (df * df * df));
+  } else {
+    const double es = m.e * sin(phi);
+    const double q = log(tan(0.25 * kPi + 0.5 * phi)) + 0.5 * m.e * log((1.0 - es) / (1.0 + es));
+    y = q * m.r0;
   }
+  return make_double2(ll.x * m.kx, y);
+}
+
+__global__ void k_mercator(const double* __restrict__ lonlat, int64_t n,
+                           const __grid_constant__ MercParams m, double* __restrict__ xy) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+    reinterpret_cast<double2*>(xy)[p] =
+        mercator_xy(reinterpret_cast<const double2*>(lonlat)[p], m);
 }
 
 // Truncated power series in d (order kOrd) on the host.
@@ -112,6 +113,7 @@ MercSeries mercator_series(double phi0, double r0, double e2) {
   m.range = 0.01;
   while (m.range > 1e-4 && c3 * pow(m.range, 3) * 1.2e-7 + c8 * pow(m.range, 8) > 2e-7)
     m.range *= 0.9;
+  m.e = e;
   return m;
 }
 
@@ -145,7 +147,8 @@ __global__ void k_prepare(const PrepInst* __restrict__ tab, int ninst, int64_t t
     bool bad = false;
     unsigned wbits = 0;
     if (p < I.n) {
-      const double2 v = reinterpret_cast<const double2*>(I.xy)[p];
+      double2 v = reinterpret_cast<const double2*>(I.xy)[p];
+      if (I.lonlat) v = mercator_xy(v, I.merc);  // Eq. 1-4 fused into the centring
       const double X = (v.x - I.ox) * I.sigma;
       const double Y = (v.y - I.oy) * I.sigma;
       wv = I.w ? I.w[p] : 1.0f;
@@ -163,9 +166,11 @@ __global__ void k_prepare(const PrepInst* __restrict__ tab, int ninst, int64_t t
     // warp-level max, one atomic per warp (all lanes share the instance)
     for (int o = 16; o > 0; o >>= 1) wbits = max(wbits, __shfl_xor_sync(0xffffffffu, wbits, o));
     const unsigned anybad = __any_sync(0xffffffffu, bad);
+    const unsigned anyneg = __any_sync(0xffffffffu, wv < 0.f);
     if ((threadIdx.x & 31) == 0) {
       if (wbits) atomicMax(&I.scal->wmax_bits, wbits);
       if (anybad) atomicOr(&I.scal->err, kErrNonFinite);
+      if (anyneg) atomicOr(&I.scal->negw, 1);
     }
   }
 }
@@ -198,13 +203,17 @@ int blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
+MercParams mercator_params(double lat0_deg) {
+  const double phi0 = lat0_deg * (kPi / 180.0);
+  const double r0 = kWgs84A * cos(phi0) / sqrt(1.0 - kWgs84E2 * sin(phi0) * sin(phi0));
+  return mercator_series(phi0, r0, kWgs84E2);
+}
+
 cudaError_t launch_mercator(const double* lonlat, int64_t n, double lat0_deg, double* xy,
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const double phi0 = lat0_deg * (kPi / 180.0);
-  const double r0 = kWgs84A * cos(phi0) / sqrt(1.0 - kWgs84E2 * sin(phi0) * sin(phi0));
-  const MercSeries m = mercator_series(phi0, r0, kWgs84E2);
-  k_mercator<<<blocks_for(n, 256), 256, 0, s>>>(lonlat, n, sqrt(kWgs84E2), m, xy);
+  const MercParams m = mercator_params(lat0_deg);
+  k_mercator<<<blocks_for(n, 256), 256, 0, s>>>(lonlat, n, m, xy);
   note_launches(1);
   return cudaGetLastError();
 }

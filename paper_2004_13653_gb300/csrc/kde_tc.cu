@@ -64,8 +64,8 @@ struct Cfg {
   // shared-memory map (offsets from a 1024-byte aligned base)
   static constexpr int kOffA = 0;                               // A_hi [, A_lo]
   static constexpr int kOffB = kParts * kABytes;                // B_hi [, B_lo]
-  static constexpr int kOffParams = kStages * kStageBytes;      // float[kPS][3][kKS]
-  static constexpr int kOffBars = kOffParams + kPS * 3 * kKS * 4;
+  static constexpr int kOffParams = kStages * kStageBytes;      // float[kPS][4][kKS]
+  static constexpr int kOffBars = kOffParams + kPS * 4 * kKS * 4;
   static constexpr int kNumBars = 2 * kStages + 2 * kPS + 4 + 1;
   static constexpr int kOffMisc = kOffBars + kNumBars * 8;      // tmem slot, abort flag
   static constexpr int kSmemBytes = kOffMisc + 64 + 1024;       // + alignment slack
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
   } else if (warp == 1) {
     // --------------------------------------------------------- point loader
     uint32_t g = 0;
-    bool ok = true, negative = false;
+    bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
       const Item itm = item_of(tab, ninst, it, kKS);
       const TcInst& I = *itm.I;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
           const uint32_t ps = g % kPS;
           if (!(ok = mbar_wait(&pempty[ps], ((g / kPS) & 1) ^ 1, abort_flag, scal, kRoleLoader)))
             break;
-          float* prm = params + ps * 3 * kKS;
+          float* prm = params + ps * 4 * kKS;
 #pragma unroll
           for (int hh = 0; hh < kPer; ++hh) {
             const int e = lane + 32 * hh;
@@ -289,16 +289,16 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
             prm[e] = (q.x - cx.x) + (q.y - cx.y);
             prm[kKS + e] = (q.z - cy.x) + (q.w - cy.y);
             const float w = W[u][hh];
-            negative |= w < 0.f;
-            // B = (w / w_max) 2^(15 - v^2) = 2^(cb - v^2); w = 0 gives cb = -inf, B = 0
-            prm[2 * kKS + e] = w > 0.f ? 15.0f + log2f(w * inv_wmax) : -INFINITY;
+            // |B| = (|w| / w_max) 2^(15 - v^2) = 2^(cb - v^2); w = 0 gives cb = -inf,
+            // B = 0; the sign of w is kept as a sign bit to apply to B
+            prm[2 * kKS + e] = w != 0.f ? 15.0f + log2f(fabsf(w) * inv_wmax) : -INFINITY;
+            reinterpret_cast<uint32_t*>(prm)[3 * kKS + e] = w < 0.f ? 0x80000000u : 0u;
           }
           mbar_arrive(&pfull[ps]);
           ++g;
         }
       }
     }
-    if (__any_sync(0xffffffffu, negative) && lane == 0) atomicOr(&scal->err, kErrNegWeight);
   } else if (warp < 6) {
     // ------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
       const Item itm = item_of(tab, ninst, it, kKS);
       const TcInst& I = *itm.I;
+      const bool signs = !isA && I.scal->negw != 0;
       float gv;
       if (isA) {
         const float2 c = I.gxt[min(itm.tm * kBM + kBM / 2, I.nx - 1)];
@@ -403,8 +404,9 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
           break;
         unsigned char* hi_row =
             smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
-        const float4* crd = reinterpret_cast<const float4*>(params + ps * 3 * kKS + (isA ? 0 : kKS));
-        const float4* cbv = reinterpret_cast<const float4*>(params + ps * 3 * kKS + 2 * kKS);
+        const float4* crd = reinterpret_cast<const float4*>(params + ps * 4 * kKS + (isA ? 0 : kKS));
+        const float4* cbv = reinterpret_cast<const float4*>(params + ps * 4 * kKS + 2 * kKS);
+        const uint4* sgn = reinterpret_cast<const uint4*>(params + ps * 4 * kKS + 3 * kKS);
 #pragma unroll 4
         for (int c = 0; c < C::kChunks; ++c) {
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
@@ -420,6 +422,12 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
           for (int e2 = 0; e2 < 8; ++e2) {
             const float u = gv - pc[e2];
             asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
+          }
+          if (signs) {  // negative weights: B takes the weight's sign
+            const uint4 s0 = sgn[2 * c], s1 = sgn[2 * c + 1];
+            const uint32_t sb[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+            for (int e2 = 0; e2 < 8; ++e2) v[e2] = __uint_as_float(__float_as_uint(v[e2]) ^ sb[e2]);
           }
           const int off = (c ^ ((r >> C::kSwzShift) & (C::kChunks - 1))) << 4;
           uint32_t hw[4], lw[4];

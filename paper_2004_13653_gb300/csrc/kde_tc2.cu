@@ -9,18 +9,35 @@
 // TMEM.  Per output pair this generates a third fewer exponentials than one
 // CTA with a 128 x 256 tile, and each SM's shared memory serves half of B.
 //
-// Roles in each CTA: warp 0 (leader CTA, one thread) issues the MMAs; warp 1
-// loads and re-centres points; warps 2-9 drain this CTA's TMEM (two warps per
-// lane quadrant, 128 columns each); warps 10-17 generate operand rows.
-// Producers of both CTAs signal the leader's stage barriers; MMA completion is
-// multicast to both CTAs; both CTAs' epilogues signal the leader when the
-// accumulator is free again.
+// Roles, by warpgroup (setmaxnreg divides the registers per warpgroup):
+//   WG0   warp 0: MMA issue (leader CTA, one thread); warp 1: loads and
+//         re-centres the points of each stage; warp 2: signals each finished
+//         stage to the leader (one cluster arrive per CTA and stage); warp 3
+//         idles.  48 registers.
+//   WG1-2 warps 4-11: epilogue.  Each thread owns one TMEM lane (an x cell)
+//         and 128 of the tile's 256 y cells, and keeps their running sums in
+//         its registers (168 registers).
+//   WG3-4 warps 12-19: operand producers, one thread per A or B row
+//         (48 registers).
 //
-// Accumulator: one N = 256 accumulator in TMEM columns [0, 256) (column j is
-// y cell j of the tile: CTA 0 supplies B rows 0-127, CTA 1 rows 128-255),
-// drained every chunk into a running sum in columns [256, 512) while the
-// tensor core waits.  N = 256 MMAs keep each SM's operand reads at 8 KB per
-// 128 cycles.
+// Accumulators: two N = 256 FP32 accumulators fill TMEM's 512 columns.  The
+// MMAs of chunk c (k_chunk points) accumulate into accumulator c mod 2 while
+// the epilogues add chunk c - 1 into their registers, so the tensor core does
+// not wait for a drain.  Chunks stay short because the tensor core's FP32
+// accumulation loses accuracy with every MMA step it adds into a large sum;
+// the running sums add the chunks with IEEE FP32 adds.
+//
+// Stage hand-off: each producer orders its shared-memory stores before the
+// tensor core's (async-proxy) reads with fence.proxy.async and arrives on a
+// named barrier without waiting; the signalling warp waits on that barrier
+// and makes one cluster-scope release arrive on the leader's stage barrier.
+// The barrier's id follows the stage slot, so a producer can reach the same
+// id again only after the MMAs have consumed that slot, i.e. after the
+// barrier completed.
+//
+// Weights enter B as log2(|w|/w_max) in the exponent; an instance with a
+// negative weight (flagged by the prepare kernel) also gets each B value's
+// sign, applied to the packed FP16 hi/lo words.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -36,9 +53,28 @@ using namespace tc;
 constexpr int kRows = 128;  // A rows and B rows each CTA of the pair generates
 constexpr int kKS = 64;     // points per stage
 constexpr int kPS = 8;      // point-parameter ring depth
-constexpr int kGroup = 4;   // stages the loader fetches at once
+constexpr int kGroup = 1;   // stages the loader fetches at once
 
-enum Role : int { kRoleMma = 11, kRoleLoader = 12, kRoleEpilogue = 13, kRoleProducer = 14 };
+// parameter ring slot: A coordinates, B coordinates, B exponent offsets
+// (-(15 + log2(|w|/w_max)), +inf for w = 0), B sign words of point pairs
+constexpr int kPrmA = 0, kPrmB = kKS, kPrmN = 2 * kKS, kPrmS = 3 * kKS;
+constexpr int kPrmFloats = 3 * kKS + kKS / 2;
+
+// warp roles and register budgets (see the file comment)
+constexpr int kWarps = 20;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kWarpMma = 0, kWarpLoader = 1, kWarpSignal = 2;
+constexpr int kFirstEpiWarp = 4, kEpiWarps = 8;
+constexpr int kFirstProducerWarp = 12, kProducerWarps = 8;
+constexpr int kRegsLaunch = 96;  // 640 threads: at most 65536 / 640 = 102, allocated in 8s
+constexpr int kRegsCtl = 48, kRegsEpi = 168, kRegsProd = 48;
+static_assert(128 * kRegsCtl + 256 * kRegsEpi + 256 * kRegsProd <= kThreads * kRegsLaunch,
+              "the warpgroups' register budgets exceed the block's pool");
+constexpr int kBarProducers = 1;  // named barriers 1..kStages: producers -> signal warp
+
+enum Role : int {
+  kRoleMma = 11, kRoleLoader = 12, kRoleEpilogue = 13, kRoleProducer = 14, kRoleSignal = 15
+};
 
 template <bool SPLIT, bool SPARSE>
 struct PairCfg {
@@ -48,25 +84,17 @@ struct PairCfg {
   static constexpr int kParts = SPLIT ? 2 : 1;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kStages = (192 * 1024) / kStageBytes;
-  // producer threads per operand row, each taking 64 / kPerRow points of a
-  // stage (one: 576 threads, which leaves the epilogue the registers for
-  // 32-column drain slices)
-  static constexpr int kPerRow = 1;
-  static constexpr int kProducers = 2 * kRows * kPerRow;
-  static constexpr int kProducerWarps = kProducers / 32;
-  static constexpr int kEpiWarps = 8;
-  static constexpr int kFirstProducerWarp = 2 + kEpiWarps;
-  static constexpr int kThreads = 32 * (kFirstProducerWarp + kProducerWarps);
   static constexpr uint32_t kTmemCols = 512;
   static constexpr uint32_t kIdesc = idesc_f16_f32(256, 256);
   static constexpr int kOffA = 0;
   static constexpr int kOffB = kParts * kABytes;
   static constexpr int kOffParams = kStages * kStageBytes;
-  static constexpr int kOffBars = kOffParams + kPS * 3 * kKS * 4;
-  static constexpr int kNumBars = 2 * kStages + 2 * kPS + 2 + 1;
+  static constexpr int kOffBars = kOffParams + kPS * kPrmFloats * 4;
+  static constexpr int kNumBars = 2 * kStages + 2 * kPS + 2 + 2 + 1;
   static constexpr int kOffMisc = kOffBars + kNumBars * 8;
   static constexpr int kSmemBytes = kOffMisc + 64 + 1024;
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+  static_assert(kBarProducers + kStages <= 16, "named barrier ids");
 };
 
 struct Item {
@@ -158,7 +186,7 @@ __device__ __forceinline__ int sched_pos(int r, int c, int nc) {
 }
 
 template <bool SPLIT, bool SPARSE>
-__global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_tc_pair(const TcInst* __restrict__ tab, int ninst, int n_items_arg,
               const __grid_constant__ SparseCtl sp, CallScalars* __restrict__ scal) {
   using C = PairCfg<SPLIT, SPARSE>;
@@ -166,13 +194,13 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* params = reinterpret_cast<float*>(smem + C::kOffParams);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBars);
-  uint64_t* full = bars;                    // [kStages] producers (both CTAs) -> leader MMA
+  uint64_t* full = bars;                    // [kStages] signal warps (both CTAs) -> leader MMA
   uint64_t* empty = bars + C::kStages;      // [kStages] MMA -> producers (multicast)
   uint64_t* pfull = bars + 2 * C::kStages;  // [kPS] loader -> producers
-  uint64_t* pempty = pfull + kPS;           // [kPS] producers -> loader
-  uint64_t* accfull = pempty + kPS;         // [1] MMA -> epilogues (multicast)
-  uint64_t* accempty = accfull + 1;         // [1] epilogues (both CTAs) -> leader MMA
-  uint64_t* mmadone = accempty + 1;         // [1]
+  uint64_t* pempty = pfull + kPS;           // [kPS] signal warp -> loader
+  uint64_t* accfull = pempty + kPS;         // [2] MMA -> epilogues (multicast)
+  uint64_t* accempty = accfull + 2;         // [2] epilogues (both CTAs) -> leader MMA
+  uint64_t* mmadone = accempty + 2;         // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kOffMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::kOffMisc + 4);
 
@@ -194,15 +222,17 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
-      mbar_init(&full[s], 2 * C::kProducerWarps);
+      mbar_init(&full[s], 2);  // one signal-warp arrive per CTA of the pair
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < kPS; ++s) {
       mbar_init(&pfull[s], 32);
-      mbar_init(&pempty[s], C::kProducerWarps);
+      mbar_init(&pempty[s], 1);
     }
-    mbar_init(accfull, 1);
-    mbar_init(accempty, 2 * C::kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 2 * kEpiWarps);
+    }
     mbar_init(mmadone, 1);
     *abort_flag = 0;
     mbar_init_fence();
@@ -214,118 +244,160 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == 0) {
-    // ------------------------------------------------- MMA issue (leader only)
-    if (rank == 0 && lane == 0) {
-      uint32_t g = 0, mc = 0;
+  if (warp < kFirstEpiWarp) {
+    regs_dec<kRegsCtl>();
+    if (warp == kWarpMma) {
+      // ----------------------------------------------- MMA issue (leader only)
+      if (rank == 0 && lane == 0) {
+        uint32_t g = 0, mc = 0;
+        bool ok = true;
+        const uint32_t smem_base = smem_u32(smem);
+        for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+             it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+          const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
+          const int CS = itm.I->chunk_stages;
+          uint32_t acc_addr = tmem_base;
+          for (int st = 0; ok && st < itm.nst; ++st, ++g) {
+            const bool fresh = st % CS == 0;
+            if (fresh) {  // both CTAs' epilogues have taken this accumulator's last chunk
+              const uint32_t b = mc & 1u;
+              if (!(ok = mbar_wait_cluster(&accempty[b], ((mc >> 1) & 1u) ^ 1u, abort_flag, scal,
+                                           kRoleMma)))
+                break;
+              tc_fence_after();
+              acc_addr = tmem_base + b * 256u;
+            }
+            const uint32_t s = g % C::kStages;
+            if (!(ok = mbar_wait_cluster(&full[s], (g / C::kStages) & 1, abort_flag, scal,
+                                         kRoleMma)))
+              break;
+            tc_fence_after();
+            const uint32_t a0 = smem_base + s * C::kStageBytes + C::kOffA;
+            const uint32_t b0 = smem_base + s * C::kStageBytes + C::kOffB;
+            const uint64_t ahi = desc_swz(a0, 2u, 1024u), alo = desc_swz(a0 + C::kABytes, 2u, 1024u);
+            const uint64_t bhi = desc_swz(b0, 2u, 1024u), blo = desc_swz(b0 + C::kBBytes, 2u, 1024u);
+#pragma unroll
+            for (int k = 0; k < kKS / 16; ++k) {
+              const uint32_t acc = (fresh && k == 0) ? 0u : 1u;
+              const uint64_t dk = (uint64_t)(2 * k);
+              mma_f16_pair(acc_addr, ahi + dk, bhi + dk, C::kIdesc, acc);
+              if (SPLIT) {
+                mma_f16_pair(acc_addr, ahi + dk, blo + dk, C::kIdesc, 1u);
+                mma_f16_pair(acc_addr, alo + dk, bhi + dk, C::kIdesc, 1u);
+              }
+            }
+            mma_commit_pair(&empty[s]);
+            if (st + 1 == itm.nst || (st + 1) % CS == 0) {
+              mma_commit_pair(&accfull[mc & 1u]);
+              ++mc;
+            }
+          }
+        }
+        if (!ok) propagate_abort();
+        mma_commit_pair(mmadone);
+        mbar_wait(mmadone, 0, abort_flag, scal, kRoleMma, /*honour_abort=*/false);
+      }
+      __syncwarp();
+    } else if (warp == kWarpLoader) {
+      // ------------------------------------------------------- point loader
+      uint32_t g = 0;
       bool ok = true;
-      const uint32_t smem_base = smem_u32(smem);
       for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
            it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
         const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
-        const int CS = itm.I->chunk_stages;
-        for (int st = 0; ok && st < itm.nst; ++st, ++g) {
-          const bool fresh = st % CS == 0;
-          if (fresh) {  // the epilogues of both CTAs have drained the accumulator
-            if (!(ok = mbar_wait_cluster(accempty, (mc & 1) ^ 1, abort_flag, scal, kRoleMma))) break;
-            ++mc;
-            tc_fence_after();
-          }
-          const uint32_t s = g % C::kStages;
-          if (!(ok = mbar_wait_cluster(&full[s], (g / C::kStages) & 1, abort_flag, scal, kRoleMma)))
-            break;
-          tc_fence_after();
-          const uint32_t a0 = smem_base + s * C::kStageBytes + C::kOffA;
-          const uint32_t b0 = smem_base + s * C::kStageBytes + C::kOffB;
-          const uint64_t ahi = desc_swz(a0, 2u, 1024u), alo = desc_swz(a0 + C::kABytes, 2u, 1024u);
-          const uint64_t bhi = desc_swz(b0, 2u, 1024u), blo = desc_swz(b0 + C::kBBytes, 2u, 1024u);
+        const TcInst& I = *itm.I;
+        const float wmax = __uint_as_float(I.scal->wmax_bits);
+        const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
+        const float2 cx = I.gxt[min(itm.tm * 256 + (int)rank * kRows + kRows / 2, I.nx - 1)];
+        const float2 cy = I.gyt[min(itm.tn * 256 + (int)rank * kRows + kRows / 2, I.ny - 1)];
+        RunCursor cur;
+        if (SPARSE)  // items exist only for tiles whose range holds points
+          cur.init(I.start, I.bin_begin, I.nbx,
+                   tile_bins(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby, itm.tm, itm.tn));
+        for (int st = 0; ok && st < itm.nst; st += kGroup) {
+          const int ng = min(kGroup, itm.nst - st);
+          float4 P[kGroup][2];
+          float W[kGroup][2];
 #pragma unroll
-          for (int k = 0; k < kKS / 16; ++k) {
-            const uint32_t acc = (fresh && k == 0) ? 0u : 1u;
-            const uint64_t dk = (uint64_t)(2 * k);
-            mma_f16_pair(tmem_base, ahi + dk, bhi + dk, C::kIdesc, acc);
-            if (SPLIT) {
-              mma_f16_pair(tmem_base, ahi + dk, blo + dk, C::kIdesc, 1u);
-              mma_f16_pair(tmem_base, alo + dk, bhi + dk, C::kIdesc, 1u);
-            }
-          }
-          mma_commit_pair(&empty[s]);
-          if (st + 1 == itm.nst || (st + 1) % CS == 0) mma_commit_pair(accfull);
-        }
-      }
-      if (!ok) propagate_abort();
-      mma_commit_pair(mmadone);
-      mbar_wait(mmadone, 0, abort_flag, scal, kRoleMma, /*honour_abort=*/false);
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    // --------------------------------------------------------- point loader
-    uint32_t g = 0;
-    bool ok = true, negative = false;
-    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
-         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
-      const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
-      const TcInst& I = *itm.I;
-      const float wmax = __uint_as_float(I.scal->wmax_bits);
-      const float inv_wmax = wmax > 0.f ? 1.0f / wmax : 1.0f;
-      const float2 cx = I.gxt[min(itm.tm * 256 + (int)rank * kRows + kRows / 2, I.nx - 1)];
-      const float2 cy = I.gyt[min(itm.tn * 256 + (int)rank * kRows + kRows / 2, I.ny - 1)];
-      RunCursor cur;
-      if (SPARSE)  // items exist only for tiles whose range holds points
-        cur.init(I.start, I.bin_begin, I.nbx,
-                 tile_bins(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby, itm.tm, itm.tn));
-      for (int st = 0; ok && st < itm.nst; st += kGroup) {
-        const int ng = min(kGroup, itm.nst - st);
-        float4 P[kGroup][2];
-        float W[kGroup][2];
+          for (int u = 0; u < kGroup; ++u)
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u)
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh)
-            if (u < ng) {
-              const int64_t v = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
-              if (!SPARSE) {
-                P[u][hh] = __ldg(I.pts + v);
-                W[u][hh] = __ldg(I.wts + v);
-              } else if (v < itm.vend) {
-                const int64_t p = cur.map(v);
-                P[u][hh] = __ldg(I.pts + p);
-                W[u][hh] = __ldg(I.wts + p);
-              } else {  // past the piece: a zero-weight point (B = 0)
-                P[u][hh] = make_float4(0.f, 0.f, 0.f, 0.f);
-                W[u][hh] = 0.f;
+            for (int hh = 0; hh < 2; ++hh)
+              if (u < ng) {
+                const int64_t v = itm.k_begin + (int64_t)(st + u) * kKS + lane + 32 * hh;
+                if (!SPARSE) {
+                  P[u][hh] = __ldg(I.pts + v);
+                  W[u][hh] = __ldg(I.wts + v);
+                } else if (v < itm.vend) {
+                  const int64_t p = cur.map(v);
+                  P[u][hh] = __ldg(I.pts + p);
+                  W[u][hh] = __ldg(I.wts + p);
+                } else {  // past the piece: a zero-weight point (B = 0)
+                  P[u][hh] = make_float4(0.f, 0.f, 0.f, 0.f);
+                  W[u][hh] = 0.f;
+                }
               }
+#pragma unroll
+          for (int u = 0; u < kGroup; ++u) {
+            if (u >= ng) break;
+            const uint32_t ps = g % kPS;
+            if (!(ok = mbar_wait(&pempty[ps], ((g / kPS) & 1) ^ 1, abort_flag, scal, kRoleLoader)))
+              break;
+            float* prm = params + ps * kPrmFloats;
+            uint32_t neg[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int e = lane + 32 * hh;
+              const float4 q = P[u][hh];
+              prm[kPrmA + e] = (q.x - cx.x) + (q.y - cx.y);
+              prm[kPrmB + e] = (q.z - cy.x) + (q.w - cy.y);
+              const float w = W[u][hh];
+              neg[hh] = w < 0.f ? 1u : 0u;
+              prm[kPrmN + e] = w != 0.f ? -(15.0f + log2f(fabsf(w) * inv_wmax)) : INFINITY;
             }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-          if (u >= ng) break;
-          const uint32_t ps = g % kPS;
-          if (!(ok = mbar_wait(&pempty[ps], ((g / kPS) & 1) ^ 1, abort_flag, scal, kRoleLoader)))
-            break;
-          float* prm = params + ps * 3 * kKS;
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int e = lane + 32 * hh;
-            const float4 q = P[u][hh];
-            prm[e] = (q.x - cx.x) + (q.y - cx.y);
-            prm[kKS + e] = (q.z - cy.x) + (q.w - cy.y);
-            const float w = W[u][hh];
-            negative |= w < 0.f;
-            prm[2 * kKS + e] = w > 0.f ? 15.0f + log2f(w * inv_wmax) : -INFINITY;
+            // sign word of points (2 lane, 2 lane + 1): bit 15 and bit 31, the
+            // sign bits of their packed FP16 halves
+            const int src = (2 * lane) & 31;
+            const uint32_t h = lane < 16 ? 0u : 1u;
+            const uint32_t s_lo = __shfl_sync(0xffffffffu, neg[0], src) |
+                                  (__shfl_sync(0xffffffffu, neg[1], src) << 1);
+            const uint32_t s_hi = __shfl_sync(0xffffffffu, neg[0], src + 1) |
+                                  (__shfl_sync(0xffffffffu, neg[1], src + 1) << 1);
+            reinterpret_cast<uint32_t*>(prm + kPrmS)[lane] =
+                (((s_lo >> h) & 1u) << 15) | (((s_hi >> h) & 1u) << 31);
+            mbar_arrive(&pfull[ps]);
+            ++g;
           }
-          mbar_arrive(&pfull[ps]);
-          ++g;
+        }
+      }
+      if (!ok && lane == 0) propagate_abort();
+    } else if (warp == kWarpSignal) {
+      // ------------------------------------------- stage hand-off to the MMA
+      // It takes part in every stage's barrier, aborted or not, because the
+      // producers arrive at every stage's barrier whatever happens.
+      const uint32_t full_leader0 = map_to_rank(smem_u32(&full[0]), 0);
+      uint32_t g = 0;
+      for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); it < n_items;
+           it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+        const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
+        for (int st = 0; st < itm.nst; ++st, ++g) {
+          const uint32_t s = g % C::kStages;
+          // every producer of this CTA has fenced and arrived for stage g
+          named_sync(kBarProducers + (int)s, 32 * (kProducerWarps + 1));
+          if (lane == 0 && !*abort_flag) {
+            mbar_arrive_cluster(full_leader0 + 8u * s);
+            mbar_arrive(&pempty[g % kPS]);
+          }
+          __syncwarp();
         }
       }
     }
-    if (!ok && lane == 0) propagate_abort();
-    if (__any_sync(0xffffffffu, negative) && lane == 0) atomicOr(&scal->err, kErrNegWeight);
-  } else if (warp < C::kFirstProducerWarp) {
+  } else if (warp < kFirstProducerWarp) {
     // ------------------------------------------------------------- epilogue
+    regs_inc<kRegsEpi>();
     const int q = warp & 3;                         // TMEM lane quadrant
-    const int colh = (warp - 2) >> 2;               // which 128 columns
+    const int colh = (warp - kFirstEpiWarp) >> 2;   // which 128 columns
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const uint32_t accempty_leader = map_to_rank(smem_u32(accempty), 0);
+    const uint32_t accempty_leader0 = map_to_rank(smem_u32(&accempty[0]), 0);
     uint32_t dc = 0;
     bool ok = true;
     for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
@@ -338,80 +410,69 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
       const int i = itm.tm * 256 + (int)rank * kRows + q * 32 + lane;
       const int j0 = itm.tn * 256 + colh * 128;
       float* slot = I.part + (int64_t)itm.s * nx * ny;
-      // sparse: the piece's own 256 x 256 partial, [j_local][i_local]
       float* piece = SPARSE ? sp.part + itm.slot * 65536 + (int64_t)(colh * 128) * 256 +
                                   (int)rank * kRows + q * 32 + lane
                             : nullptr;
-      if (!SPARSE && itm.nst == 0) {
-        if (i < nx)
+      if (itm.nst == 0) {  // no points in this item's range: its sums are zero
+        if (SPARSE)
+          for (int c = 0; c < 128; ++c) piece[c * 256] = 0.f;
+        else if (i < nx)
           for (int c = 0; c < 128 && j0 + c < ny; ++c) slot[(int64_t)(j0 + c) * nx + i] = 0.f;
         continue;
       }
+      float run[128];
       const int nchunks = (itm.nst + CS - 1) / CS;
       for (int ch = 0; ok && ch < nchunks; ++ch, ++dc) {
-        const bool first = ch == 0, final = ch == nchunks - 1;
-        if (!(ok = mbar_wait(accfull, dc & 1, abort_flag, scal, kRoleEpilogue))) break;
+        const uint32_t b = dc & 1u;
+        if (!(ok = mbar_wait(&accfull[b], (dc >> 1) & 1u, abort_flag, scal, kRoleEpilogue))) break;
         tc_fence_after();
-        const uint32_t acc_col = tmem_base + lane_off + colh * 128;
-        const uint32_t run_col = acc_col + 256;
-        // 32-column slices, the accumulator and running-sum loads in flight
-        // together; the accumulator is released as soon as its last slice is
-        // in registers (the MMAs never touch the running sum's columns)
-#pragma unroll 1
-        for (int cb = 0; cb < 4; ++cb) {
-          uint32_t ra[32], rr[32];
-          tmem_ld32_async(acc_col + cb * 32, ra);
-          if (!first) tmem_ld32_async(run_col + cb * 32, rr);
+        const uint32_t acc_col = tmem_base + b * 256u + lane_off + colh * 128;
+#pragma unroll
+        for (int cb = 0; cb < 16; ++cb) {
+          uint32_t ra[8];
+          tmem_ld8_async(acc_col + cb * 8, ra);
           tmem_wait_ld();
-          if (cb == 3) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(accempty_leader);
-          }
-          float a[32];
+          if (ch == 0) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) a[c] = __uint_as_float(ra[c]);
-          if (!first) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) a[c] += __uint_as_float(rr[c]);
-          }
-          if (final && SPARSE) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) piece[(cb * 32 + c) * 256] = a[c] * scale;
-          } else if (final) {
-            if (i < nx) {
-#pragma unroll
-              for (int c = 0; c < 32; ++c) {
-                const int j = j0 + cb * 32 + c;
-                if (j < ny) slot[(int64_t)j * nx + i] = a[c] * scale;
-              }
-            }
+            for (int c = 0; c < 8; ++c) run[cb * 8 + c] = __uint_as_float(ra[c]);
           } else {
-            tmem_st32(run_col + cb * 32, a);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) run[cb * 8 + c] += __uint_as_float(ra[c]);
           }
         }
-        // the running sum's stores complete before this thread's next loads
-        if (!final) tmem_wait_st();
+        // the accumulator is read: the MMAs of chunk dc + 2 may overwrite it
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(accempty_leader0 + 8u * b);
+      }
+      if (!ok) break;
+      if (SPARSE) {  // the piece's own 256 x 256 partial, [j_local][i_local]
+#pragma unroll
+        for (int c = 0; c < 128; ++c) piece[c * 256] = run[c] * scale;
+      } else if (i < nx) {
+#pragma unroll
+        for (int c = 0; c < 128; ++c)
+          if (j0 + c < ny) slot[(int64_t)(j0 + c) * nx + i] = run[c] * scale;
       }
     }
     if (!ok && lane == 0) propagate_abort();
   } else {
     // ------------------------------------------------------------ producers
-    const int t = threadIdx.x - C::kFirstProducerWarp * 32;
-    const bool isA = t < kRows * C::kPerRow;  // warp-uniform
-    const int tl = isA ? t : t - kRows * C::kPerRow;
-    const int r = tl % kRows;
-    const int chunk0 = (tl / kRows) * (8 / C::kPerRow);  // first 8-point chunk of this thread
+    regs_dec<kRegsProd>();
+    const int t = threadIdx.x - kFirstProducerWarp * 32;
+    const bool isA = t < kRows;  // warp-uniform
+    const int r = t & (kRows - 1);
     const int lo_off = isA ? C::kABytes : C::kBBytes;
-    uint32_t full_leader[C::kStages];
-#pragma unroll
-    for (int s = 0; s < C::kStages; ++s) full_leader[s] = map_to_rank(smem_u32(&full[s]), 0);
     uint32_t g = 0;
     bool ok = true;
-    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
+    // every stage ends with an arrive at its barrier, also after an abort
+    // (then without waiting or storing), so the signalling warp never waits
+    // on a barrier that cannot complete
+    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); it < n_items;
          it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
+      const bool signs = !isA && I.scal->negw != 0;
       float gv;
       if (isA) {
         const int base = itm.tm * 256 + (int)rank * kRows;
@@ -424,61 +485,70 @@ __global__ void __launch_bounds__(PairCfg<SPLIT, SPARSE>::kThreads, 1)
         const float2 v = I.gyt[min(base + r, I.ny - 1)];
         gv = (v.x - c.x) + (v.y - c.y);
       }
+      const float2 ng2 = make_float2(-gv, -gv);
       for (int st = 0; st < itm.nst; ++st, ++g) {
         const uint32_t s = g % C::kStages, ps = g % kPS;
-        if (!(ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer))) break;
-        if (!(ok = mbar_wait(&empty[s], ((g / C::kStages) & 1) ^ 1, abort_flag, scal,
-                             kRoleProducer)))
-          break;
+        if (ok) ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer);
+        if (ok)
+          ok = mbar_wait(&empty[s], ((g / C::kStages) & 1) ^ 1, abort_flag, scal, kRoleProducer);
+        if (!ok) {
+          named_arrive(kBarProducers + (int)s, 32 * (kProducerWarps + 1));
+          continue;
+        }
         unsigned char* hi_row =
             smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
-        const float4* crd = reinterpret_cast<const float4*>(params + ps * 3 * kKS + (isA ? 0 : kKS));
-        const float4* cbv = reinterpret_cast<const float4*>(params + ps * 3 * kKS + 2 * kKS);
+        const float* prm = params + ps * kPrmFloats;
+        const float4* crd = reinterpret_cast<const float4*>(prm + (isA ? kPrmA : kPrmB));
+        const float4* nce = reinterpret_cast<const float4*>(prm + kPrmN);
+        const uint4* sgn = reinterpret_cast<const uint4*>(prm + kPrmS);
 #pragma unroll
-        for (int c = chunk0; c < chunk0 + 8 / C::kPerRow; ++c) {
+        for (int c = 0; c < 8; ++c) {
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
-          float4 c0 = make_float4(15.f, 15.f, 15.f, 15.f), c1 = c0;
+          float4 n0 = make_float4(-15.f, -15.f, -15.f, -15.f), n1 = n0;
           if (!isA) {
-            c0 = cbv[2 * c];
-            c1 = cbv[2 * c + 1];
+            n0 = nce[2 * c];
+            n1 = nce[2 * c + 1];
           }
-          const float pc[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-          const float ce[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-          float v[8];
-#pragma unroll
-          for (int e2 = 0; e2 < 8; ++e2) {
-            const float u = gv - pc[e2];
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
-          }
-          const int off = (c ^ (r & 7)) << 4;
+          const float2 P2[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w),
+                                make_float2(p1.x, p1.y), make_float2(p1.z, p1.w)};
+          const float2 N2[4] = {make_float2(n0.x, n0.y), make_float2(n0.z, n0.w),
+                                make_float2(n1.x, n1.y), make_float2(n1.z, n1.w)};
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int e2 = 0; e2 < 4; ++e2) {
+            const float2 u = add2(P2[e2], ng2);     // point - cell, in units of h sqrt(2 ln 2)
+            const float2 y = fma2(u, u, N2[e2]);    // u^2 - exponent offset
+            const float v0 = ex2_neg(y.x), v1 = ex2_neg(y.y);
             if (SPLIT) {
-              const float h0 = __uint_as_float(__float_as_uint(v[2 * e2]) & 0xFFFFE000u);
-              const float h1 = __uint_as_float(__float_as_uint(v[2 * e2 + 1]) & 0xFFFFE000u);
+              // hi = v with 11 significant bits (exact in FP16), lo = v - hi
+              const float h0 = __uint_as_float(__float_as_uint(v0) & 0xFFFFE000u);
+              const float h1 = __uint_as_float(__float_as_uint(v1) & 0xFFFFE000u);
+              const float2 l = sub2(make_float2(v0, v1), make_float2(h0, h1));
               const __half2 hh = __floats2half2_rn(h0, h1);
-              const __half2 ll = __floats2half2_rn(v[2 * e2] - h0, v[2 * e2 + 1] - h1);
+              const __half2 ll = __floats2half2_rn(l.x, l.y);
               hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
               lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
             } else {
-              const __half2 hh = __floats2half2_rn(v[2 * e2], v[2 * e2 + 1]);
+              const __half2 hh = __floats2half2_rn(v0, v1);
               hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
             }
           }
+          if (signs) {  // negative weights: flip the FP16 sign bits of those points
+            const uint4 sg = sgn[c];
+            hw[0] ^= sg.x; hw[1] ^= sg.y; hw[2] ^= sg.z; hw[3] ^= sg.w;
+            if (SPLIT) {
+              lw[0] ^= sg.x; lw[1] ^= sg.y; lw[2] ^= sg.z; lw[3] ^= sg.w;
+            }
+          }
+          const int off = (c ^ (r & 7)) << 4;
           *reinterpret_cast<uint4*>(hi_row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           if (SPLIT)
             *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        // each writer orders its stores to this CTA's shared memory before
-        // the tensor core's (async-proxy) reads of it, then the warp signals
-        // the leader's stage barrier once
+        // order this thread's stores before the tensor core's reads of them,
+        // then hand the stage to the signalling warp without waiting
         fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive_cluster(full_leader[s]);
-          mbar_arrive(&pempty[ps]);
-        }
+        named_arrive(kBarProducers + (int)s, 32 * (kProducerWarps + 1));
       }
     }
     if (!ok && lane == 0) propagate_abort();
@@ -498,14 +568,20 @@ template <bool SPLIT, bool SPARSE>
 cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
                         const SparseCtl& sp, CallScalars* err, cudaStream_t s) {
   using C = PairCfg<SPLIT, SPARSE>;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_pair<SPLIT, SPARSE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  // setmaxnreg draws on the registers the block was launched with: refuse a
+  // build whose launch register count would not hold the warpgroups' budgets
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_tc_pair<SPLIT, SPARSE>);
+  if (e != cudaSuccess) return e;
+  if ((fa.numRegs + 7) / 8 * 8 < kRegsLaunch) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(k_tc_pair<SPLIT, SPARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           C::kSmemBytes);
   if (e != cudaSuccess) return e;
   // the sparse work list's length is known only on the device
   const int clusters = SPARSE ? std::max(1, p.ctas / 2) : std::max(1, std::min(n_items, p.ctas / 2));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * clusters);
-  cfg.blockDim = dim3(C::kThreads);
+  cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = C::kSmemBytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

@@ -109,3 +109,33 @@ def test_mercator_rejects_bad_arguments(lib):
     assert lib.kde_project_mercator(None, -1, 0.0, None, None) == kde.KDE_EINVAL
     assert lib.kde_project_mercator(8, 1, 95.0, 8, None) == kde.KDE_EINVAL
     assert lib.kde_project_mercator(None, 0, 30.0, None, None) == kde.KDE_OK
+
+
+def _noalloc(lib, n, kernel_id=6, nx=4, ny=4):
+    org = (ctypes.c_double * 2)(0.0, 0.0)
+    # fake, aligned non-null addresses: the call must refuse before it touches them
+    return lib.kde_grid_noalloc(4096, None, n, ctypes.byref(org), 1.0, nx, ny, 1.0, kernel_id,
+                                4096, None)
+
+
+@pytest.mark.parametrize("n", [2 ** 62, 2 ** 60 + 1, (8 << 20) // 20 + 1])
+def test_noalloc_rejects_point_counts_beyond_its_scratch_on_host(lib, n):
+    # 2^62 points: 16 n and 4 n are 0 modulo 2^64, so a size computed before the
+    # count is bounded would wrap around to a small number and pass
+    assert _noalloc(lib, n) == kde.KDE_EINVAL
+    assert "static maximum" in lib.kde_last_error().decode()
+
+
+def test_noalloc_rejects_a_grid_that_leaves_no_room_on_host(lib):
+    assert _noalloc(lib, 1000, nx=1 << 20, ny=1) == kde.KDE_EINVAL
+    assert "static maximum" in lib.kde_last_error().decode()
+
+
+def test_noalloc_kernel_ids_on_host(lib):
+    # the radial Gaussian (14) is the product Gaussian and passes the kernel
+    # check (the oversized count stops it next); radial compact kernels do not
+    assert _noalloc(lib, 2 ** 62, kernel_id=14) == kde.KDE_EINVAL
+    assert "static maximum" in lib.kde_last_error().decode()
+    for kid in (10, 15, 16, -1):
+        assert _noalloc(lib, 10, kernel_id=kid) == kde.KDE_EINVAL
+        assert "kernel_id" in lib.kde_last_error().decode()

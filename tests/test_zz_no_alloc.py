@@ -53,6 +53,25 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row(lib):
         assert rel_linf(got, ref.cpu().numpy()) <= TOL_FP32
 
 
+def test_noalloc_takes_no_device_memory(lib):
+    # after one call (which loads the kernels and looks up the scratch), further
+    # calls leave the device's free memory exactly as it was
+    wl = workloads.config1()
+    out = torch.empty((wl.ny, wl.nx), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    pts, w = _noalloc(lib, wl, oracle.GAUSSIAN, out, stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for kernel in (oracle.GAUSSIAN, 14):  # 14: the radial Gaussian, the same density
+        org = (ctypes.c_double * 2)(*wl.origin)
+        rc = lib.kde_grid_noalloc(pts.data_ptr(), w.data_ptr(), wl.n, ctypes.byref(org), wl.cell,
+                                  wl.nx, wl.ny, wl.h, kernel, out.data_ptr(), stream.cuda_stream)
+        assert rc == kde.KDE_OK, lib.kde_last_error().decode()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_rejects_inputs_beyond_its_scratch(lib):
     wl = workloads.random_points(801, 1_000_000, 5000.0, 10.0, 64, 64, 30.0, oracle.GAUSSIAN)
     out = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
