@@ -600,19 +600,34 @@ def batched_leg(dev, peaks, sms, local):
     outs = [torch.empty((x.ny, x.nx), device=dev) for x in inst]
     for d, o in zip(insts, outs):
         d["out"] = o
-    ms = _time(lambda: kde.grid_batched(insts), reps=2)
+    from paper_2004_13653_gb300 import autotune
+    ms_default = _time(lambda: kde.grid_batched(insts), reps=2)
+    # tiles per instance class from the autotuner (timed here on first use,
+    # then cached), one persistent launch per tile family
+    import tempfile
+    t0 = time.perf_counter()
+    tilings = autotune.tune_batch(insts, cache_path=os.path.join(tempfile.gettempdir(),
+                                                                 "kde_bench_autotune.json"))
+    tune_s = time.perf_counter() - t0
+    ms = _time(lambda: kde.grid_batched(insts, tilings=tilings), reps=2)
     g = torch.cuda.CUDAGraph()
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(st):
         with torch.cuda.graph(g, stream=st):
-            kde.grid_batched(insts, stream=st)
+            kde.grid_batched(insts, stream=st, tilings=tilings)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     gms = _time(g.replay, reps=3)
     clk = clocks.stop()
+    chosen = {}
+    for t in tilings:
+        if t is not None:
+            k = ("pair" if t["flags"] == autotune.PAIR else "one-cta") + \
+                f" {256 if t['flags'] == autotune.PAIR else 128}x{t['tile_n']} s{t['stage_points']}"
+            chosen[k] = chosen.get(k, 0) + 1
     # parity: the largest instances of each kernel, 64 sampled cells each
     errs = {}
     for kid, name in ((6, "gaussian"), (2, "epanechnikov")):
@@ -641,6 +656,8 @@ def batched_leg(dev, peaks, sms, local):
     torch.cuda.empty_cache()
     return {"instances": len(inst), "points": int(sum(x.n for x in inst)), "ms": ms,
             "graph_replay_ms": gms, "value": pairs / gms / 1e6, "unit": UNIT,
+            "autotuned": {"tilings": chosen, "tuning_s": tune_s,
+                          "ms_with_default_tiles": ms_default},
             "kernels": {"gaussian": sum(x.kernel == 6 for x in inst),
                         "epanechnikov": sum(x.kernel == 2 for x in inst)},
             "roofline": {"bound": "tensor+alu", "roofline_ms": t_roof * 1e3,

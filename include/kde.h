@@ -236,8 +236,15 @@ int kde_grid_batched_tiled(const kde_args* inst, const kde_tiling* tiles, int co
  *   dL/dx_p = c w_p sum_ij G_ij (gx_i - x_p)/h^2 A_ip B_jp (same for y),
  *   dL/dh   = -(2/h) sum_ij G_ij F_ij + c sum_p w_p sum_ij G_ij r^2/h^3 A B,
  * c = 1/(2 pi N h^2), A, B the 1-D Gaussian factors, recomputed on the fly.
+ * Two forms: a window kernel that sums each point's +-8h window on the FP32
+ * pipes (opts->path KDE_PATH_SIMT_FP32), and, for wide bandwidths, two
+ * tcgen05 contractions U = G B and V = G^T A (split-FP16, three products;
+ * KDE_PATH_TC_SPLIT16 or KDE_PATH_TC_FP16) whose epilogues fold U and V
+ * into the per-point sums.  KDE_PATH_AUTO takes the contractions when the
+ * window covers more than 2% of the grid padded to 256-cell tiles.
  * Requires a->points on the device and kernel_id == KDE_GAUSSIAN.  dL/dh
- * makes the call synchronous.
+ * makes the call synchronous (and reports KDE_ETIMEOUT from the
+ * contractions' bounded waits).
  */
 int kde_grid_backward(const kde_args* a, const float* grad_out,
                       float* grad_points, float* grad_weights, double* grad_h,
@@ -251,8 +258,8 @@ int kde_grid_backward(const kde_args* a, const float* grad_out,
  * F_p = w_p K(|g - x_p|/h)/(N h^2) point p's own term at the cell centres g
  * (K(u) = exp(-u^2/2)/(2 pi)), bilerp = bilinear interpolation between cell
  * centres with zero outside the grid; bilerp(F - F_p, x_p) is the
- * leave-one-out density at x_p interpolated from the grid.  F: device [ny*nx] (as computed by
- * kde_grid_ex for the same arguments).  Writes the loss to *loss (host),
+ * leave-one-out density at x_p interpolated from the grid.  F: device
+ * [ny*nx] (as computed by kde_grid_ex for the same arguments).  Writes the loss to *loss (host),
  * dL/dF to grad_F (device [ny*nx], FP32), and the loss's direct partial
  * derivatives w.r.t. w_p and x_p (not through F) to grad_w_direct (device
  * [n]) and grad_points_direct (device [2n]); either may be NULL.  The

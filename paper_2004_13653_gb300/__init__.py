@@ -298,8 +298,9 @@ def grid_batched(instances, path="auto", flags=0, stream=None, tilings=None, **t
 
 
 def grid_backward(points, weights, origin, cell, nx, ny, h, grad_out, stream=None,
-                  want_h=True):
-    """kde_grid_backward (Gaussian): (dL/dpoints [n,2] f32, dL/dw [n] f32, dL/dh)."""
+                  want_h=True, path="auto"):
+    """kde_grid_backward (Gaussian): (dL/dpoints [n,2] f32, dL/dw [n] f32, dL/dh).
+    path: "auto", "simt" (the window kernel) or "tc_split16" (the contractions)."""
     import torch
     n = _count(points) // 2
     gxy = torch.empty((n, 2), dtype=torch.float32, device=points.device)
@@ -308,7 +309,7 @@ def grid_backward(points, weights, origin, cell, nx, ny, h, grad_out, stream=Non
     if stream is None:
         stream = _current_stream(points.device)
     a = make_args(points, weights, origin, cell, nx, ny, h, "gaussian", grad_out)
-    o = make_opts("auto", 0, stream)
+    o = make_opts(path, 0, stream)
     check(load().kde_grid_backward(ctypes.byref(a), _ptr(grad_out.contiguous()), _ptr(gxy),
                                    _ptr(gw), ctypes.byref(gh) if want_h else None,
                                    ctypes.byref(o)))

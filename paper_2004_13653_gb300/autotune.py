@@ -1,12 +1,16 @@
-"""Autotuner for the tensor-core tiling: tile width, accumulator chunk and
-pipeline stage, chosen per workload class by timing the candidates with CUDA
-events and cached as JSON.
+"""Autotuner for the tensor-core tiling: tile shape (256 x 256 on CTA pairs,
+128 x 256 or 128 x 128 on one CTA), pipeline stage and accumulator chunk,
+chosen per workload class by timing the candidates with CUDA events and cached
+as JSON.  tune_batch() gives every Gaussian instance of a batch its class's
+tiling, which kde_grid_batched_tiled turns into one persistent launch per tile
+family.
 
 A class is (path, kernel, log2 of the grid sides, log2 of the point count,
 bandwidth in cells rounded to a power of two).  Only candidates that keep the
 path within its accuracy budget are tried: split-FP16 drains its FP32
-accumulator at least every 512 points (the tensor core's accumulation error
-grows with each MMA step added into a large sum).
+accumulator every 256 points (the tensor core's accumulation error grows with
+each MMA step added into a large sum; 512-point chunks reached the 1e-5
+tolerance on a dense batched instance).
 """
 from __future__ import annotations
 
@@ -17,11 +21,16 @@ import threading
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "kde_gb300_autotune.json")
 
+PAIR, ONE_CTA = 4, 8  # KDE_FLAG_CTA_PAIR, KDE_FLAG_ONE_CTA
+
+# the first candidate of each list is the library's own default for large grids
 CANDIDATES = {
-    "tc_split16": [dict(tile_n=t, k_chunk=c, stage_points=s)
-                   for t in (256, 128) for c in (256, 512) for s in (64, 32)],
-    "tc_fp16": [dict(tile_n=t, k_chunk=c, stage_points=s)
-                for t in (256, 128) for c in (512, 1024, 2048) for s in (64,)],
+    "tc_split16": [dict(flags=PAIR, tile_n=256, stage_points=64, k_chunk=256)] +
+                  [dict(flags=ONE_CTA, tile_n=t, stage_points=s, k_chunk=256)
+                   for t in (256, 128) for s in (64, 32)],
+    "tc_fp16": [dict(flags=PAIR, tile_n=256, stage_points=64, k_chunk=1024)] +
+               [dict(flags=ONE_CTA, tile_n=t, stage_points=64, k_chunk=c)
+                for t in (256, 128) for c in (1024, 2048)],
 }
 
 _lock = threading.Lock()
@@ -107,3 +116,24 @@ def tune(points, weights, origin, cell, nx, ny, h, path="tc_split16", cache_path
                       "tried": [[o, t] for o, t in timings]}
         save_cache(cache, cache_path)
     return dict(best_opts)
+
+
+def tune_batch(instances, path="tc_split16", cache_path=DEFAULT_CACHE, retune=False, timer=None):
+    """One tiling per instance of a batch (dicts as kde.grid_batched's
+    `tilings`): each Gaussian instance gets the tiling tuned for its class
+    (timed once per class, on the first instance of that class, then cached);
+    other instances get None."""
+    out, seen = [], {}
+    for d in instances:
+        kern = d.get("kernel", "gaussian")
+        if kern not in ("gaussian", 6, "radial_gaussian", 14):
+            out.append(None)
+            continue
+        n = int(d["points"].shape[0])
+        key = class_key(path, "gaussian", d["nx"], d["ny"], n, d["h"], d["cell"])
+        if key not in seen:
+            seen[key] = tune(d["points"], d.get("weights"), d["origin"], d["cell"], d["nx"],
+                             d["ny"], d["h"], path=path, cache_path=cache_path, retune=retune,
+                             timer=timer)
+        out.append(dict(seen[key]))
+    return out

@@ -221,6 +221,10 @@ struct InstPlan {
 // the FP32 rounding of the offsets and of ex2.approx.
 constexpr double kSparseReach = 6.45;
 
+// The adjoint takes the tensor-core contractions when the window kernel's
+// cells per point exceed this fraction of the (padded) grid.
+constexpr double kAdjointTcRatio = 0.02;
+
 // Tensor-core instances that share a tile shape and pipeline stage: one
 // persistent launch over their work items.
 struct TcFamily {
@@ -228,7 +232,41 @@ struct TcFamily {
   std::vector<int> order;  // instances, most expensive items first
   int items = 0;
   int tab_begin = 0;       // first entry of the family in the TC table
+  // CTA-pair batches: each pair's items (offsets, then item indices), from a
+  // longest-processing-time-first assignment; empty = round robin
+  std::vector<uint32_t> sched;
+  size_t off_sched = 0;
 };
+
+// Longest processing time first: the items, longest first, each to the CTA
+// pair with the least work so far; returns offsets[clusters + 1] followed by
+// the item indices of each pair in the order it takes them.  cost[i] is the
+// item's length in pipeline stages plus a fixed cost for its final drain.
+std::vector<uint32_t> lpt_schedule(const std::vector<int64_t>& cost, int clusters) {
+  const int n = (int)cost.size();
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<uint32_t>> per(clusters);
+  std::vector<std::pair<int64_t, int>> heap;  // (load, pair), smallest load on top
+  for (int c = 0; c < clusters; ++c) heap.push_back({0, c});
+  auto cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+    return a.first != b.first ? a.first > b.first : a.second > b.second;
+  };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  for (int i : idx) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    auto& top = heap.back();
+    per[top.second].push_back((uint32_t)i);
+    top.first += cost[i];
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  std::vector<uint32_t> t(clusters + 1);
+  t[0] = 0;
+  for (int c = 0; c < clusters; ++c) t[c + 1] = t[c] + (uint32_t)per[c].size();
+  for (int c = 0; c < clusters; ++c) t.insert(t.end(), per[c].begin(), per[c].end());
+  return t;
+}
 
 struct BatchPlan {
   int count;
@@ -504,6 +542,26 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
   if (P->cut_m >= ((int64_t)1 << 32)) return fail(KDE_EINVAL, "too many points to sort in one batch");
   for (int k : P->tc_order) P->tc_items += P->in[k].items;
   if ((int64_t)P->tc_items > 0x7fffffff) return fail(KDE_EINVAL, "too many work items");
+  // batches on CTA pairs: balance the pairs' work with a host-side schedule
+  // (items of different instances differ in length; round robin left the last
+  // pair finishing 7% after the mean on the 256-instance batch)
+  if (count > 1 && !P->sparse) {
+    for (TcFamily& f : P->fam) {
+      if (!f.plan.pair || f.items < 2) continue;
+      std::vector<int64_t> cost;
+      cost.reserve(f.items);
+      for (int k : f.order) {
+        const InstPlan& I = P->in[k];
+        const int64_t per_tile = (int64_t)I.tiles_m * I.tiles_n;
+        for (int local = 0; local < I.items; ++local) {
+          const int64_t s = local / per_tile;
+          const int64_t len = std::min<int64_t>(I.per_split, I.n_pad - s * I.per_split);
+          cost.push_back(std::max<int64_t>(len, 0) / f.plan.stage_points + 4);
+        }
+      }
+      f.sched = lpt_schedule(cost, pair_clusters(f.plan, f.items));
+    }
+  }
   if (P->sparse && P->fam.size() > 1) return fail(KDE_EINVAL, "block-sparse batch with two tilings");
   P->cz = cutoff_sizes(P->cut_m, P->total_bins);
 
@@ -516,6 +574,8 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
   P->off_tab_tc = take(sizeof(TcInst) * (size_t)std::max(P->n_tc, 1));
   P->off_tab_cut = take(sizeof(CutInst) * (size_t)std::max(P->n_cut + (P->sparse ? P->n_tc : 0), 1));
   P->off_tab_red = take(sizeof(ReduceInst) * (size_t)std::max(P->n_reduce, 1));
+  for (TcFamily& f : P->fam)
+    if (!f.sched.empty()) f.off_sched = take(sizeof(uint32_t) * f.sched.size());
   for (int k = 0; k < count; ++k) {
     InstPlan& I = P->in[k];
     I.off_gxt = take(sizeof(float2) * (size_t)A[k].nx);
@@ -802,6 +862,11 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
     KDE_CUDA(launch_upload(cut.data(), sizeof(CutInst) * cut.size(), d_cut, s), "upload tables");
   if (!red.empty())
     KDE_CUDA(launch_upload(red.data(), sizeof(ReduceInst) * red.size(), d_red, s), "upload tables");
+  for (const TcFamily& f : P.fam)
+    if (!f.sched.empty())
+      KDE_CUDA(launch_upload(f.sched.data(), sizeof(uint32_t) * f.sched.size(), base + f.off_sched,
+                             s),
+               "upload schedule");
 
   // ---- launches
   KDE_CUDA(launch_prepare(d_prep, count, P.total_pad, P.max_side, s), "prepare points");
@@ -861,16 +926,18 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
                                 reinterpret_cast<uint32_t*>(base + P.off_sp_nf),
                                 reinterpret_cast<uint32_t*>(base + P.off_sp_temp), batch_scal, s),
              "block-sparse work list");
-    KDE_CUDA(launch_tc_pair(P.fam[0].plan, d_tc, P.n_tc, 0, &sp, batch_scal, s),
+    KDE_CUDA(launch_tc_pair(P.fam[0].plan, d_tc, P.n_tc, 0, &sp, nullptr, batch_scal, s),
              "block-sparse tensor-core contraction");
     KDE_CUDA(launch_sparse_reduce(d_tc, P.n_tc, sp, s), "block-sparse reduce");
   } else if (P.n_tc) {
     for (const TcFamily& f : P.fam) {  // one persistent launch per tile family
       if (f.items < 1) continue;
       const int nf = (int)f.order.size();
-      KDE_CUDA(f.plan.pair
-                   ? launch_tc_pair(f.plan, d_tc + f.tab_begin, nf, f.items, nullptr, batch_scal, s)
-                   : launch_tc(f.plan, d_tc + f.tab_begin, nf, f.items, batch_scal, s),
+      const uint32_t* sched =
+          f.sched.empty() ? nullptr : reinterpret_cast<const uint32_t*>(base + f.off_sched);
+      KDE_CUDA(f.plan.pair ? launch_tc_pair(f.plan, d_tc + f.tab_begin, nf, f.items, nullptr, sched,
+                                            batch_scal, s)
+                           : launch_tc(f.plan, d_tc + f.tab_begin, nf, f.items, batch_scal, s),
                "tensor-core contraction");
     }
   }
@@ -1030,6 +1097,17 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
     return KDE_OK;
   }
   const int64_t n_pad = (a->n + 511) / 512 * 512;
+  // Window kernel or the two tensor-core contractions: the window sums about
+  // (16 h / cell)^2 cells per point on the FP32 pipes, the contractions
+  // nx ny cells per point (twice, three FP16 products) on the tensor cores.
+  const int path = opts ? opts->path : KDE_PATH_AUTO;
+  bool use_tc = path == KDE_PATH_TC_SPLIT16 || path == KDE_PATH_TC_FP16;
+  if (path == KDE_PATH_AUTO) {
+    const double R = std::ceil(8.0 * a->h / a->cell);
+    const double win = std::min(2.0 * R + 1.0, (double)a->nx) * std::min(2.0 * R + 1.0, (double)a->ny);
+    const double nxp = std::ceil(a->nx / 256.0) * 256.0, nyp = std::ceil(a->ny / 256.0) * 256.0;
+    use_tc = win > kAdjointTcRatio * nxp * nyp;
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
   const size_t o_scal = take(sizeof(CallScalars));
@@ -1042,6 +1120,7 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
   const size_t o_lt = take(sizeof(double) * a->n);
   const size_t o_part = take(sizeof(double) * 2 * sum_partials(a->n));
   const size_t o_res = take(sizeof(double) * 2);
+  const size_t o_tc = take(use_tc ? adjoint_tc_workspace(a->nx, a->ny) : 0);
   void* wsv = nullptr;
   rc = acquire_workspace(opts, off, s, &wsv);
   if (rc) return rc;
@@ -1059,8 +1138,9 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
   q.begin = 0;
   q.ox = a->origin_x;
   q.oy = a->origin_y;
-  q.sigma = 1.0 / a->h;  // offsets in bandwidths
-  q.cell_sigma = a->cell / a->h;
+  // offsets in bandwidths (window kernel) or in h sqrt(2 ln 2) (contractions)
+  q.sigma = use_tc ? kernel_sigma(KDE_GAUSSIAN, a->h) : 1.0 / a->h;
+  q.cell_sigma = a->cell * q.sigma;
   q.nx = a->nx;
   q.ny = a->ny;
   double* ht = reinterpret_cast<double*>(base + o_ht);
@@ -1072,9 +1152,18 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
   KDE_CUDA(launch_prepare(reinterpret_cast<PrepInst*>(base + o_tab), 1, n_pad,
                           std::max(a->nx, a->ny), s),
            "prepare points");
-  KDE_CUDA(launch_adjoint_gauss(q.pts, q.wts, a->n, grad_out, q.gxt, q.gyt, a->nx, a->ny, a->cell,
-                                a->h, grad_points, grad_weights, ht, lt, s),
-           "adjoint");
+  if (use_tc) {
+    const int sms = sm_count();
+    const int ctas = (opts && opts->max_ctas > 0) ? std::min(opts->max_ctas, sms) : sms;
+    KDE_CUDA(launch_adjoint_gauss_tc(q.pts, q.wts, a->n, grad_out, q.gxt, q.gyt, a->nx, a->ny,
+                                     a->cell, a->h, grad_points, grad_weights, ht, lt,
+                                     base + o_tc, ctas, s),
+             "adjoint contractions");
+  } else {
+    KDE_CUDA(launch_adjoint_gauss(q.pts, q.wts, a->n, grad_out, q.gxt, q.gyt, a->nx, a->ny,
+                                  a->cell, a->h, grad_points, grad_weights, ht, lt, s),
+             "adjoint");
+  }
   const bool sync = grad_h || (opts && (opts->flags & KDE_FLAG_SYNC));
   if (grad_h) {
     const size_t np = sum_partials(a->n);
@@ -1083,13 +1172,22 @@ int kde_grid_backward(const kde_args* a, const float* grad_out, float* grad_poin
   }
   if (sync) {
     double hres[2] = {0.0, 0.0};
-    int err = 0;
+    int err = 0, err_tc = 0, where = 0;
     if (grad_h)
       KDE_CUDA(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s), "read result");
     KDE_CUDA(cudaMemcpyAsync(&err, &q.scal->err, sizeof(int), cudaMemcpyDeviceToHost, s),
              "read status");
+    if (use_tc) {
+      const CallScalars* ts = reinterpret_cast<const CallScalars*>(base + o_tc);
+      KDE_CUDA(cudaMemcpyAsync(&err_tc, &ts->err, sizeof(int), cudaMemcpyDeviceToHost, s),
+               "read status");
+      KDE_CUDA(cudaMemcpyAsync(&where, &ts->timeout_where, sizeof(int), cudaMemcpyDeviceToHost, s),
+               "read status");
+    }
     KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
     if (err & kErrNonFinite) return fail(KDE_EDATA, "non-finite coordinate or weight");
+    if (err_tc & kErrTimeout)
+      return fail(KDE_ETIMEOUT, "a device-side wait of the adjoint gave up (role %d)", where);
     // dL/dh = -(2/h) sum G F + sum_p h-terms, with sum G F = sum_p w_p dL/dw_p
     if (grad_h) *grad_h = -2.0 / a->h * hres[1] + hres[0];
   }

@@ -335,6 +335,17 @@ cudaError_t launch_adjoint_gauss(const float4* pts, const float* wts, int64_t n,
                                  const float2* gxt, const float2* gyt, int nx, int ny,
                                  double cell, double h, float* grad_xy, float* grad_w,
                                  double* hterm, double* lterm, cudaStream_t s);
+// The same adjoint as two tcgen05 contractions (points prepared in the
+// Gaussian's units, sigma = 1/(h sqrt(2 ln 2)), and their cell tables):
+// U = G B and V = G^T A with the points' operands generated on chip.  ws:
+// adjoint_tc_workspace(nx, ny) bytes (the cotangent's FP16 tiles and a status
+// word); errors of its waits are recorded in ws's CallScalars.
+size_t adjoint_tc_workspace(int nx, int ny);
+cudaError_t launch_adjoint_gauss_tc(const float4* pts, const float* wts, int64_t n, const float* G,
+                                    const float2* gxt, const float2* gyt, int nx, int ny,
+                                    double cell, double h, float* grad_xy, float* grad_w,
+                                    double* hterm, double* lterm, void* ws, int max_ctas,
+                                    cudaStream_t s);
 // Gd: FP64 scratch for the cotangent (cells), G: FP32 cotangent out; loo and
 // hdir: per-point leave-one-out terms and direct dL/dh terms (sum hdir * 2/N).
 cudaError_t launch_lscv(const float4* pts, const float* wts, int64_t n, const float* F, int nx,
@@ -381,9 +392,13 @@ cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_it
                       CallScalars* err, cudaStream_t s);
 // The same on CTA pairs (tiles_m / tiles_n of the table count 256-cell tiles).
 // With sp != nullptr the work items are the pieces of the block-sparse work
-// list (their count is read on the device).
+// list (their count is read on the device).  sched (device, or nullptr for
+// round robin): the items of each of the pair_clusters() CTA pairs, as
+// offsets[clusters + 1] followed by the item indices.
+int pair_clusters(const TcPlan& plan, int n_items);
 cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
-                           const SparseCtl* sp, CallScalars* err, cudaStream_t s);
+                           const SparseCtl* sp, const uint32_t* sched, CallScalars* err,
+                           cudaStream_t s);
 // Block-sparse work list: tile totals, pieces and full pieces per tile and
 // their exclusive scans, the tail pieces ordered longest first.  npieces and
 // nfull are [tiles_total + 1] scratch words.

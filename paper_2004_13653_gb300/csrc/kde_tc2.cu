@@ -188,7 +188,8 @@ __device__ __forceinline__ int sched_pos(int r, int c, int nc) {
 template <bool SPLIT, bool SPARSE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_pair(const TcInst* __restrict__ tab, int ninst, int n_items_arg,
-              const __grid_constant__ SparseCtl sp, CallScalars* __restrict__ scal) {
+              const __grid_constant__ SparseCtl sp, const uint32_t* __restrict__ sched,
+              CallScalars* __restrict__ scal) {
   using C = PairCfg<SPLIT, SPARSE>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -218,6 +219,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
   auto propagate_abort = [&]() {
     store_cluster_u32(map_to_rank(smem_u32((const void*)abort_flag), peer), 1u);
+  };
+  // The item at position k of this CTA pair's list, -1 past its end: from the
+  // host's schedule table when there is one (offsets[n_clusters + 1], then
+  // the items), else round robin (snake order for block-sparse pieces).
+  // Every role of both CTAs walks the same list.
+  auto item_at = [&](int k) -> int {
+    if (sched) {
+      const uint32_t a = __ldg(sched + cluster), b = __ldg(sched + cluster + 1);
+      return a + (uint32_t)k < b ? (int)__ldg(sched + n_clusters + 1 + a + k) : -1;
+    }
+    const int it = sched_pos<SPARSE>(k, cluster, n_clusters);
+    return it < n_items ? it : -1;
   };
 
   if (threadIdx.x == 0) {
@@ -252,8 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t g = 0, mc = 0;
         bool ok = true;
         const uint32_t smem_base = smem_u32(smem);
-        for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
-             it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+        for (int rd = 0, it = item_at(0); ok && it >= 0; it = item_at(++rd)) {
           const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
           const int CS = itm.I->chunk_stages;
           uint32_t acc_addr = tmem_base;
@@ -302,8 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ------------------------------------------------------- point loader
       uint32_t g = 0;
       bool ok = true;
-      for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
-           it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+      for (int rd = 0, it = item_at(0); ok && it >= 0; it = item_at(++rd)) {
         const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
         const TcInst& I = *itm.I;
         const float wmax = __uint_as_float(I.scal->wmax_bits);
@@ -376,8 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // producers arrive at every stage's barrier whatever happens.
       const uint32_t full_leader0 = map_to_rank(smem_u32(&full[0]), 0);
       uint32_t g = 0;
-      for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); it < n_items;
-           it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+      for (int rd = 0, it = item_at(0); it >= 0; it = item_at(++rd)) {
         const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
         for (int st = 0; st < itm.nst; ++st, ++g) {
           const uint32_t s = g % C::kStages;
@@ -400,8 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t accempty_leader0 = map_to_rank(smem_u32(&accempty[0]), 0);
     uint32_t dc = 0;
     bool ok = true;
-    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); ok && it < n_items;
-         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+    for (int rd = 0, it = item_at(0); ok && it >= 0; it = item_at(++rd)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const int nx = I.nx, ny = I.ny, CS = I.chunk_stages;
@@ -468,8 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // every stage ends with an arrive at its barrier, also after an abort
     // (then without waiting or storing), so the signalling warp never waits
     // on a barrier that cannot complete
-    for (int rd = 0, it = sched_pos<SPARSE>(0, cluster, n_clusters); it < n_items;
-         it = sched_pos<SPARSE>(++rd, cluster, n_clusters)) {
+    for (int rd = 0, it = item_at(0); it >= 0; it = item_at(++rd)) {
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const bool signs = !isA && I.scal->negw != 0;
@@ -564,9 +572,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+}  // namespace
+
+int pair_clusters(const TcPlan& plan, int n_items);
+
+namespace {
+
 template <bool SPLIT, bool SPARSE>
 cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_items,
-                        const SparseCtl& sp, CallScalars* err, cudaStream_t s) {
+                        const SparseCtl& sp, const uint32_t* sched, CallScalars* err,
+                        cudaStream_t s) {
   using C = PairCfg<SPLIT, SPARSE>;
   // setmaxnreg draws on the registers the block was launched with: refuse a
   // build whose launch register count would not hold the warpgroups' budgets
@@ -578,7 +593,7 @@ cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_ite
                            C::kSmemBytes);
   if (e != cudaSuccess) return e;
   // the sparse work list's length is known only on the device
-  const int clusters = SPARSE ? std::max(1, p.ctas / 2) : std::max(1, std::min(n_items, p.ctas / 2));
+  const int clusters = SPARSE ? std::max(1, p.ctas / 2) : pair_clusters(p, n_items);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * clusters);
   cfg.blockDim = dim3(kThreads);
@@ -591,7 +606,7 @@ cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_ite
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_tc_pair<SPLIT, SPARSE>, tab, ninst, n_items, sp, err);
+  e = cudaLaunchKernelEx(&cfg, k_tc_pair<SPLIT, SPARSE>, tab, ninst, n_items, sp, sched, err);
   note_launches(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -599,18 +614,23 @@ cudaError_t launch_pair(const TcPlan& p, const TcInst* tab, int ninst, int n_ite
 
 }  // namespace
 
+int pair_clusters(const TcPlan& plan, int n_items) {
+  return std::max(1, std::min(n_items, plan.ctas / 2));
+}
+
 cudaError_t launch_tc_pair(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
-                           const SparseCtl* sp, CallScalars* err, cudaStream_t s) {
+                           const SparseCtl* sp, const uint32_t* sched, CallScalars* err,
+                           cudaStream_t s) {
   if (ninst < 1 || plan.ctas < 2 || plan.stage_points != kKS) return cudaErrorInvalidValue;
   if (sp) {
     if (sp->tiles_total < 1 || sp->piece_len < kKS || sp->piece_len % kKS) return cudaErrorInvalidValue;
-    return plan.split16 ? launch_pair<true, true>(plan, tab, ninst, 0, *sp, err, s)
-                        : launch_pair<false, true>(plan, tab, ninst, 0, *sp, err, s);
+    return plan.split16 ? launch_pair<true, true>(plan, tab, ninst, 0, *sp, nullptr, err, s)
+                        : launch_pair<false, true>(plan, tab, ninst, 0, *sp, nullptr, err, s);
   }
   if (n_items < 1) return cudaErrorInvalidValue;
   const SparseCtl none = {};
-  return plan.split16 ? launch_pair<true, false>(plan, tab, ninst, n_items, none, err, s)
-                      : launch_pair<false, false>(plan, tab, ninst, n_items, none, err, s);
+  return plan.split16 ? launch_pair<true, false>(plan, tab, ninst, n_items, none, sched, err, s)
+                      : launch_pair<false, false>(plan, tab, ninst, n_items, none, sched, err, s);
 }
 
 }  // namespace kde

@@ -146,3 +146,58 @@ def test_fit_bandwidth_decreases_loss_and_resumes(tmp_path):
     assert len(losses_res) == 40
     assert h_res == pytest.approx(h_full, rel=1e-6)
     assert losses_res[-1] == pytest.approx(losses[-1], rel=1e-6)
+
+
+def _rel_per_point(got, ref, floor=0.1):
+    """Largest error relative to each component itself, over the components
+    whose size is at least `floor` of the largest (small-gradient points are
+    checked by the L-inf test, where the largest component normalises)."""
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    big = np.abs(ref) >= floor * np.max(np.abs(ref))
+    return float(np.max(np.abs(got[big] - ref[big]) / np.abs(ref[big])))
+
+
+@pytest.mark.parametrize("path", ["simt", "tc_split16"])
+def test_both_adjoint_forms_match_oracle(path):
+    """The window kernel and the two tensor-core contractions, forced, on the
+    same case: dL/dw, dL/dpoints and dL/dh against the oracle's VJP."""
+    wl, G = _case(seed=905, n=777, nx=300, ny=130)
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                                    _dev(G, torch.float32), path=path)
+    rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, G)
+    assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
+    assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    assert _rel_per_point(gxy.cpu().numpy(), rxy) <= 10 * TOL_GRAD
+    assert gh == pytest.approx(rh, rel=TOL_GRAD)
+
+
+def test_contraction_adjoint_wide_bandwidth_large_grid():
+    """h = 16 cells on a 520 x 540 grid (ragged 256-cell tiles and 64-cell
+    stages), 2001 points partly outside the grid: the contractions (AUTO picks
+    them here) against the oracle's VJP on 300 sampled points, and dL/dh
+    against the oracle on all points."""
+    rng = np.random.default_rng(906)
+    wl = workloads.random_points(906, 2001, 5200.0, 10.0, 520, 540, 160.0, oracle.GAUSSIAN)
+    G = rng.normal(0, 1, (540, 520)) + 0.5 * np.sin(np.arange(520) / 17.0)[None, :]
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, 520, 540, wl.h, _dev(G, torch.float32))
+    sel = np.sort(rng.choice(wl.n, 300, replace=False))
+    rw, rxy, _ = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, 520, 540, wl.h, G,
+                                      pts=sel)
+    got_w, got_xy = gw.cpu().numpy()[sel], gxy.cpu().numpy()[sel]
+    assert rel_linf(got_w, rw) <= TOL_GRAD
+    assert rel_linf(got_xy, rxy) <= TOL_GRAD
+    assert _rel_per_point(got_w, rw) <= 10 * TOL_GRAD
+    _, _, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, 520, 540, wl.h, G)
+    assert gh == pytest.approx(rh, rel=TOL_GRAD)
+
+
+def test_contraction_adjoint_zero_cotangent():
+    wl, _ = _case(seed=907, n=129)
+    G = np.zeros((wl.ny, wl.nx))
+    gxy, gw, gh = kde.grid_backward(_dev(wl.xy, torch.float64), _dev(wl.w, torch.float32),
+                                    wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                                    _dev(G, torch.float32), path="tc_split16")
+    assert not gxy.any() and not gw.any() and gh == 0.0

@@ -123,3 +123,65 @@ def test_config4_batch_sampled():
         ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel,
                                cells)
         assert rel_linf(F.reshape(-1)[cells], ref) <= _tol(wl), (k, wl.kernel, wl.n)
+
+
+_TILINGS = [dict(flags=kde.FLAG_CTA_PAIR, tile_n=256, stage_points=64, k_chunk=256, split_k=2),
+            dict(flags=kde.FLAG_ONE_CTA, tile_n=128, stage_points=64, k_chunk=256, split_k=3),
+            dict(flags=kde.FLAG_ONE_CTA, tile_n=256, stage_points=32, k_chunk=128, split_k=1),
+            dict(flags=kde.FLAG_ONE_CTA, tile_n=128, stage_points=32, k_chunk=96, split_k=2)]
+
+
+def test_tiled_batch_families_match_oracle_and_single_calls():
+    """Per-instance tilings (kde_grid_batched_tiled): the Gaussian instances
+    fall into four tile families, one launch each; every instance matches the
+    oracle and, bit for bit, the same instance run alone with its tiling."""
+    wls = _mixed(seed=660, count=12)
+    insts = [_dev(wl) for wl in wls]
+    tilings = [_TILINGS[k % 4] if wl.kernel == oracle.GAUSSIAN else None
+               for k, wl in enumerate(wls)]
+    outs = kde.grid_batched(insts, flags=kde.FLAG_SYNC, tilings=tilings)
+    for wl, d, F, tl in zip(wls, insts, outs, tilings):
+        F = F.cpu().numpy()
+        ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel)
+        if wl.n == 0 or not ref.any():
+            assert not F.any()
+            continue
+        assert rel_linf(F, ref) <= _tol(wl), (wl.name, wl.kernel, tl)
+        if tl is not None:
+            alone = kde.grid(d["points"], d["weights"], wl.origin, wl.cell, wl.nx, wl.ny, wl.h,
+                             wl.kernel, path="tc_split16", flags=kde.FLAG_SYNC | tl["flags"],
+                             tile_n=tl["tile_n"], stage_points=tl["stage_points"],
+                             k_chunk=tl["k_chunk"], split_k=tl["split_k"]).cpu().numpy()
+            assert np.array_equal(F, alone), (wl.name, tl)
+
+
+def test_autotuned_batch_replays_in_a_graph(tmp_path):
+    """The autotuner's per-class tilings feed the batch; the tiled call is
+    captured in a CUDA graph and its replay matches the eager call and the
+    oracle."""
+    from paper_2004_13653_gb300 import autotune
+    wls = _mixed(seed=670, count=8)
+    insts = [_dev(wl) for wl in wls]
+    tilings = autotune.tune_batch(insts, cache_path=str(tmp_path / "tune.json"))
+    assert all((t is None) == (wl.kernel != oracle.GAUSSIAN) for t, wl in zip(tilings, wls))
+    outs = [torch.full((wl.ny, wl.nx), -1.0, device="cuda") for wl in wls]
+    for d, o in zip(insts, outs):
+        d["out"] = o
+    kde.grid_batched(insts, flags=kde.FLAG_SYNC, tilings=tilings)
+    eager = [o.clone() for o in outs]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            kde.grid_batched(insts, stream=s, tilings=tilings)
+    torch.cuda.synchronize()
+    for o in outs:
+        o.fill_(-1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for wl, a, b in zip(wls, eager, outs):
+        assert torch.equal(a, b)
+        ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel)
+        if ref.any():
+            assert rel_linf(b.cpu().numpy(), ref) <= _tol(wl)

@@ -125,8 +125,10 @@ def test_autotuned_tiling_is_valid_and_accurate(tmp_path):
     assert opts in autotune.CANDIDATES["tc_split16"]
     assert autotune.tune(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "tc_split16",
                          cache_path=cache) == opts  # served from the cache
+    tiling = dict(opts)
+    flags = kde.FLAG_SYNC | tiling.pop("flags")
     F = kde.grid(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, "gaussian", path="tc_split16",
-                 flags=kde.FLAG_SYNC, **opts).cpu().numpy()
+                 flags=flags, **tiling).cpu().numpy()
     cells = sample_cells(F, 128, seed=13)
     ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN,
                            cells)
