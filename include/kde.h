@@ -241,7 +241,7 @@ int kde_grid_batched_tiled(const kde_args* inst, const kde_tiling* tiles, int co
  * tcgen05 contractions U = G B and V = G^T A (split-FP16, three products;
  * KDE_PATH_TC_SPLIT16 or KDE_PATH_TC_FP16) whose epilogues fold U and V
  * into the per-point sums.  KDE_PATH_AUTO takes the contractions when the
- * window covers more than 2% of the grid padded to 256-cell tiles.
+ * window covers more than 0.6% of the grid padded to 256-cell tiles.
  * Requires a->points on the device and kernel_id == KDE_GAUSSIAN.  dL/dh
  * makes the call synchronous (and reports KDE_ETIMEOUT from the
  * contractions' bounded waits).

@@ -222,8 +222,11 @@ struct InstPlan {
 constexpr double kSparseReach = 6.45;
 
 // The adjoint takes the tensor-core contractions when the window kernel's
-// cells per point exceed this fraction of the (padded) grid.
-constexpr double kAdjointTcRatio = 0.02;
+// cells per point exceed this fraction of the grid padded to 256-cell tiles
+// (measured on 1M points x 1024^2: the contractions take 6.2 ms at every h,
+// the window 5.7 ms at h = 5.1 cells and 26 ms at h = 8.2 cells, about 1 ns
+// per window cell and point).
+constexpr double kAdjointTcRatio = 0.006;
 
 // Tensor-core instances that share a tile shape and pipeline stage: one
 // persistent launch over their work items.
