@@ -145,6 +145,13 @@ def parse():
                     help="grid side for the FP32 SIMT comparison (same points; 0 = skip)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batch leg")
     ap.add_argument("--no-lscv", action="store_true", help="skip the LSCV bandwidth-fit leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint leg (window kernel vs contractions)")
+    ap.add_argument("--adjoint-traj", type=int, default=2000,
+                    help="trajectories of 500 fixes for the adjoint leg (default 1M fixes)")
+    ap.add_argument("--adjoint-h-m", type=float, default=800.0,
+                    help="bandwidth of the adjoint leg in metres (16.4 cells)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sparse", action="store_true", help="skip the block-sparse leg")
@@ -267,6 +274,11 @@ def run_ours(args):
     import paper_2004_13653_gb300 as kde
 
     world, rank, local = dist_setup(args)
+    if args.adjoint_only:
+        kde.load(build_if_stale=True)
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_leg(torch.device("cuda", local), args, local)}))
+        return
     dev = torch.device("cuda", local)
     kde.load(build_if_stale=True)
     peaks, peak_kind = load_peaks()
@@ -488,7 +500,7 @@ def run_ours(args):
 
     if rank == 0 and args.extra:
         result["binned_estimator"] = binned_leg(dev, wl, xy_dev, origin, out_dev)
-    if rank == 0 and not (args.no_batched and args.no_lscv and not args.extra):
+    if rank == 0 and not (args.no_batched and args.no_lscv and args.no_adjoint and not args.extra):
         del lonlat_dev, xy_dev, out_dev
         torch.cuda.empty_cache()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -496,6 +508,8 @@ def run_ours(args):
             result["batched"] = batched_leg(dev, peaks, sms, local)
         if not args.no_lscv:
             result["lscv_fit"] = lscv_leg(dev, local)
+        if not args.no_adjoint:
+            result["adjoint"] = adjoint_leg(dev, args, local)
         if args.extra:
             result["extra"] = extra_workloads(dev)
 
@@ -719,6 +733,57 @@ def lscv_leg(dev, local):
             "clocks": clk,
             "input": "GPU Douglas-Peucker output at eps = 10 m, initial weights = raw fixes each "
                      "kept fix stands for"}
+
+
+def adjoint_leg(dev, args, local):
+    """The adjoint (kde_grid_backward: dL/dw, dL/dpoints, dL/dh) of the config-2
+    fixes on 1024^2 for a random cotangent at a wide bandwidth (default 800 m,
+    16.4 cells): the +-8h window kernel and the two tensor-core contractions,
+    both forced, timed, and checked against the oracle's VJP on sampled points.
+    Roofline of the contractions: 2 x 3 x N_pad x nx_pad x ny_pad FP16
+    multiply-adds against the measured sustained peak."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2004_13653_gb300 as kde
+    import workloads
+    wl = workloads.config2(n_traj=args.adjoint_traj)
+    h = args.adjoint_h_m
+    pts = torch.as_tensor(wl.xy, dtype=torch.float64, device=dev)
+    w = torch.as_tensor(wl.w, device=dev)
+    G = torch.randn((wl.ny, wl.nx), device=dev, generator=torch.Generator(dev).manual_seed(11))
+    res = {"points": int(wl.n), "grid": [wl.nx, wl.ny], "h_m": h, "h_cells": h / wl.cell}
+    outs = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for path in ("simt", "tc_split16"):
+        run = lambda: kde.grid_backward(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, h, G,
+                                        want_h=False, path=path)
+        res[{"simt": "window_ms", "tc_split16": "contractions_ms"}[path]] = _time(run, reps=3)
+        outs[path] = run()
+    res["clocks"] = clocks.stop()
+    rng = np.random.default_rng(12)
+    sel = np.sort(rng.choice(wl.n, 128, replace=False))
+    rw, rxy, _ = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, h,
+                                      G.cpu().numpy().astype(np.float64), pts=sel,
+                                      threads=os.cpu_count() or 1)
+    for path, (gxy, gw, _) in outs.items():
+        e_w = float(np.max(np.abs(gw.cpu().numpy()[sel] - rw)) / np.max(np.abs(rw)))
+        e_xy = float(np.max(np.abs(gxy.cpu().numpy()[sel] - rxy)) / np.max(np.abs(rxy)))
+        res[{"simt": "window", "tc_split16": "contractions"}[path] + "_rel_linf_vs_oracle"] = \
+            max(e_w, e_xy)
+    n_pad = (wl.n + 511) // 512 * 512
+    pad = lambda v: (v + 255) // 256 * 256
+    flops = 2 * 3 * 2.0 * n_pad * pad(wl.nx) * pad(wl.ny)
+    peaks, _ = load_peaks()
+    ach = flops / (res["contractions_ms"] * 1e-3) / 1e12
+    res["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"],
+                       "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops_sustained"],
+                       "note": "both contractions and the cotangent tiling, whole call"}
+    res["speedup"] = res["window_ms"] / res["contractions_ms"]
+    return res
 
 
 def sparse_leg(step, stream, out_dense, new_pair, dense_kernel_ms, evals, sample):
