@@ -94,8 +94,8 @@ typedef enum {
                                  /* on CTA pairs (KDE_ENOTSUP with ONE_CTA).    */
                                  /* Workspace grows by the piece partials.      */
 #define KDE_FLAG_CTA_PAIR 4u     /* TC paths: 256x256 tiles on pairs of CTAs    */
-                                 /* (tcgen05 cta_group::2); the default for     */
-                                 /* split-FP16 with 256-wide tiles              */
+                                 /* (tcgen05 cta_group::2); the default with    */
+                                 /* 256-wide tiles                              */
 #define KDE_FLAG_ONE_CTA 8u      /* TC paths: 128xN tiles on single CTAs        */
 #define KDE_FLAG_LONLAT 16u      /* points are (lon, lat) in degrees: the call  */
                                  /* projects them with Eq. 1-4 (as            */

@@ -174,7 +174,7 @@ def test_cta_pair_batched_matches_single():
 
 @pytest.mark.parametrize("path,flags", [
     ("auto", 0), ("tc_split16", kde.FLAG_CTA_PAIR), ("tc_split16", kde.FLAG_ONE_CTA),
-    ("tc_fp16", 0), ("tc_fp16", kde.FLAG_CTA_PAIR), ("tc_split16", kde.FLAG_SKIP_ZERO)],
+    ("tc_fp16", kde.FLAG_ONE_CTA), ("tc_fp16", kde.FLAG_CTA_PAIR), ("tc_split16", kde.FLAG_SKIP_ZERO)],
     ids=["auto", "split-pair", "split-one-cta", "fp16-one-cta", "fp16-pair", "split-sparse"])
 def test_signed_weights_match_oracle(path, flags):
     """Weights of both signs (a density minus another, Eq. 7 with signed w):
