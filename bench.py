@@ -152,6 +152,8 @@ def parse():
                     help="trajectories of 500 fixes for the adjoint leg (default 1M fixes)")
     ap.add_argument("--adjoint-h-m", type=float, default=800.0,
                     help="bandwidth of the adjoint leg in metres (16.4 cells)")
+    ap.add_argument("--no-peak-probe", action="store_true",
+                    help="skip the measured tensor-core and ex2 rates")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sparse", action="store_true", help="skip the block-sparse leg")
@@ -470,6 +472,21 @@ def run_ours(args):
                          "kernel_ms": statistics.mean(a.elapsed_time(b) for a, b in e2e_pairs),
                          "clocks": e2e_clocks.stop()}
         del ws
+
+    if rank == 0 and not args.no_peak_probe:
+        # the tcgen05 FP16 and ex2 rates measured by the library's own probes,
+        # at the clock the GPU runs at now (after the steps above)
+        probe_clocks = ClockSampler(local)
+        probe_clocks.start()
+        time.sleep(0.2)
+        rates = kde.peak_rates()
+        result["measured_rates"] = dict(rates, clocks=probe_clocks.stop(),
+                                        note="kde_diag_peak_rates: MMAs on resident operands, "
+                                             "every SM, second of two passes")
+        if roof["bound"] == "tensor":
+            one_cta = args.flags & kde.FLAG_ONE_CTA  # CTA pairs are the default
+            probe = rates["mma_f16_cta_tflops" if one_cta else "mma_f16_pair_tflops"]
+            roof["frac_of_probe"] = roof["achieved"] / probe
 
     sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -36,6 +36,20 @@ int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int pe
  */
 int kde_diag_wait_timeout(int64_t limit_ns, void* stream);
 
+/*
+ * kde_diag_peak_rates — measures, at the clock the GPU runs at, the rates the
+ * rooflines of the tensor-core and exp-bound kernels are set against (no
+ * counterpart in the paper): rates[0] = tcgen05 kind::f16 MMAs on CTA pairs
+ * (M = 256, N = 256, K = 16, operands resident in shared memory), TFLOP/s;
+ * rates[1] = the same on single CTAs (M = 128, N = 256); rates[2] = MUFU
+ * ex2.approx results per second, in units of 1e12.  rates: host, [3] double,
+ * written only on success.  Each probe runs for a few milliseconds on every
+ * SM, twice (the first pass warms the clocks up).  Synchronous; uses the
+ * library workspace.  Errors: KDE_EINVAL (null rates), KDE_ENOMEM, KDE_ECUDA,
+ * KDE_ETIMEOUT (a bounded device-side wait gave up).
+ */
+int kde_diag_peak_rates(double* rates, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,7 @@ EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
            "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
-           "kde_grid_binned", "kde_dp_simplify")
+           "kde_grid_binned", "kde_dp_simplify", "kde_diag_peak_rates")
 
 _lib = None
 
@@ -121,6 +121,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_dp_simplify.restype = i32
     lib.kde_diag_wait_timeout.argtypes = [i64, vp]
     lib.kde_diag_wait_timeout.restype = i32
+    lib.kde_diag_peak_rates.argtypes = [P(ctypes.c_double * 3), vp]
+    lib.kde_diag_peak_rates.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
     lib.kde_diag_exclusive_scan.restype = i32
     lib.kde_version.argtypes = []
@@ -400,6 +402,16 @@ def exclusive_scan(values, per_block=2048, out=None):
     check(load().kde_diag_exclusive_scan(_ptr(values), _ptr(out), _count(values), int(per_block),
                                          None))
     return out
+
+
+def peak_rates(stream=None) -> dict:
+    """kde_diag_peak_rates: the measured tcgen05 FP16 rates (TFLOP/s, CTA
+    pairs and single CTAs) and the MUFU ex2 rate (1e12 per second)."""
+    r = (ctypes.c_double * 3)()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    check(load().kde_diag_peak_rates(ctypes.byref(r), stream))
+    return {"mma_f16_pair_tflops": r[0], "mma_f16_cta_tflops": r[1], "ex2_tera_per_s": r[2]}
 
 
 def release() -> None:

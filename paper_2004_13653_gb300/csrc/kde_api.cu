@@ -1439,6 +1439,27 @@ int kde_diag_wait_timeout(int64_t limit_ns, void* stream) {
   return KDE_OK;
 }
 
+int kde_diag_peak_rates(double* rates, void* stream) {
+  if (!rates) return fail(KDE_EINVAL, "null pointer");
+  void* ws = nullptr;
+  int rc = library_workspace(sizeof(CallScalars) + 256 * sizeof(float), &ws);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CallScalars* scal = static_cast<CallScalars*>(ws);
+  float* sink = reinterpret_cast<float*>(static_cast<char*>(ws) + sizeof(CallScalars));
+  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars), s), "clear scalars");
+  double r[3] = {0.0, 0.0, 0.0};
+  KDE_CUDA(run_peak_probes(sm_count(), scal, sink, r, s), "peak probes");
+  CallScalars hs;
+  KDE_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s), "read status");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  if (hs.err & kErrTimeout)
+    return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs.timeout_where);
+  for (int k = 0; k < 3; ++k) rates[k] = r[k];
+  g_err[0] = 0;
+  return KDE_OK;
+}
+
 int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int per_block,
                             void* stream) {
   if (n < 0 || per_block < 1 || per_block > 2048)

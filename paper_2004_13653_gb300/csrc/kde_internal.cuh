@@ -387,6 +387,10 @@ struct TcPlan {
 size_t tc_smem_bytes(const TcPlan& p);
 // Diagnostic: one wait that times out after limit_ns (sets kErrTimeout).
 cudaError_t launch_wait_timeout(CallScalars* scal, uint64_t limit_ns, cudaStream_t s);
+// Diagnostic: measured tcgen05 FP16 rates (pairs, single CTAs; TFLOP/s) and
+// the ex2 rate (1e12 per second) in rates[0..2].  sink: device, 256 floats.
+cudaError_t run_peak_probes(int sms, CallScalars* scal, float* sink, double* rates,
+                            cudaStream_t s);
 // One persistent launch over the work items of every instance in `tab`.
 cudaError_t launch_tc(const TcPlan& plan, const TcInst* tab, int ninst, int n_items,
                       CallScalars* err, cudaStream_t s);

@@ -12,9 +12,9 @@
 //   warp 0      one thread issues tcgen05.mma (FP16 x FP16 -> FP32 in TMEM)
 //   warp 1      loads 64 points per stage and re-centres them on the tile
 //   warps 2-5   epilogue: TMEM -> registers -> partial grid in global memory
-//   warps 6..   producers: one operand row each, 64 exponentials per stage,
-//               written as FP16 (or hi + lo FP16 pairs) into shared memory in
-//               the 128-byte-swizzled K-major layout the MMA reads directly.
+//   warps 6..   producers: one warp per 32 operand rows; each thread writes
+//               a share of the chunks of up to four rows, as FP16 (or hi + lo
+//               FP16 pairs) in the swizzled K-major layout the MMA reads.
 // A and B never exist in global memory.  The FP32 accumulator is drained
 // every k_chunk points into the partial grid (double-buffered in TMEM) so the
 // tensor core never adds more than k_chunk/16 products into one FP32 value.
@@ -54,8 +54,12 @@ struct Cfg {
   static constexpr int kParts = SPLIT ? 2 : 1;
   static constexpr int kStageBytes = kParts * (kABytes + kBBytes);
   static constexpr int kStages = (192 * 1024) / kStageBytes;
-  static constexpr int kProducers = kBM + BN;
+  static constexpr int kProducers = kBM + BN;  // operand rows (one producer thread per row)
   static constexpr int kProducerWarps = kProducers / 32;
+  // rows per producer thread: a block of 32 * RPT rows is written by RPT
+  // warps, each taking kChunks / RPT of the row's chunks
+  static constexpr int kRowsPerThread =
+      (kProducers % 128 == 0 && kChunks % 4 == 0) ? 4 : (kProducers % 64 == 0 && kChunks % 2 == 0) ? 2 : 1;
   static constexpr int kThreads = 32 * (6 + kProducerWarps);
   // TMEM: accumulator halves in columns [0, BN), running sums in [BN, 2 BN)
   static constexpr uint32_t kTmemCols = 2 * BN;
@@ -377,9 +381,17 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ producers
-    const int t = threadIdx.x - 6 * 32;
-    const bool isA = t < kBM;  // warp-uniform
-    const int r = isA ? t : t - kBM;
+    // Rows come in blocks of 32 * RPT (A rows first, then B rows); the RPT
+    // warps of a block split its chunks, and lane l writes rows l + 32 k.  A
+    // thread reuses each broadcast load of a chunk's point parameters for
+    // its RPT rows, which keeps these loads a small share of the shared-
+    // memory bandwidth the operand stores and the tensor core's reads take.
+    constexpr int RPT = C::kRowsPerThread, CPT = C::kChunks / RPT;
+    const int pw = warp - 6;
+    const int rowblock = pw / RPT, cset = pw % RPT;
+    const int row_first = rowblock * 32 * RPT;  // in A rows, then B rows
+    const bool isA = row_first < kBM;           // warp-uniform
+    const int r0 = (isA ? row_first : row_first - kBM) + lane;
     const int lo_off = isA ? C::kABytes : C::kBBytes;
     uint32_t g = 0;
     bool ok = true;
@@ -387,28 +399,32 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
       const Item itm = item_of(tab, ninst, it, kKS);
       const TcInst& I = *itm.I;
       const bool signs = !isA && I.scal->negw != 0;
-      float gv;
-      if (isA) {
-        const float2 c = I.gxt[min(itm.tm * kBM + kBM / 2, I.nx - 1)];
-        const float2 v = I.gxt[min(itm.tm * kBM + r, I.nx - 1)];
-        gv = (v.x - c.x) + (v.y - c.y);
-      } else {
-        const float2 c = I.gyt[min(itm.tn * BN + BN / 2, I.ny - 1)];
-        const float2 v = I.gyt[min(itm.tn * BN + r, I.ny - 1)];
-        gv = (v.x - c.x) + (v.y - c.y);
+      float gv[RPT];
+      {
+        const float2* tab_g = isA ? I.gxt : I.gyt;
+        const int base = isA ? itm.tm * kBM : itm.tn * BN;
+        const int half = isA ? kBM / 2 : BN / 2;
+        const int n_g = isA ? I.nx : I.ny;
+        const float2 c = tab_g[min(base + half, n_g - 1)];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const float2 v = tab_g[min(base + r0 + 32 * k, n_g - 1)];
+          gv[k] = (v.x - c.x) + (v.y - c.y);
+        }
       }
       for (int st = 0; st < itm.nst; ++st, ++g) {
         const uint32_t s = g % C::kStages, ps = g % kPS;
         if (!(ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer))) break;
         if (!(ok = mbar_wait(&empty[s], ((g / C::kStages) & 1) ^ 1, abort_flag, scal, kRoleProducer)))
           break;
-        unsigned char* hi_row =
-            smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
+        unsigned char* row0 =
+            smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r0 * C::kRowBytes;
         const float4* crd = reinterpret_cast<const float4*>(params + ps * 4 * kKS + (isA ? 0 : kKS));
         const float4* cbv = reinterpret_cast<const float4*>(params + ps * 4 * kKS + 2 * kKS);
         const uint4* sgn = reinterpret_cast<const uint4*>(params + ps * 4 * kKS + 3 * kKS);
-#pragma unroll 4
-        for (int c = 0; c < C::kChunks; ++c) {
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+          const int c = cset * CPT + cc;
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
           float4 c0 = make_float4(15.f, 15.f, 15.f, 15.f), c1 = c0;
           if (!isA) {
@@ -417,38 +433,44 @@ __global__ void __launch_bounds__(Cfg<BN, SPLIT, KS>::kThreads, 1)
           }
           const float pc[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
           const float ce[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-          float v[8];
-#pragma unroll
-          for (int e2 = 0; e2 < 8; ++e2) {
-            const float u = gv - pc[e2];
-            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
-          }
+          uint32_t sb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
           if (signs) {  // negative weights: B takes the weight's sign
             const uint4 s0 = sgn[2 * c], s1 = sgn[2 * c + 1];
-            const uint32_t sb[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-#pragma unroll
-            for (int e2 = 0; e2 < 8; ++e2) v[e2] = __uint_as_float(__float_as_uint(v[e2]) ^ sb[e2]);
+            sb[0] = s0.x; sb[1] = s0.y; sb[2] = s0.z; sb[3] = s0.w;
+            sb[4] = s1.x; sb[5] = s1.y; sb[6] = s1.z; sb[7] = s1.w;
           }
-          const int off = (c ^ ((r >> C::kSwzShift) & (C::kChunks - 1))) << 4;
-          uint32_t hw[4], lw[4];
+          // rows lane + 32 k share the swizzle phase of row lane
+          const int off = (c ^ ((lane >> C::kSwzShift) & (C::kChunks - 1))) << 4;
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            if (SPLIT) {
-              // hi keeps 11 significant bits (exact in FP16), lo = v - hi exactly
-              const float h0 = __uint_as_float(__float_as_uint(v[2 * e2]) & 0xFFFFE000u);
-              const float h1 = __uint_as_float(__float_as_uint(v[2 * e2 + 1]) & 0xFFFFE000u);
-              const __half2 hh = __floats2half2_rn(h0, h1);
-              const __half2 ll = __floats2half2_rn(v[2 * e2] - h0, v[2 * e2 + 1] - h1);
-              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
-              lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
-            } else {
-              const __half2 hh = __floats2half2_rn(v[2 * e2], v[2 * e2 + 1]);
-              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+          for (int k = 0; k < RPT; ++k) {
+            float v[8];
+#pragma unroll
+            for (int e2 = 0; e2 < 8; ++e2) {
+              const float u = gv[k] - pc[e2];
+              asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v[e2]) : "f"(fmaf(-u, u, ce[e2])));
+              if (signs) v[e2] = __uint_as_float(__float_as_uint(v[e2]) ^ sb[e2]);
             }
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              if (SPLIT) {
+                // hi keeps 11 significant bits (exact in FP16), lo = v - hi exactly
+                const float h0 = __uint_as_float(__float_as_uint(v[2 * e2]) & 0xFFFFE000u);
+                const float h1 = __uint_as_float(__float_as_uint(v[2 * e2 + 1]) & 0xFFFFE000u);
+                const __half2 hh = __floats2half2_rn(h0, h1);
+                const __half2 ll = __floats2half2_rn(v[2 * e2] - h0, v[2 * e2 + 1] - h1);
+                hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+                lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
+              } else {
+                const __half2 hh = __floats2half2_rn(v[2 * e2], v[2 * e2 + 1]);
+                hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+              }
+            }
+            unsigned char* row = row0 + 32 * k * C::kRowBytes;
+            *reinterpret_cast<uint4*>(row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if (SPLIT)
+              *reinterpret_cast<uint4*>(row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
           }
-          *reinterpret_cast<uint4*>(hi_row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          if (SPLIT)
-            *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         // each writer makes its stores visible to the tensor core's proxy; the
         // warp then signals once (__syncwarp orders the lanes' writes first)

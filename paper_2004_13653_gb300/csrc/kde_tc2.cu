@@ -17,8 +17,8 @@
 //   WG1-2 warps 4-11: epilogue.  Each thread owns one TMEM lane (an x cell)
 //         and 128 of the tile's 256 y cells, and keeps their running sums in
 //         its registers (168 registers).
-//   WG3-4 warps 12-19: operand producers, one thread per A or B row
-//         (48 registers).
+//   WG3-4 warps 12-19: operand producers, four per operand; each thread
+//         writes a quarter of four A or B rows (48 registers).
 //
 // Accumulators: two N = 256 FP32 accumulators fill TMEM's 512 columns.  The
 // MMAs of chunk c (k_chunk points) accumulate into accumulator c mod 2 while
@@ -66,6 +66,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kWarpMma = 0, kWarpLoader = 1, kWarpSignal = 2;
 constexpr int kFirstEpiWarp = 4, kEpiWarps = 8;
 constexpr int kFirstProducerWarp = 12, kProducerWarps = 8;
+constexpr int kRowsPerThread = kRows / 32;  // operand rows per producer thread
 constexpr int kRegsLaunch = 96;  // 640 threads: at most 65536 / 640 = 102, allocated in 8s
 constexpr int kRegsCtl = 48, kRegsEpi = 168, kRegsProd = 48;
 static_assert(128 * kRegsCtl + 256 * kRegsEpi + 256 * kRegsProd <= kThreads * kRegsLaunch,
@@ -467,10 +468,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok && lane == 0) propagate_abort();
   } else {
     // ------------------------------------------------------------ producers
+    // Four warps per operand; lane l of warp k of a group writes rows l,
+    // l + 32, l + 64, l + 96 in chunks 2k and 2k + 1.  A thread reuses each
+    // broadcast load of a chunk's point parameters for its four rows, which
+    // keeps these loads a small share of the shared-memory bandwidth the
+    // tensor core's operand reads and the operand stores already take.
     regs_dec<kRegsProd>();
-    const int t = threadIdx.x - kFirstProducerWarp * 32;
-    const bool isA = t < kRows;  // warp-uniform
-    const int r = t & (kRows - 1);
+    const int pw = warp - kFirstProducerWarp;
+    const bool isA = pw < kProducerWarps / 2;  // warp-uniform
+    const int c0 = 2 * (pw & 3);
     const int lo_off = isA ? C::kABytes : C::kBBytes;
     uint32_t g = 0;
     bool ok = true;
@@ -481,19 +487,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const Item itm = get_item<SPARSE>(tab, ninst, sp, it);
       const TcInst& I = *itm.I;
       const bool signs = !isA && I.scal->negw != 0;
-      float gv;
-      if (isA) {
-        const int base = itm.tm * 256 + (int)rank * kRows;
-        const float2 c = I.gxt[min(base + kRows / 2, I.nx - 1)];
-        const float2 v = I.gxt[min(base + r, I.nx - 1)];
-        gv = (v.x - c.x) + (v.y - c.y);
-      } else {
-        const int base = itm.tn * 256 + (int)rank * kRows;
-        const float2 c = I.gyt[min(base + kRows / 2, I.ny - 1)];
-        const float2 v = I.gyt[min(base + r, I.ny - 1)];
-        gv = (v.x - c.x) + (v.y - c.y);
+      float ngv[kRowsPerThread];  // minus the rows' cell coordinates
+      {
+        const int base = (isA ? itm.tm : itm.tn) * 256 + (int)rank * kRows;
+        const float2* tab_g = isA ? I.gxt : I.gyt;
+        const int n_g = isA ? I.nx : I.ny;
+        const float2 c = tab_g[min(base + kRows / 2, n_g - 1)];
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+          const float2 v = tab_g[min(base + k * 32 + lane, n_g - 1)];
+          ngv[k] = -((v.x - c.x) + (v.y - c.y));
+        }
       }
-      const float2 ng2 = make_float2(-gv, -gv);
       for (int st = 0; st < itm.nst; ++st, ++g) {
         const uint32_t s = g % C::kStages, ps = g % kPS;
         if (ok) ok = mbar_wait(&pfull[ps], (g / kPS) & 1, abort_flag, scal, kRoleProducer);
@@ -503,55 +508,63 @@ __global__ void __launch_bounds__(kThreads, 1)
           named_arrive(kBarProducers + (int)s, 32 * (kProducerWarps + 1));
           continue;
         }
-        unsigned char* hi_row =
-            smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + r * C::kRowBytes;
+        unsigned char* row0 =
+            smem + s * C::kStageBytes + (isA ? C::kOffA : C::kOffB) + lane * C::kRowBytes;
         const float* prm = params + ps * kPrmFloats;
         const float4* crd = reinterpret_cast<const float4*>(prm + (isA ? kPrmA : kPrmB));
         const float4* nce = reinterpret_cast<const float4*>(prm + kPrmN);
         const uint4* sgn = reinterpret_cast<const uint4*>(prm + kPrmS);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = c0 + cc;
           const float4 p0 = crd[2 * c], p1 = crd[2 * c + 1];
           float4 n0 = make_float4(-15.f, -15.f, -15.f, -15.f), n1 = n0;
           if (!isA) {
             n0 = nce[2 * c];
             n1 = nce[2 * c + 1];
           }
+          uint4 sg = make_uint4(0u, 0u, 0u, 0u);
+          if (signs) sg = sgn[c];
           const float2 P2[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w),
                                 make_float2(p1.x, p1.y), make_float2(p1.z, p1.w)};
           const float2 N2[4] = {make_float2(n0.x, n0.y), make_float2(n0.z, n0.w),
                                 make_float2(n1.x, n1.y), make_float2(n1.z, n1.w)};
-          uint32_t hw[4], lw[4];
+          // rows lane + 32 k share the swizzle phase lane & 7
+          const int off = (c ^ (lane & 7)) << 4;
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            const float2 u = add2(P2[e2], ng2);     // point - cell, in units of h sqrt(2 ln 2)
-            const float2 y = fma2(u, u, N2[e2]);    // u^2 - exponent offset
-            const float v0 = ex2_neg(y.x), v1 = ex2_neg(y.y);
-            if (SPLIT) {
-              // hi = v with 11 significant bits (exact in FP16), lo = v - hi
-              const float h0 = __uint_as_float(__float_as_uint(v0) & 0xFFFFE000u);
-              const float h1 = __uint_as_float(__float_as_uint(v1) & 0xFFFFE000u);
-              const float2 l = sub2(make_float2(v0, v1), make_float2(h0, h1));
-              const __half2 hh = __floats2half2_rn(h0, h1);
-              const __half2 ll = __floats2half2_rn(l.x, l.y);
-              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
-              lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
-            } else {
-              const __half2 hh = __floats2half2_rn(v0, v1);
-              hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+          for (int k = 0; k < kRowsPerThread; ++k) {
+            const float2 ng2 = make_float2(ngv[k], ngv[k]);
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              const float2 u = add2(P2[e2], ng2);     // point - cell, in units of h sqrt(2 ln 2)
+              const float2 y = fma2(u, u, N2[e2]);    // u^2 - exponent offset
+              const float v0 = ex2_neg(y.x), v1 = ex2_neg(y.y);
+              if (SPLIT) {
+                // hi = v with 11 significant bits (exact in FP16), lo = v - hi
+                const float h0 = __uint_as_float(__float_as_uint(v0) & 0xFFFFE000u);
+                const float h1 = __uint_as_float(__float_as_uint(v1) & 0xFFFFE000u);
+                const float2 l = sub2(make_float2(v0, v1), make_float2(h0, h1));
+                const __half2 hh = __floats2half2_rn(h0, h1);
+                const __half2 ll = __floats2half2_rn(l.x, l.y);
+                hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+                lw[e2] = *reinterpret_cast<const uint32_t*>(&ll);
+              } else {
+                const __half2 hh = __floats2half2_rn(v0, v1);
+                hw[e2] = *reinterpret_cast<const uint32_t*>(&hh);
+              }
             }
-          }
-          if (signs) {  // negative weights: flip the FP16 sign bits of those points
-            const uint4 sg = sgn[c];
-            hw[0] ^= sg.x; hw[1] ^= sg.y; hw[2] ^= sg.z; hw[3] ^= sg.w;
-            if (SPLIT) {
-              lw[0] ^= sg.x; lw[1] ^= sg.y; lw[2] ^= sg.z; lw[3] ^= sg.w;
+            if (signs) {  // negative weights: flip the FP16 sign bits of those points
+              hw[0] ^= sg.x; hw[1] ^= sg.y; hw[2] ^= sg.z; hw[3] ^= sg.w;
+              if (SPLIT) {
+                lw[0] ^= sg.x; lw[1] ^= sg.y; lw[2] ^= sg.z; lw[3] ^= sg.w;
+              }
             }
+            unsigned char* row = row0 + k * 32 * C::kRowBytes;
+            *reinterpret_cast<uint4*>(row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if (SPLIT)
+              *reinterpret_cast<uint4*>(row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
           }
-          const int off = (c ^ (r & 7)) << 4;
-          *reinterpret_cast<uint4*>(hi_row + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          if (SPLIT)
-            *reinterpret_cast<uint4*>(hi_row + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         // order this thread's stores before the tensor core's reads of them,
         // then hand the stage to the signalling warp without waiting
