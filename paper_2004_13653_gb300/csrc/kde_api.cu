@@ -279,6 +279,7 @@ struct BatchPlan {
   std::vector<int> tc_order;  // TC instances: the families' orders concatenated
   int n_tc = 0, n_cut = 0, n_simt = 0, n_reduce = 0, tc_items = 0, max_side = 1;
   int64_t total_pad = 0, cut_m = 0, total_bins = 0, reduce_cells = 0, cut_bins = 0;
+  int64_t cut_slice_bins = 0;  // output blocks of cutoff instances that split heavy blocks
   bool sparse = false;  // block-sparse tensor-core instances
   int tiles_total = 0, piece_len = 0, max_pieces = 0;
   size_t off_sp_total = 0, off_sp_np = 0, off_sp_pb = 0, off_sp_nf = 0, off_sp_fb = 0,
@@ -287,7 +288,8 @@ struct BatchPlan {
   bool host_pts = false, host_w = false, host_out = false;
   size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
   size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
-      off_co_spts, off_co_sw, off_co_order, off_co_totals, off_co_ocount, off_hxy, off_hw,
+      off_co_spts, off_co_sw, off_co_order, off_co_totals, off_co_ranges, off_co_ocount, off_hxy,
+      off_hw,
       off_hout, total;
 };
 
@@ -483,6 +485,7 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
       I.oby = (a->ny + kCutoffBin - 1) / kCutoffBin;
       I.out_begin = (int)P->cut_bins;
       P->cut_bins += (int64_t)I.obx * I.oby;
+      if (I.geo.bin == 4) P->cut_slice_bins += (int64_t)I.obx * I.oby;
       I.cut_begin = P->cut_m;
       P->cut_m += I.n_pad;
       ++P->n_cut;
@@ -595,14 +598,15 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
       P->off_co_vals[k] = take(u * (size_t)P->cut_m);
     }
     P->off_co_hist = take(u * P->cz.hist_words);
-    P->off_co_hscan = take(u * P->cz.hist_words);
+    P->off_co_hscan = take(u);  // unused by the one-sweep sort
     P->off_co_stemp = take(u * (P->cz.scan_words + 64));
     P->off_co_start = take(u * ((size_t)P->total_bins + 1));
     P->off_co_spts = take(sizeof(float4) * (size_t)P->cut_m);
     P->off_co_sw = take(sizeof(float) * (size_t)P->cut_m);
     P->off_co_order = take(u * (size_t)std::max<int64_t>(P->cut_bins, 1));
     P->off_co_totals = take(u * (size_t)std::max<int64_t>(P->cut_bins, 1));
-    P->off_co_ocount = take(u * 2 * kCutOrderKeys);
+    P->off_co_ranges = take(sizeof(int4) * (size_t)std::max<int64_t>(P->cut_bins, 1));
+    P->off_co_ocount = take(u * kCutOcountWords);
   }
   if (P->sparse) {
     const size_t u = sizeof(uint32_t);
@@ -812,6 +816,7 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
       q.ny = A[k].ny;
       q.kid = kid_of(&A[k]);
       q.scale = compact_scale(k);
+      q.slice = I.geo.bin == 4;
       cut.push_back(q);
     }
     if (I.splits > 1) {
@@ -890,7 +895,9 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
     cs.sw = reinterpret_cast<float*>(base + P.off_co_sw);
     cs.order = reinterpret_cast<uint32_t*>(base + P.off_co_order);
     cs.totals = reinterpret_cast<uint32_t*>(base + P.off_co_totals);
+    cs.ranges = reinterpret_cast<int4*>(base + P.off_co_ranges);
     cs.ocount = reinterpret_cast<uint32_t*>(base + P.off_co_ocount);
+    cs.err = batch_scal;
   }
   // The compact instances (sort and gather) overlap the tensor-core
   // contraction on the side stream when no block-sparse instance needs the
@@ -957,11 +964,13 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
     KDE_CUDA(cudaStreamWaitEvent(s2, fork, 0), "side stream waits for the prepared points");
     KDE_CUDA(launch_bin_sort(d_cut, (int)cut.size(), P.cut_m, P.total_bins, pts, wts, P.cz, cs, s2),
              "bin sort");
-    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, cs, s2), "cutoff evaluation");
+    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, P.cut_slice_bins, cs, s2),
+             "cutoff evaluation");
     KDE_CUDA(cudaEventRecord(join, s2), "join from the side stream");
     KDE_CUDA(cudaStreamWaitEvent(s, join, 0), "join the side stream");
   } else if (P.n_cut) {
-    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, cs, s), "cutoff evaluation");
+    KDE_CUDA(launch_cutoff_eval(d_cut, n_cut_only, P.cut_bins, P.cut_slice_bins, cs, s),
+             "cutoff evaluation");
   }
   if (ev) KDE_CUDA(cudaEventRecord(ev[1], s), "record end event");
   if (P.n_reduce) KDE_CUDA(launch_reduce(d_red, P.n_reduce, P.reduce_cells, s), "split-K reduce");

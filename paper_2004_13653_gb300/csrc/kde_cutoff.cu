@@ -15,6 +15,7 @@
 // block-sparse tensor-core path.
 #include "kde_internal.cuh"
 #include "kernel_factors.cuh"
+#include "tc_ptx.cuh"
 
 namespace kde {
 namespace {
@@ -25,6 +26,7 @@ constexpr int kGroups = 8;          // point groups per CTA (one output block)
 constexpr int kSortThreads = 256;   // 8 warps
 constexpr int kSortRounds = 8;      // 32-element rounds per warp
 constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
+constexpr int kMaxPasses = 4;     // 8-bit digits of 32-bit keys
 constexpr int kBatch = 32;          // points per shared-memory batch (one per lane)
 
 template <class T>
@@ -40,36 +42,61 @@ __device__ __forceinline__ int find_by(const T* tab, int ninst, int64_t v, int64
 // Bin key of each point of every instance (points centred and scaled):
 // key = bin_begin + by * nbx + bx, or total_bins for padding and for points
 // that cannot reach their grid.  vals = the point's index in the prepared
-// arrays.
-__global__ void k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m,
-                           const float4* __restrict__ prepared, uint32_t total_bins,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// arrays.  Each CTA also counts the digits of every radix pass of its keys
+// (lanes that share a digit add once) and adds them to the per-pass
+// histograms ghist[pass][256].
+__global__ void __launch_bounds__(256)
+    k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m,
+               const float4* __restrict__ prepared, uint32_t total_bins, int passes,
+               uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+               uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kMaxPasses][256];
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < m; g += stride) {
-    const CutInst& I = tab[find_by(tab, ninst, g, &CutInst::cut_begin)];
-    const int64_t p = g - I.cut_begin;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count, so every lane takes part in the matches
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); g0 < m; g0 += stride) {
+    const int64_t g = g0 + lane;
+    const bool valid = g < m;
     uint32_t key = total_bins;
-    if (p < I.n) {
-      // FP32 throughout (FP64 is slow here): the keys can be one bin off near
-      // a bin edge, which the ranges' widened reach covers
-      const float4 q = prepared[I.prep_begin + p];
-      const float X = q.x + q.y, Y = q.z + q.w;
-      // a point reaches the grid only if it lies within the reach of it
-      if (X >= I.key_lo && Y >= I.key_lo && X <= I.key_hx && Y <= I.key_hy) {
-        const int bx = min(max((int)floorf(X * I.key_inv), 0), I.nbx - 1);
-        const int by = min(max((int)floorf(Y * I.key_inv), 0), I.nby - 1);
-        key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
+    if (valid) {
+      const CutInst& I = tab[find_by(tab, ninst, g, &CutInst::cut_begin)];
+      const int64_t p = g - I.cut_begin;
+      if (p < I.n) {
+        // FP32 throughout (FP64 is slow here): the keys can be one bin off near
+        // a bin edge, which the ranges' widened reach covers
+        const float4 q = prepared[I.prep_begin + p];
+        const float X = q.x + q.y, Y = q.z + q.w;
+        // a point reaches the grid only if it lies within the reach of it
+        if (X >= I.key_lo && Y >= I.key_lo && X <= I.key_hx && Y <= I.key_hy) {
+          const int bx = min(max((int)floorf(X * I.key_inv), 0), I.nbx - 1);
+          const int by = min(max((int)floorf(Y * I.key_inv), 0), I.nby - 1);
+          key = (uint32_t)I.bin_begin + (uint32_t)by * I.nbx + bx;
+        }
       }
+      keys[g] = key;
+      vals[g] = (uint32_t)(I.prep_begin + p);
     }
-    keys[g] = key;
-    vals[g] = (uint32_t)(I.prep_begin + p);
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    for (int pass = 0; pass < passes; ++pass) {
+      const uint32_t d = (key >> (8 * pass)) & 255u;
+      const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 256u) & act;
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[pass][d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(&ghist[i], c);
   }
 }
 
 // Rank of each key's digit among equal digits earlier in this block's chunk:
-// each warp walks its 256 keys in rounds of 32, peers found with match_any,
-// per-warp digit counts kept in shared memory.  Deterministic.
-__device__ __forceinline__ void rank_digits(const uint32_t* __restrict__ keys, int64_t m,
+// each warp walks its 256 keys (kv, loaded beforehand) in rounds of 32, peers
+// found with match_any, per-warp digit counts kept in shared memory.
+// Deterministic.
+__device__ __forceinline__ void rank_digits(const uint32_t (&kv)[kSortRounds], int64_t m,
                                             int64_t base, int shift,
                                             uint32_t (*cnt)[256], uint32_t (&digit)[kSortRounds],
                                             uint32_t (&rank)[kSortRounds]) {
@@ -79,7 +106,7 @@ __device__ __forceinline__ void rank_digits(const uint32_t* __restrict__ keys, i
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t e = base + (int64_t)warp * 32 * kSortRounds + r * 32 + lane;
     const bool valid = e < m;
-    const uint32_t d = valid ? (keys[e] >> shift) & 255u : 0u;
+    const uint32_t d = valid ? (kv[r] >> shift) & 255u : 0u;
     const uint32_t active = __ballot_sync(0xffffffffu, valid);
     uint32_t peers = 0, old = 0;
     if (valid) {
@@ -94,51 +121,126 @@ __device__ __forceinline__ void rank_digits(const uint32_t* __restrict__ keys, i
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-    k_radix_count(const uint32_t* __restrict__ keys, int64_t m, int shift, int nchunks,
-                  uint32_t* __restrict__ hist) {
-  __shared__ uint32_t cnt[kSortThreads / 32][256];
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
-  __syncthreads();
-  uint32_t digit[kSortRounds], rank[kSortRounds];
-  rank_digits(keys, m, (int64_t)blockIdx.x * kSortChunk, shift, cnt, digit, rank);
-  __syncthreads();
-  const int d = threadIdx.x;  // 256 threads, one digit each
-  uint32_t sum = 0;
-  for (int w = 0; w < kSortThreads / 32; ++w) sum += cnt[w][d];
-  hist[(int64_t)d * nchunks + blockIdx.x] = sum;
+// Look-back status of one (chunk, digit) of a radix pass: bits 61-63 the pass
+// number plus one (0 or another pass: not yet published by this pass), bit 60
+// set when the value is the inclusive prefix over chunks 0..c, clear when it
+// is the chunk's own count; bits 0-39 the value.
+constexpr unsigned long long kStatusIncl = 1ull << 60;
+constexpr unsigned long long kStatusValue = (1ull << 40) - 1;
+constexpr int kRoleLookback = 31;  // timeout role id of the look-back wait
+
+__device__ __forceinline__ unsigned long long status_word(int pass, bool incl, uint64_t v) {
+  return ((unsigned long long)(pass + 1) << 61) | (incl ? kStatusIncl : 0ull) | v;
 }
 
+// One stable counting pass over 8 bits of the keys (Merrill and Garland's
+// single-pass prefix scan with decoupled look-back, applied per digit).  CTAs
+// take 2048-key chunks in the order they start (a counter), so every chunk a
+// CTA waits for belongs to a CTA that is already running.  Each CTA ranks its
+// keys per digit (stable: warps in order, lanes in order), publishes its
+// per-digit counts, then walks back over earlier chunks until it meets an
+// inclusive prefix, publishes its own inclusive prefix and scatters: position
+// = (keys of smaller digits) + (same digit in earlier chunks) + rank.  The
+// last pass writes the permuted points and weights instead of the indices.
+// A wait that does not end within the limit records a timeout in err; the
+// positions are then bounded, not correct.
 __global__ void __launch_bounds__(kSortThreads)
-    k_radix_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                    int64_t m, int shift, int nchunks, const uint32_t* __restrict__ offs,
-                    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+    k_radix_pass(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
+                 int pass, const uint32_t* __restrict__ ghist, uint32_t* __restrict__ chunk_ctr,
+                 unsigned long long* __restrict__ status, uint32_t* __restrict__ keys_out,
+                 uint32_t* __restrict__ vals_out, const float4* __restrict__ prepared,
+                 const float* __restrict__ wts, float4* __restrict__ spts, float* __restrict__ sw,
+                 int last, CallScalars* __restrict__ err) {
   __shared__ uint32_t cnt[kSortThreads / 32][256];
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t wsum[kSortThreads / 32];
+  __shared__ uint32_t chunk_s;
+  if (threadIdx.x == 0) chunk_s = atomicAdd(&chunk_ctr[pass], 1u);
   for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  uint32_t digit[kSortRounds], rank[kSortRounds];
-  const int64_t base = (int64_t)blockIdx.x * kSortChunk;
-  rank_digits(keys, m, base, shift, cnt, digit, rank);
-  __syncthreads();
-  {  // exclusive prefix of the per-warp counts, per digit
-    const int d = threadIdx.x;
-    uint32_t run = 0;
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      const uint32_t c = cnt[w][d];
-      cnt[w][d] = run;
-      run += c;
-    }
+  const uint32_t chunk = chunk_s;
+  const int shift = 8 * pass;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e0 = (int64_t)chunk * kSortChunk + (int64_t)warp * 32 * kSortRounds + lane;
+  // every key and index of this thread in flight at once
+  uint32_t kv[kSortRounds], vv[kSortRounds];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t e = e0 + r * 32;
+    kv[r] = e < m ? keys[e] : 0u;
+    vv[r] = e < m ? vals[e] : 0u;
   }
+  uint32_t digit[kSortRounds], rank[kSortRounds];
+  rank_digits(kv, m, (int64_t)chunk * kSortChunk, shift, cnt, digit, rank);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d = threadIdx.x;  // 256 threads, one digit each
+  uint32_t total = 0;
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    const uint32_t c = cnt[w][d];
+    cnt[w][d] = total;  // exclusive prefix over the warps
+    total += c;
+  }
+  volatile unsigned long long* st = status + (size_t)chunk * 256 + d;
+  *st = status_word(pass, chunk == 0, total);
+  uint64_t excl = 0;
+  if (chunk > 0) {
+    // four earlier chunks per step, their words loaded together; the walk
+    // ends at the first inclusive prefix (chunk 0 publishes one at once)
+    constexpr int kLook = 4;
+    const uint64_t t0 = tc::globaltimer_ns();
+    int64_t c = (int64_t)chunk - 1;
+    for (uint32_t it = 1;; ++it) {
+      unsigned long long v[kLook];
+#pragma unroll
+      for (int j = 0; j < kLook; ++j)
+        v[j] = c - j >= 0 ? *(volatile unsigned long long*)(status + (size_t)(c - j) * 256 + d)
+                          : 0ull;
+      bool done = false;
+      int j = 0;
+      for (; j < kLook; ++j) {
+        if ((int)(v[j] >> 61) != pass + 1) break;  // not yet published
+        excl += v[j] & kStatusValue;
+        if (v[j] & kStatusIncl) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      c -= j;
+      if (j == 0 && (it & 63) == 0 &&
+          (tc::globaltimer_ns() - t0 > tc::kWaitLimitNs || it > (1u << 30))) {
+        if (atomicOr(&err->err, kErrTimeout) == 0) atomicExch(&err->timeout_where, kRoleLookback);
+        break;
+      }
+    }
+    *st = status_word(pass, true, excl + total);
+  }
+  // keys of smaller digits: exclusive scan of this pass's histogram
+  const uint32_t gh = ghist[pass * 256 + d];
+  uint32_t inc = gh;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  base[d] = before + inc - gh + (uint32_t)excl;
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     if (digit[r] == 0xffffffffu) continue;
-    const int64_t e = base + (int64_t)warp * 32 * kSortRounds + r * 32 + lane;
-    const uint32_t pos =
-        offs[(int64_t)digit[r] * nchunks + blockIdx.x] + cnt[warp][digit[r]] + rank[r];
-    keys_out[pos] = keys[e];
-    vals_out[pos] = vals[e];
+    const uint32_t pos = base[digit[r]] + cnt[warp][digit[r]] + rank[r];
+    if (pos >= m) continue;  // only after a timed-out wait
+    keys_out[pos] = kv[r];
+    const uint32_t v = vv[r];
+    if (last) {
+      spts[pos] = prepared[v];
+      sw[pos] = wts[v];
+    } else {
+      vals_out[pos] = v;
+    }
   }
 }
 
@@ -155,61 +257,63 @@ __global__ void k_bin_bounds(const uint32_t* __restrict__ skeys, int64_t m, int 
   start[k] = (uint32_t)lo;
 }
 
-__global__ void k_permute(const float4* __restrict__ pts, const float* __restrict__ wts,
-                          const uint32_t* __restrict__ order, int64_t count,
-                          float4* __restrict__ pts_out, float* __restrict__ w_out) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const uint32_t src = order[i];
-    pts_out[i] = pts[src];
-    w_out[i] = wts[src];
-  }
-}
 
-
-// Accumulate one batch's outer products into a thread's eight cells (columns
-// cx, cx+1, rows cy0..cy0+3; acc[2 r + c]): product kernels from tabulated
-// factors, radial kernels from tabulated squared offsets and the profile per
-// pair.  Per point one 8-byte and one 16-byte table read feed eight FMAs.
-template <int KID, bool RADIAL>
+// Accumulate one batch's outer products into a thread's cells: columns cx,
+// cx+1 of RPL rows from cy0 (acc[2 r + c]); RPL = 4 for a whole 16-row
+// block, 1 for a 4-row slice of a heavy block.  Product kernels from
+// tabulated factors, radial kernels from tabulated squared offsets and the
+// profile per pair.  Per point one 8-byte and one 4*RPL-byte table read feed
+// 2*RPL FMAs.
+template <int KID, bool RADIAL, int RPL>
 __device__ __forceinline__ void accumulate(const float (*KX)[kBin], const float (*KY)[kBin],
                                            const float* sW, int cnt, int cx, int cy0,
-                                           float (&acc)[8]) {
+                                           float (&acc)[2 * RPL]) {
+  static_assert(RPL == 4 || RPL == 1, "rows per lane");
+  auto load_y = [&](int c, float (&y)[RPL]) {
+    if constexpr (RPL == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(&KY[c][cy0]);
+      y[0] = v.x;
+      y[1] = v.y;
+      y[2] = v.z;
+      y[3] = v.w;
+    } else {
+      y[0] = KY[c][cy0];
+    }
+  };
   int c = 0;
   if (!RADIAL) {  // two points per step so their table reads are in flight together
     for (; c + 2 <= cnt; c += 2) {
       float2 kx[2];
-      float4 ky[2];
+      float y[2][RPL];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         kx[u] = *reinterpret_cast<const float2*>(&KX[c + u][cx]);
-        ky[u] = *reinterpret_cast<const float4*>(&KY[c + u][cy0]);
+        load_y(c + u, y[u]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const float y[4] = {ky[u].x, ky[u].y, ky[u].z, ky[u].w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          acc[2 * r] = fmaf(kx[u].x, y[r], acc[2 * r]);
-          acc[2 * r + 1] = fmaf(kx[u].y, y[r], acc[2 * r + 1]);
+        for (int r = 0; r < RPL; ++r) {
+          acc[2 * r] = fmaf(kx[u].x, y[u][r], acc[2 * r]);
+          acc[2 * r + 1] = fmaf(kx[u].y, y[u][r], acc[2 * r + 1]);
         }
       }
     }
   }
   for (; c < cnt; ++c) {
     const float2 kx = *reinterpret_cast<const float2*>(&KX[c][cx]);
-    const float4 ky4 = *reinterpret_cast<const float4*>(&KY[c][cy0]);
-    const float y[4] = {ky4.x, ky4.y, ky4.z, ky4.w};
+    float y[RPL];
+    load_y(c, y);
     if (RADIAL) {
       const float w = sW[c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < RPL; ++r) {
         acc[2 * r] = fmaf(w, kradial<KID>(kx.x + y[r]), acc[2 * r]);
         acc[2 * r + 1] = fmaf(w, kradial<KID>(kx.y + y[r]), acc[2 * r + 1]);
       }
     } else {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < RPL; ++r) {
         acc[2 * r] = fmaf(kx.x, y[r], acc[2 * r]);
         acc[2 * r + 1] = fmaf(kx.y, y[r], acc[2 * r + 1]);
       }
@@ -248,16 +352,33 @@ __device__ __forceinline__ int weight_key(uint32_t total) {
   return 1 + 2 * b + (b >= 1 ? (int)((total >> (b - 1)) & 1u) : 0);
 }
 
-// Points within reach of each output block, and the count of blocks per
-// weight class.  The rows' runs are read two at a time so their loads overlap.
+// Blocks with at least 4096 points within reach (weight class 25 and up) of
+// an instance whose supports allow it are computed as four items of four rows
+// each, so a dense cluster's block is spread over four CTAs instead of
+// holding one for the whole launch; their order keys sit above all others, so
+// they come first.  The split depends only on the block's own point count
+// and its instance, so a block is computed the same way in every run and in a
+// batch as on its own.
+constexpr int kHeavyKey = 25;  // weight_key(4096)
+__device__ __forceinline__ int order_key(const CutInst& I, uint32_t total) {
+  const int k = weight_key(total);
+  return I.slice && k >= kHeavyKey ? kCutOrderClasses + k : k;
+}
+
+// Points within reach of each output block, the block's range of sort bins
+// (found once here, in FP64, so the gather itself needs no FP64), and the
+// count of blocks per weight class.  The rows' runs are read two at a time so
+// their loads overlap.
 __global__ void k_cut_block_totals(const CutInst* __restrict__ tab, int ninst,
                                    const uint32_t* __restrict__ start, int nblocks,
-                                   uint32_t* __restrict__ totals, uint32_t* __restrict__ ocount) {
+                                   uint32_t* __restrict__ totals, int4* __restrict__ ranges,
+                                   uint32_t* __restrict__ ocount) {
   const int blk = blockIdx.x * blockDim.x + threadIdx.x;
   if (blk >= nblocks) return;
   int bx, by;
   const CutInst& I = output_block(tab, ninst, blk, bx, by);
   const BinRange br = output_block_bins(I, bx, by);
+  ranges[blk] = make_int4(br.lo_bx, br.hi_bx, br.lo_by, br.hi_by);
   uint32_t total = 0;
   if (!range_empty(br)) {
     int r = br.lo_by;
@@ -274,7 +395,7 @@ __global__ void k_cut_block_totals(const CutInst* __restrict__ tab, int ninst,
     }
   }
   totals[blk] = total;
-  atomicAdd(&ocount[weight_key(total)], 1u);
+  atomicAdd(&ocount[order_key(I, total)], 1u);
 }
 
 // The output blocks in decreasing weight class (a counting sort; within a
@@ -282,7 +403,8 @@ __global__ void k_cut_block_totals(const CutInst* __restrict__ tab, int ninst,
 // own cells, so the order changes the schedule, never a result: the heaviest
 // blocks (dense clusters) start first instead of wherever raster order puts
 // them.
-__global__ void k_cut_order_scatter(const uint32_t* __restrict__ totals, int nblocks,
+__global__ void k_cut_order_scatter(const CutInst* __restrict__ tab, int ninst,
+                                    const uint32_t* __restrict__ totals, int nblocks,
                                     uint32_t* __restrict__ ocount, uint32_t* __restrict__ order) {
   __shared__ uint32_t first[kCutOrderKeys];
   if (threadIdx.x == 0) {
@@ -291,11 +413,14 @@ __global__ void k_cut_order_scatter(const uint32_t* __restrict__ totals, int nbl
       first[k] = acc;
       acc += ocount[k];
     }
+    // the blocks to be split into slices come first; the gather needs their count
+    if (blockIdx.x == 0) ocount[2 * kCutOrderKeys] = first[kCutOrderClasses - 1];
   }
   __syncthreads();
   const int blk = blockIdx.x * blockDim.x + threadIdx.x;
   if (blk >= nblocks) return;
-  const int key = weight_key(__ldg(totals + blk));
+  int bx, by;
+  const int key = order_key(output_block(tab, ninst, blk, bx, by), __ldg(totals + blk));
   order[first[key] + atomicAdd(&ocount[kCutOrderKeys + key], 1u)] = (uint32_t)blk;
 }
 
@@ -307,21 +432,25 @@ struct GroupTables {
   __align__(16) float KY[kBatch][kBin];
 };
 
-// The block's work, for one kernel.  The points that can reach the block are
-// the runs of the sort bins in its range, one run per bin row; their
-// concatenation is cut into kBatch-point batches, and warp g of the CTA takes
-// batches g, g+G, g+2G, ... (fetching the next while computing the current;
-// the warp synchronises only itself) and ends with the two-sum of its eight
-// cells in run.
-template <int KID, bool RADIAL>
+constexpr int kSliceRows = 4;
+constexpr int kSlices = kBin / kSliceRows;  // items per heavy block
+
+// The work of one item, for one kernel: rows y_off..y_off + 4 RPL - 1 of the
+// block (RPL = 4: all 16 rows; RPL = 1: a 4-row slice).  The points that can
+// reach those rows are the runs of the sort bins in range br, one run per bin
+// row; their concatenation is cut into kBatch-point batches, and warp g of
+// the CTA takes batches g, g+G, g+2G, ... (fetching the next while computing
+// the current; the warp synchronises only itself) and ends with the two-sum
+// of its cells in run.
+template <int KID, bool RADIAL, int RPL>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
-                                             int64_t total, int g, int lane, GroupTables& T,
-                                             float2 (&run)[8]) {
+                                             int y_off, const BinRange& br, int64_t total, int g,
+                                             int lane, GroupTables& T, float2 (&run)[2 * RPL]) {
   const int nx = I.nx, ny = I.ny;
   const int x0 = bx * kBin, y0 = by * kBin;
-  const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
+  const int cx = 2 * (lane & 7), cy0 = y_off + RPL * (lane >> 3);
   // table role: column (and row) ej for the points of one parity, c = 2k + half
   constexpr int kEvalPts = kBatch * kBin / kGroupThreads;
   static_assert(kGroupThreads == 2 * kBin && kBatch == kGroupThreads, "table roles");
@@ -329,7 +458,6 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
   if (total == 0) return;
-  const BinRange br = output_block_bins(I, bx, by);
   RunCursor cur;
   cur.init(start, I.bin_begin, I.nbx, br);
   constexpr int64_t kStride = (int64_t)kGroups * kBatch;
@@ -371,46 +499,40 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
       }
     }
     __syncwarp();
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    accumulate<KID, RADIAL>(T.KX, T.KY, T.W, cnt, cx, cy0, acc);
+    float acc[2 * RPL];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) two_sum_acc(run[r], acc[r]);
+    for (int r = 0; r < 2 * RPL; ++r) acc[r] = 0.f;
+    accumulate<KID, RADIAL, RPL>(T.KX, T.KY, T.W, cnt, cx, cy0, acc);
+#pragma unroll
+    for (int r = 0; r < 2 * RPL; ++r) two_sum_acc(run[r], acc[r]);
   }
 }
 
-// One CTA per 16x16-cell output block of some instance (the order list maps
-// CTAs to blocks, heaviest first), kGroups one-warp point groups: a dense
-// block's points are shared out over the groups, whose (hi, lo) sums are
-// added in group order at the end, so results are reproducible.  Blocks of 16
-// cells spread a dense region over many CTAs; the finer sort bins keep the
-// points a block reads close to those its cells' supports actually reach.
-__global__ void __launch_bounds__(kGroups * kGroupThreads)
-    k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
-             const float* __restrict__ W, const uint32_t* __restrict__ start,
-             const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals) {
-  // the groups' tables; after every group is done, their partial sums
-  constexpr size_t kTablesBytes = sizeof(GroupTables) * kGroups;
-  constexpr size_t kPartBytes = sizeof(float2) * kGroups * kGroupThreads * 8;
-  __shared__ __align__(16) unsigned char smem[kTablesBytes > kPartBytes ? kTablesBytes
-                                                                        : kPartBytes];
-  GroupTables* tables = reinterpret_cast<GroupTables*>(smem);
-  float2 (*part)[kGroupThreads][8] = reinterpret_cast<float2 (*)[kGroupThreads][8]>(smem);
-  int bx, by;
-  const int blk = (int)__ldg(order + blockIdx.x);
-  const CutInst& I = output_block(tab, ninst, blk, bx, by);
-  const int64_t total = __ldg(totals + blk);
-  const int g = threadIdx.x / kGroupThreads, lane = threadIdx.x % kGroupThreads;
-  float2 run[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) run[r] = make_float2(0.f, 0.f);
-  GroupTables& T = tables[g];
+// Points of the sort bins in range br (the runs of its bin rows).
+__device__ __forceinline__ uint32_t range_total(const uint32_t* __restrict__ start, int row0,
+                                                int nbx, const BinRange& br) {
+  uint32_t total = 0;
+  if (range_empty(br)) return 0;
+  for (int r = br.lo_by; r <= br.hi_by; ++r) {
+    const uint32_t* a = start + row0 + r * nbx;
+    total += __ldg(a + br.hi_bx + 1) - __ldg(a + br.lo_bx);
+  }
+  return total;
+}
+
+template <int RPL>
+__device__ __forceinline__ void group_dispatch(const CutInst& I, const float4* __restrict__ P,
+                                               const float* __restrict__ W,
+                                               const uint32_t* __restrict__ start, int bx, int by,
+                                               int y_off, const BinRange& br, int64_t total, int g,
+                                               int lane, GroupTables& T, float2 (&run)[2 * RPL]) {
   switch (I.kid) {
-#define KDE_CUT(K)                                                                      \
-  case K:                                                                               \
-    cutoff_group<K, false>(I, P, W, start, bx, by, total, g, lane, T, run);             \
-    break;                                                                              \
-  case kRadial + K:                                                                     \
-    cutoff_group<K, true>(I, P, W, start, bx, by, total, g, lane, T, run);              \
+#define KDE_CUT(K)                                                                       \
+  case K:                                                                                \
+    cutoff_group<K, false, RPL>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run); \
+    break;                                                                               \
+  case kRadial + K:                                                                      \
+    cutoff_group<K, true, RPL>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run);  \
     break;
     KDE_CUT(KDE_UNIFORM)
     KDE_CUT(KDE_TRIANGULAR)
@@ -422,22 +544,107 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
 #undef KDE_CUT
     default: break;
   }
-  __syncthreads();  // every group is done with its tables
+}
+
+// One CTA of kGroups one-warp point groups per item: first the four slices of
+// every heavy block, then the other blocks, each in the order list's
+// heaviest-first order (CTAs past the last item return at once).  A whole
+// block's eight cells per thread, or a slice's two, are summed over the groups
+// in group order at the end, so every cell is computed by one CTA in a fixed
+// order and results are reproducible bit for bit.  Blocks of 16 cells spread a
+// dense region over many CTAs; the finer sort bins keep the points an item
+// reads close to those its cells' supports actually reach.
+__global__ void __launch_bounds__(kGroups * kGroupThreads)
+    k_cutoff(const CutInst* __restrict__ tab, int ninst, const float4* __restrict__ P,
+             const float* __restrict__ W, const uint32_t* __restrict__ start,
+             const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals,
+             const int4* __restrict__ ranges, const uint32_t* __restrict__ heavy_count,
+             int nblocks) {
+  // the groups' tables; after every group is done, their partial sums
+  constexpr size_t kTablesBytes = sizeof(GroupTables) * kGroups;
+  constexpr size_t kPartBytes = sizeof(float2) * kGroups * kGroupThreads * 8;
+  __shared__ __align__(16) unsigned char smem[kTablesBytes > kPartBytes ? kTablesBytes
+                                                                        : kPartBytes];
+  __shared__ int4 s_rg;
+  __shared__ uint32_t s_total;
+  GroupTables* tables = reinterpret_cast<GroupTables*>(smem);
+  float2 (*part)[8][kGroupThreads] = reinterpret_cast<float2 (*)[8][kGroupThreads]>(smem);
+  const int g = threadIdx.x / kGroupThreads, lane = threadIdx.x % kGroupThreads;
+  GroupTables& T = tables[g];
+  const int64_t heavy = __ldg(heavy_count);
+  const int64_t item = blockIdx.x;
+  if (item >= (int64_t)nblocks + (int64_t)(kSlices - 1) * heavy) return;
+  {
+    int64_t pos;
+    int slice;
+    if (item < kSlices * heavy) {
+      pos = item / kSlices;
+      slice = (int)(item % kSlices);
+    } else {
+      pos = heavy + (item - kSlices * heavy);
+      slice = -1;
+    }
+    const int blk = (int)__ldg(order + pos);
+    int bx, by;
+    const CutInst& I = output_block(tab, ninst, blk, bx, by);
+    if (threadIdx.x == 0) {
+      if (slice < 0) {
+        s_rg = __ldg(ranges + blk);
+        s_total = __ldg(totals + blk);
+      } else {  // the slice's own bin range and point count
+        const BinRange b = block_bins_rect(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby,
+                                           bx * kBin, by * kBin + slice * kSliceRows, kBin,
+                                           kSliceRows);
+        s_rg = make_int4(b.lo_bx, b.hi_bx, b.lo_by, b.hi_by);
+        s_total = range_total(start, I.bin_begin, I.nbx, b);
+      }
+    }
+    __syncthreads();
+    const int4 rg = s_rg;
+    const BinRange br = {rg.x, rg.y, rg.z, rg.w};
+    const int64_t total = s_total;
+    if (slice < 0) {
+      float2 run[8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) part[g][lane][r] = run[r];
-  __syncthreads();
-  if (g == 0) {
-    const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
+      for (int r = 0; r < 8; ++r) run[r] = make_float2(0.f, 0.f);
+      group_dispatch<4>(I, P, W, start, bx, by, 0, br, total, g, lane, T, run);
+      __syncthreads();  // every group is done with its tables
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float2 sum = part[0][lane][r];
+      for (int r = 0; r < 8; ++r) part[g][r][lane] = run[r];
+      __syncthreads();
+      // group g combines cell r = g of every thread's eight, over the groups in
+      // order (the same order for every block and run)
+      static_assert(kGroups == 8, "one cell of eight per group");
+      const int r = g;
+      const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
+      float2 sum = part[0][r][lane];
+#pragma unroll
       for (int h = 1; h < kGroups; ++h) {
-        const float2 o = part[h][lane][r];
+        const float2 o = part[h][r][lane];
         two_sum_acc(sum, o.x);
         sum.y += o.y;
       }
       const int x = bx * kBin + cx + (r & 1), y = by * kBin + cy0 + (r >> 1);
       if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
+    } else {
+      float2 run[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      group_dispatch<1>(I, P, W, start, bx, by, slice * kSliceRows, br, total, g, lane, T, run);
+      __syncthreads();
+      part[g][0][lane] = run[0];
+      part[g][1][lane] = run[1];
+      __syncthreads();
+      if (threadIdx.x < 2 * kGroupThreads) {  // 64 cells, one thread each
+        const int l = threadIdx.x >> 1, r = threadIdx.x & 1;
+        float2 sum = part[0][r][l];
+#pragma unroll
+        for (int h = 1; h < kGroups; ++h) {
+          const float2 o = part[h][r][l];
+          two_sum_acc(sum, o.x);
+          sum.y += o.y;
+        }
+        const int x = bx * kBin + 2 * (l & 7) + r, y = by * kBin + slice * kSliceRows + (l >> 3);
+        if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
+      }
     }
   }
 }
@@ -475,8 +682,10 @@ CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {
   int bits = 1;
   while ((1ll << bits) <= (long long)total_bins) ++bits;  // keys 0..total_bins
   z.passes = (bits + 7) / 8;
-  z.hist_words = (size_t)256 * z.nchunks;
-  z.scan_words = scan_temp_words((int64_t)z.hist_words, 2048);
+  // look-back status (one 64-bit word per chunk and digit), the per-pass
+  // digit histograms and the per-pass chunk counters, cleared together
+  z.hist_words = (size_t)2 * 256 * z.nchunks + (size_t)kMaxPasses * 256 + kMaxPasses;
+  z.scan_words = 0;
   return z;
 }
 
@@ -484,22 +693,23 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
                             const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                             CutoffScratch ws, cudaStream_t s) {
   if (ninst <= 0 || m <= 0) return cudaSuccess;
-  k_bin_keys<<<grid_for(m), 256, 0, s>>>(tab, ninst, m, prepared, (uint32_t)total_bins,
-                                         ws.keys[0], ws.vals[0]);
-  note_launches(1);
-  cudaError_t e = cudaGetLastError();
+  if (z.passes < 1 || z.passes > kMaxPasses) return cudaErrorInvalidValue;
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(ws.hist);
+  uint32_t* ghist = ws.hist + (size_t)2 * 256 * z.nchunks;
+  uint32_t* chunk_ctr = ghist + kMaxPasses * 256;
+  cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * z.hist_words, s);
   if (e != cudaSuccess) return e;
+  k_bin_keys<<<grid_for(m), 256, 0, s>>>(tab, ninst, m, prepared, (uint32_t)total_bins, z.passes,
+                                         ws.keys[0], ws.vals[0], ghist);
+  note_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int cur = 0;
   for (int pass = 0; pass < z.passes; ++pass) {
-    const int shift = 8 * pass;
-    k_radix_count<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], m, shift, z.nchunks, ws.hist);
-    note_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_exclusive_scan(ws.hist, ws.hist_scan, (int64_t)z.hist_words, 2048, ws.scan_temp, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, shift,
-                                                        z.nchunks, ws.hist_scan, ws.keys[cur ^ 1],
-                                                        ws.vals[cur ^ 1]);
+    const int last = pass == z.passes - 1;
+    k_radix_pass<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, pass, ghist,
+                                                    chunk_ctr, status, ws.keys[cur ^ 1],
+                                                    ws.vals[cur ^ 1], prepared, prepared_w, ws.spts,
+                                                    ws.sw, last, ws.err);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cur ^= 1;
@@ -507,23 +717,27 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
   k_bin_bounds<<<(int)((total_bins + 1 + 255) / 256), 256, 0, s>>>(ws.keys[cur], m,
                                                                    (int)total_bins, ws.start);
   note_launches(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_permute<<<grid_for(m), 256, 0, s>>>(prepared, prepared_w, ws.vals[cur], m, ws.spts, ws.sw);
-  note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
+cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins, int64_t slice_bins,
                                const CutoffScratch& ws, cudaStream_t s) {
   if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
   if (cut_bins > 0x7fffffff) return cudaErrorInvalidValue;
   const int nb = (int)cut_bins, grid = (nb + 255) / 256;
-  cudaError_t e = cudaMemsetAsync(ws.ocount, 0, sizeof(uint32_t) * 2 * kCutOrderKeys, s);
+  // per-key counts and cursors of the order, then the gather's item counter
+  cudaError_t e = cudaMemsetAsync(ws.ocount, 0, sizeof(uint32_t) * kCutOcountWords, s);
   if (e != cudaSuccess) return e;
-  k_cut_block_totals<<<grid, 256, 0, s>>>(tab, ninst, ws.start, nb, ws.totals, ws.ocount);
-  k_cut_order_scatter<<<grid, 256, 0, s>>>(ws.totals, nb, ws.ocount, ws.order);
-  k_cutoff<<<(unsigned)nb, kGroups * kGroupThreads, 0, s>>>(tab, ninst, ws.spts, ws.sw,
-                                                             ws.start, ws.order, ws.totals);
+  k_cut_block_totals<<<grid, 256, 0, s>>>(tab, ninst, ws.start, nb, ws.totals, ws.ranges,
+                                          ws.ocount);
+  k_cut_order_scatter<<<grid, 256, 0, s>>>(tab, ninst, ws.totals, nb, ws.ocount, ws.order);
+  // one CTA per item: every block, plus three more slices for each block of a
+  // slicing instance that may turn out heavy
+  const int64_t ctas = (int64_t)nb + (int64_t)(kSlices - 1) * slice_bins;
+  if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
+  k_cutoff<<<(unsigned)ctas, kGroups * kGroupThreads, 0, s>>>(
+      tab, ninst, ws.spts, ws.sw, ws.start, ws.order, ws.totals, ws.ranges,
+      ws.ocount + 2 * kCutOrderKeys, nb);
   note_launches(3);
   return cudaGetLastError();
 }

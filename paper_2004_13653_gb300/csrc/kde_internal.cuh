@@ -123,23 +123,29 @@ struct TcInst {
 };
 
 // Points of bin rows lo_by..hi_by, columns lo_bx..hi_bx can reach the block
-// of side x side cells whose first cell is (cx0, cy0): every other point lies
+// of w x h cells whose first cell is (cx0, cy0): every other point lies
 // farther than `reach` (prepared units) from each of the block's cell centres
 // along x or along y.  Used by the kernels that plan work and those that do it,
 // so the two agree bit for bit.  An empty range has lo > hi.
 struct BinRange {
   int lo_bx, hi_bx, lo_by, hi_by;
 };
-__host__ __device__ inline BinRange block_bins(double cs, double reach, double inv_binw, int nbx,
-                                               int nby, int cx0, int cy0, int side) {
+__host__ __device__ inline BinRange block_bins_rect(double cs, double reach, double inv_binw,
+                                                    int nbx, int nby, int cx0, int cy0, int w,
+                                                    int h) {
   BinRange r;
-  const double x0 = ((double)cx0 + 0.5) * cs - reach, x1 = ((double)cx0 + side - 0.5) * cs + reach;
-  const double y0 = ((double)cy0 + 0.5) * cs - reach, y1 = ((double)cy0 + side - 0.5) * cs + reach;
+  const double x0 = ((double)cx0 + 0.5) * cs - reach, x1 = ((double)cx0 + w - 0.5) * cs + reach;
+  const double y0 = ((double)cy0 + 0.5) * cs - reach, y1 = ((double)cy0 + h - 0.5) * cs + reach;
   r.lo_bx = (int)fmin((double)nbx, fmax(0.0, floor(x0 * inv_binw)));
   r.hi_bx = (int)fmin((double)(nbx - 1), floor(x1 * inv_binw));
   r.lo_by = (int)fmin((double)nby, fmax(0.0, floor(y0 * inv_binw)));
   r.hi_by = (int)fmin((double)(nby - 1), floor(y1 * inv_binw));
   return r;
+}
+// the same for a block of side x side cells
+__host__ __device__ inline BinRange block_bins(double cs, double reach, double inv_binw, int nbx,
+                                               int nby, int cx0, int cy0, int side) {
+  return block_bins_rect(cs, reach, inv_binw, nbx, nby, cx0, cy0, side, side);
 }
 // the 256 x 256 tile (tm, tn) of the tensor-core paths
 __host__ __device__ inline BinRange tile_bins(double cs, double reach, double inv_binw, int nbx,
@@ -229,6 +235,10 @@ struct CutInst {
   int nbx, nby, bin_begin, nx, ny, kid;
   int obx, oby, out_begin;
   float scale;
+  // heavy output blocks (4096 or more points within reach) are computed as
+  // four 4-row slices: set for supports of at most 6 cells (4-cell sort bins),
+  // where a slice reads about half of the block's points
+  int slice;
 };
 
 struct ReduceInst {
@@ -310,10 +320,17 @@ struct CutoffScratch {
   float* sw;
   uint32_t* order;  // [cutoff output blocks] the blocks, heaviest first
   uint32_t* totals; // [cutoff output blocks] points within reach of each block
-  uint32_t* ocount; // [2 * kCutOrderKeys] per-key block counts and cursors
+  int4* ranges;     // [cutoff output blocks] each block's sort-bin range (BinRange)
+  uint32_t* ocount; // [kCutOcountWords] per-key block counts and cursors, blocks to split
+  CallScalars* err; // where a timed-out wait of the sort's look-back is recorded
 };
-// Weight classes of the cutoff path's output blocks (by points within reach).
-constexpr int kCutOrderKeys = 66;
+// Weight classes of the cutoff path's output blocks (by points within reach:
+// 66 classes, and the same again above them for the heavy blocks the gather
+// splits into row slices); the ocount scratch holds their counts, their
+// cursors and the number of blocks to be split.
+constexpr int kCutOrderClasses = 66;
+constexpr int kCutOrderKeys = 2 * kCutOrderClasses;
+constexpr int kCutOcountWords = 2 * kCutOrderKeys + 1;
 struct CutoffSizes {
   int nchunks, passes;
   size_t hist_words, scan_words;
@@ -321,12 +338,17 @@ struct CutoffSizes {
 CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
 // Keys, stable radix sort, bin starts and the permuted points for every
 // instance of `tab` (cutoff instances and block-sparse tensor-core instances).
+// One kernel computes the keys and the digit histograms of every pass; each
+// 8-bit pass is then one kernel whose chunk offsets come from a decoupled
+// look-back (bounded waits, recorded in ws.err); the last pass writes the
+// permuted points.  ws.hist holds z.hist_words words of look-back state.
 cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
                             const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                             CutoffScratch ws, cudaStream_t s);
 // The cutoff evaluation of the first ninst instances (output blocks
-// 0..cut_bins-1, one CTA each).
-cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins,
+// 0..cut_bins-1, of which slice_bins belong to instances with CutInst::slice
+// set): one CTA per block, or per 4-row slice of a heavy block.
+cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins, int64_t slice_bins,
                                const CutoffScratch& ws, cudaStream_t s);
 
 // Adjoint of the Gaussian density (points prepared with sigma = 1/h) and the

@@ -177,3 +177,47 @@ def test_points_on_sort_bin_edges_far_from_origin(kid):
     ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
     assert np.max(ref) > 0
     assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
+
+
+def _heavy_cluster(seed, kid, h_cells, n=30_000, dense=20_000):
+    """n points on a ragged 150 x 120 grid of 10 m cells, `dense` of them in a
+    180 m square that straddles output-block borders: the blocks there have
+    4096 points or more within reach, and for supports of up to 6 cells they
+    are computed as four 4-row slices."""
+    cell = 10.0
+    wl = workloads.random_points(seed, n, 1600.0, cell, 150, 120, h_cells * cell, kid % oracle.RADIAL)
+    rng = np.random.default_rng(seed + 1)
+    wl.local[:dense] = rng.uniform([470.0, 310.0], [650.0, 490.0], size=(dense, 2))
+    return wl
+
+
+@pytest.mark.parametrize("h_cells", [1.0, 3.5, 12.0, 30.0])
+@pytest.mark.parametrize("kid", [oracle.EPANECHNIKOV, oracle.RADIAL + oracle.TRICUBE],
+                         ids=["epanechnikov", "radial_tricube"])
+def test_heavy_blocks_in_row_slices(h_cells, kid):
+    """Heavy blocks next to light ones against the oracle on the whole grid:
+    split into row slices, each with its own range of sort bins, at h = 1
+    and 3.5 cells (4-cell sort bins); whole at 12 and 30 cells (8- and
+    16-cell sort bins)."""
+    wl = _heavy_cluster(585 + int(h_cells), kid, h_cells)
+    F = run_gpu(wl, kid)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+    assert rel_linf(F, ref) <= TOL_FP32
+
+
+def test_heavy_blocks_reproducible_and_same_in_a_batch():
+    """A block's split into slices depends only on its own point count: the
+    result is the same bits run after run and inside a batch."""
+    kid = oracle.QUARTIC
+    wl = _heavy_cluster(590, kid, 3.0)
+    other = workloads.random_points(591, 5000, 900.0, 7.5, 97, 61, 20.0, oracle.EPANECHNIKOV)
+    a = run_gpu(wl, kid)
+    assert np.array_equal(a, run_gpu(wl, kid))
+
+    def inst(x, k):
+        return dict(points=torch.as_tensor(x.xy, dtype=torch.float64, device="cuda"),
+                    weights=torch.as_tensor(x.w, dtype=torch.float32, device="cuda"),
+                    origin=x.origin, cell=x.cell, nx=x.nx, ny=x.ny, h=x.h, kernel=k)
+    outs = kde.grid_batched([inst(other, oracle.EPANECHNIKOV), inst(wl, kid)], flags=kde.FLAG_SYNC)
+    assert np.array_equal(outs[1].cpu().numpy(), a)
+    assert np.array_equal(outs[0].cpu().numpy(), run_gpu(other, oracle.EPANECHNIKOV))
