@@ -144,6 +144,8 @@ def parse():
     ap.add_argument("--simt-grid", type=int, default=4096,
                     help="grid side for the FP32 SIMT comparison (same points; 0 = skip)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batch leg")
+    ap.add_argument("--no-configs12", action="store_true",
+                    help="skip the legs of the 2,000-fix and 1M-fix workloads")
     ap.add_argument("--no-lscv", action="store_true", help="skip the LSCV bandwidth-fit leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adjoint-only", action="store_true",
@@ -517,10 +519,13 @@ def run_ours(args):
 
     if rank == 0 and args.extra:
         result["binned_estimator"] = binned_leg(dev, wl, xy_dev, origin, out_dev)
-    if rank == 0 and not (args.no_batched and args.no_lscv and args.no_adjoint and not args.extra):
+    if rank == 0 and not (args.no_batched and args.no_lscv and args.no_adjoint and
+                          args.no_configs12 and not args.extra):
         del lonlat_dev, xy_dev, out_dev
         torch.cuda.empty_cache()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        if not args.no_configs12:
+            result["configs12"] = configs12_leg(dev, peaks, sms, local)
         if not args.no_batched:
             result["batched"] = batched_leg(dev, peaks, sms, local)
         if not args.no_lscv:
@@ -607,6 +612,80 @@ def alu_peak_pairs(peaks, sms):
     128 FP32 lanes per SM per clock."""
     clk_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
     return sms * clk_hz * min(128 / 1.14, 16 / (6144 / (32 * 8192)))
+
+
+def configs12_leg(dev, peaks, sms, local):
+    """Configs 1 and 2 on their own: the 2,000-fix Gaussian on 64^2 through the
+    FP32 SIMT path against the oracle on every cell, and the 1M lane fixes on
+    1024^2 (h = 150 m) with the Gaussian on the FP32 SIMT path and on the
+    split-FP16 tensor path and the Epanechnikov on the cutoff path, each timed
+    as a whole call (device-resident inputs; centring, sort and reduce
+    included) and checked on sampled cells."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2004_13653_gb300 as kde
+    import workloads
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from kde_testutil import sample_cells
+
+    def err(F, ref):
+        return float(np.max(np.abs(F - ref)) / np.max(np.abs(ref)))
+
+    out = {}
+    c1 = workloads.config1()
+    xy1 = torch.as_tensor(c1.xy, dtype=torch.float64, device=dev)
+    run1 = lambda: kde.grid(xy1, None, c1.origin, c1.cell, c1.nx, c1.ny, c1.h, "gaussian",
+                            path="simt")
+    ms1 = _time(run1, reps=20)
+    ref1 = oracle.kde_grid(c1.xy, c1.w, c1.origin, c1.cell, c1.nx, c1.ny, c1.h, oracle.GAUSSIAN)
+    out["config1_simt_fp32"] = {"points": c1.n, "grid": [c1.nx, c1.ny], "ms_per_call": ms1,
+                                "rel_linf_vs_oracle_all_cells": err(run1().cpu().numpy(), ref1)}
+    c2 = workloads.config2()
+    xy2 = torch.as_tensor(c2.xy, dtype=torch.float64, device=dev)
+    evals = float(c2.n) * c2.nx * c2.ny
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    res = {}
+    for name, kernel, path, reps in (("gaussian_simt_fp32", "gaussian", "simt", 2),
+                                     ("gaussian_tc_split16", "gaussian", "tc_split16", 5),
+                                     ("epanechnikov_cutoff", "epanechnikov", "cutoff", 20)):
+        call = lambda: kde.grid(xy2, None, c2.origin, c2.cell, c2.nx, c2.ny, c2.h, kernel,
+                                path=path)
+        res[name] = (_time(call, reps=reps), call().cpu().numpy())
+    clk = clocks.stop()
+    for kid, names in ((oracle.GAUSSIAN, ("gaussian_simt_fp32", "gaussian_tc_split16")),
+                       (oracle.EPANECHNIKOV, ("epanechnikov_cutoff",))):
+        cells = sample_cells(res[names[-1]][1], 256, seed=12)
+        ref = oracle.kde_cells(c2.xy, c2.w, c2.origin, c2.cell, c2.nx, c2.ny, c2.h, kid, cells,
+                               threads=os.cpu_count() or 1)
+        for name in names:
+            ms, F = res[name]
+            out[f"config2_{name}"] = {"ms_per_call": ms, "value": evals / ms / 1e6, "unit": UNIT,
+                                      "rel_linf_vs_oracle_on_sample":
+                                          err(F.reshape(-1)[cells], ref)}
+    tc = out["config2_gaussian_tc_split16"]
+    tflops = 6.0 * evals / (tc["ms_per_call"] * 1e-3) / 1e12
+    tc["roofline"] = {"bound": "tensor", "achieved": tflops,
+                      "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                      "frac": tflops / peaks["bf16_tflops_sustained"],
+                      "note": "whole call: centring, contraction and split-K reduce"}
+    tc["vs_simt"] = out["config2_gaussian_simt_fp32"]["ms_per_call"] / tc["ms_per_call"]
+    cut = out["config2_epanechnikov_cutoff"]
+    pairs = cutoff_pairs(c2.xy, c2.origin, c2.cell, c2.nx, c2.ny, c2.h)
+    peak_a = alu_peak_pairs(peaks, sms)
+    cut["roofline"] = {"bound": "alu", "achieved": pairs / (cut["ms_per_call"] * 1e-3) / 1e12,
+                       "peak": peak_a / 1e12, "unit": "Tpair/s",
+                       "frac": pairs / (cut["ms_per_call"] * 1e-3) / peak_a,
+                       "note": "evaluated pairs (16x16-cell blocks x points of the sort bins "
+                               "within reach) over the whole call"}
+    out["config2_points"] = c2.n
+    out["clocks"] = clk
+    del xy1, xy2
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_leg(dev, peaks, sms, local):
