@@ -42,6 +42,9 @@ def test_adjoint_matches_oracle_vjp():
     rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, G)
     assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
     assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    # each component of at least a tenth of the largest, against itself
+    assert _rel_per_point(gw.cpu().numpy(), rw) <= 10 * TOL_GRAD
+    assert _rel_per_point(gxy.cpu().numpy(), rxy) <= 10 * TOL_GRAD
     assert gh == pytest.approx(rh, rel=TOL_GRAD)
 
 
@@ -71,6 +74,8 @@ def test_adjoint_narrow_windows(h_cells, n):
     rw, rxy, rh = oracle.kde_vjp_gauss(wl.xy, wl.w, wl.origin, wl.cell, 60, 50, wl.h, G)
     assert rel_linf(gw.cpu().numpy(), rw) <= TOL_GRAD
     assert rel_linf(gxy.cpu().numpy(), rxy) <= TOL_GRAD
+    assert _rel_per_point(gw.cpu().numpy(), rw) <= 10 * TOL_GRAD
+    assert _rel_per_point(gxy.cpu().numpy(), rxy) <= 10 * TOL_GRAD
     assert gh == pytest.approx(rh, rel=TOL_GRAD)
 
 
