@@ -37,6 +37,19 @@ int kde_diag_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, int pe
 int kde_diag_wait_timeout(int64_t limit_ns, void* stream);
 
 /*
+ * kde_diag_sort_wait_timeout — exercises the bounded wait of the bin sort's
+ * look-back (no counterpart in the paper; the sort orders the points of the
+ * cutoff path, Sec. III-C with Eq. 8, and of the block-sparse path): one
+ * radix pass over 4096 zero keys runs as the second of two chunks while the
+ * first never publishes its counts, so the pass gives up after limit_ns
+ * nanoseconds, records the timeout (role 31), keeps every position it writes
+ * inside its buffers and returns, leaving the context usable.  Returns
+ * KDE_ETIMEOUT (the expected outcome), or KDE_EINVAL for a limit outside
+ * [1 us, 2 s].  Synchronous; uses the library workspace.
+ */
+int kde_diag_sort_wait_timeout(int64_t limit_ns, void* stream);
+
+/*
  * kde_diag_peak_rates — measures, at the clock the GPU runs at, the rates the
  * rooflines of the tensor-core and exp-bound kernels are set against (no
  * counterpart in the paper): rates[0] = tcgen05 kind::f16 MMAs on CTA pairs

@@ -63,7 +63,8 @@ EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_grid_backward", "kde_lscv_grid",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
            "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
-           "kde_grid_binned", "kde_dp_simplify", "kde_diag_peak_rates")
+           "kde_grid_binned", "kde_dp_simplify", "kde_diag_peak_rates",
+           "kde_diag_sort_wait_timeout")
 
 _lib = None
 
@@ -121,6 +122,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_dp_simplify.restype = i32
     lib.kde_diag_wait_timeout.argtypes = [i64, vp]
     lib.kde_diag_wait_timeout.restype = i32
+    lib.kde_diag_sort_wait_timeout.argtypes = [i64, vp]
+    lib.kde_diag_sort_wait_timeout.restype = i32
     lib.kde_diag_peak_rates.argtypes = [P(ctypes.c_double * 3), vp]
     lib.kde_diag_peak_rates.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]

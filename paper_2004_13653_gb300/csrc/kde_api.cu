@@ -1448,6 +1448,27 @@ int kde_diag_wait_timeout(int64_t limit_ns, void* stream) {
   return KDE_OK;
 }
 
+int kde_diag_sort_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 2000000000ll)
+    return fail(KDE_EINVAL, "limit_ns must be in [1 us, 2 s]");
+  void* ws = nullptr;
+  const size_t o_buf = align256(sizeof(CallScalars));
+  int rc = library_workspace(o_buf + sizeof(uint32_t) * lookback_probe_words(), &ws);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CallScalars* scal = static_cast<CallScalars*>(ws);
+  uint32_t* buf = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + o_buf);
+  KDE_CUDA(cudaMemsetAsync(scal, 0, sizeof(CallScalars), s), "clear scalars");
+  KDE_CUDA(launch_lookback_timeout_probe(buf, scal, (uint64_t)limit_ns, s), "look-back diagnostic");
+  CallScalars hs;
+  KDE_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s), "read status");
+  KDE_CUDA(cudaStreamSynchronize(s), "synchronize");
+  if (hs.err & kErrTimeout)
+    return fail(KDE_ETIMEOUT, "a device-side wait gave up (role %d)", hs.timeout_where);
+  g_err[0] = 0;
+  return KDE_OK;
+}
+
 int kde_diag_peak_rates(double* rates, void* stream) {
   if (!rates) return fail(KDE_EINVAL, "null pointer");
   void* ws = nullptr;

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kSortThreads)
                  unsigned long long* __restrict__ status, uint32_t* __restrict__ keys_out,
                  uint32_t* __restrict__ vals_out, const float4* __restrict__ prepared,
                  const float* __restrict__ wts, float4* __restrict__ spts, float* __restrict__ sw,
-                 int last, CallScalars* __restrict__ err) {
+                 int last, CallScalars* __restrict__ err, uint64_t limit_ns) {
   __shared__ uint32_t cnt[kSortThreads / 32][256];
   __shared__ uint32_t base[256];
   __shared__ uint32_t wsum[kSortThreads / 32];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kSortThreads)
       if (done) break;
       c -= j;
       if (j == 0 && (it & 63) == 0 &&
-          (tc::globaltimer_ns() - t0 > tc::kWaitLimitNs || it > (1u << 30))) {
+          (tc::globaltimer_ns() - t0 > limit_ns || it > (1u << 30))) {
         if (atomicOr(&err->err, kErrTimeout) == 0) atomicExch(&err->timeout_where, kRoleLookback);
         break;
       }
@@ -424,6 +424,40 @@ __global__ void k_cut_order_scatter(const CutInst* __restrict__ tab, int ninst,
   order[first[key] + atomicAdd(&ocount[kCutOrderKeys + key], 1u)] = (uint32_t)blk;
 }
 
+// The RunCursor walk with 32-bit positions (a block's or slice's reach list
+// and the sorted points number fewer than 2^32): fewer registers in the
+// gather, whose occupancy its register count sets.
+struct RunCursor32 {
+  const uint32_t* row;  // start + row0 + by * nbx
+  int nbx, lo_bx, hi_bx, by, hi_by;
+  uint32_t vr, ra, rb;
+  __device__ __forceinline__ void load_run() {
+    ra = __ldg(row + lo_bx);
+    rb = __ldg(row + hi_bx + 1);
+  }
+  __device__ __forceinline__ void init(const uint32_t* start, int row0, int nbx_,
+                                       const BinRange& br) {
+    nbx = nbx_;
+    lo_bx = br.lo_bx;
+    hi_bx = br.hi_bx;
+    by = br.lo_by;
+    hi_by = br.hi_by;
+    row = start + row0 + by * nbx;
+    vr = 0;
+    load_run();
+  }
+  // index of position v (v below the range's total, not decreasing)
+  __device__ __forceinline__ uint32_t map(uint32_t v) {
+    while (v >= vr + (rb - ra) && by < hi_by) {
+      vr += rb - ra;
+      ++by;
+      row += nbx;
+      load_run();
+    }
+    return ra + (v - vr);
+  }
+};
+
 // Shared-memory tables of one point group.
 struct GroupTables {
   float4 P[kBatch];
@@ -433,6 +467,9 @@ struct GroupTables {
 };
 
 constexpr int kSliceRows = 4;
+// dynamic shared memory of the gather: the groups' tables, then their running sums
+constexpr size_t kCutTablesBytes = sizeof(GroupTables) * kGroups;
+constexpr size_t kCutSmemBytes = kCutTablesBytes + sizeof(float2) * kGroups * 8 * kGroupThreads;
 constexpr int kSlices = kBin / kSliceRows;  // items per heavy block
 
 // The work of one item, for one kernel: rows y_off..y_off + 4 RPL - 1 of the
@@ -440,14 +477,16 @@ constexpr int kSlices = kBin / kSliceRows;  // items per heavy block
 // reach those rows are the runs of the sort bins in range br, one run per bin
 // row; their concatenation is cut into kBatch-point batches, and warp g of
 // the CTA takes batches g, g+G, g+2G, ... (fetching the next while computing
-// the current; the warp synchronises only itself) and ends with the two-sum
-// of its cells in run.
+// the current; the warp synchronises only itself) and adds each batch into
+// the (hi, lo) running sums of its cells with a two-sum; the running sums
+// live in shared memory (run[r * 32] for cell r of this lane), which keeps
+// the kernel at 64 registers and four CTAs per SM.
 template <int KID, bool RADIAL, int RPL>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
                                              int y_off, const BinRange& br, int64_t total, int g,
-                                             int lane, GroupTables& T, float2 (&run)[2 * RPL]) {
+                                             int lane, GroupTables& T, float2* run) {
   const int nx = I.nx, ny = I.ny;
   const int x0 = bx * kBin, y0 = by * kBin;
   const int cx = 2 * (lane & 7), cy0 = y_off + RPL * (lane >> 3);
@@ -458,27 +497,28 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
   if (total == 0) return;
-  RunCursor cur;
+  RunCursor32 cur;
   cur.init(start, I.bin_begin, I.nbx, br);
-  constexpr int64_t kStride = (int64_t)kGroups * kBatch;
-  int64_t v = (int64_t)g * kBatch + lane;  // this lane's point of the warp's current batch
+  constexpr uint32_t kStride = kGroups * kBatch;
+  const uint32_t total32 = (uint32_t)total;
+  uint32_t v = g * kBatch + lane;  // this lane's point of the warp's current batch
   float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
   float wf = 0.f;
-  if (v < total) {
-    const int64_t p = cur.map(v);
+  if (v < total32) {
+    const uint32_t p = cur.map(v);
     pf = P[p];
     wf = W[p];
   }
-  for (int64_t b0 = (int64_t)g * kBatch; b0 < total; b0 += kStride, v += kStride) {
-    const int cnt = (int)min((int64_t)kBatch, total - b0);
+  for (uint32_t b0 = g * kBatch; b0 < total32; b0 += kStride, v += kStride) {
+    const int cnt = (int)min((uint32_t)kBatch, total32 - b0);
     __syncwarp();  // the warp's previous batch is consumed
     if (lane < cnt) {
       T.P[lane] = pf;
       T.W[lane] = wf;
     }
     __syncwarp();
-    if (v + kStride < total) {  // next batch, in flight
-      const int64_t p = cur.map(v + kStride);
+    if (v + kStride < total32) {  // next batch, in flight
+      const uint32_t p = cur.map(v + kStride);
       pf = P[p];
       wf = W[p];
     }
@@ -504,7 +544,11 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
     for (int r = 0; r < 2 * RPL; ++r) acc[r] = 0.f;
     accumulate<KID, RADIAL, RPL>(T.KX, T.KY, T.W, cnt, cx, cy0, acc);
 #pragma unroll
-    for (int r = 0; r < 2 * RPL; ++r) two_sum_acc(run[r], acc[r]);
+    for (int r = 0; r < 2 * RPL; ++r) {
+      float2 x = run[r * kGroupThreads];
+      two_sum_acc(x, acc[r]);
+      run[r * kGroupThreads] = x;
+    }
   }
 }
 
@@ -525,7 +569,7 @@ __device__ __forceinline__ void group_dispatch(const CutInst& I, const float4* _
                                                const float* __restrict__ W,
                                                const uint32_t* __restrict__ start, int bx, int by,
                                                int y_off, const BinRange& br, int64_t total, int g,
-                                               int lane, GroupTables& T, float2 (&run)[2 * RPL]) {
+                                               int lane, GroupTables& T, float2* run) {
   switch (I.kid) {
 #define KDE_CUT(K)                                                                       \
   case K:                                                                                \
@@ -560,15 +604,14 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
              const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals,
              const int4* __restrict__ ranges, const uint32_t* __restrict__ heavy_count,
              int nblocks) {
-  // the groups' tables; after every group is done, their partial sums
-  constexpr size_t kTablesBytes = sizeof(GroupTables) * kGroups;
-  constexpr size_t kPartBytes = sizeof(float2) * kGroups * kGroupThreads * 8;
-  __shared__ __align__(16) unsigned char smem[kTablesBytes > kPartBytes ? kTablesBytes
-                                                                        : kPartBytes];
+  // the groups' tables, then their running sums (cell r of lane l of group g
+  // at part[g][r][l])
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_rg;
   __shared__ uint32_t s_total;
   GroupTables* tables = reinterpret_cast<GroupTables*>(smem);
-  float2 (*part)[8][kGroupThreads] = reinterpret_cast<float2 (*)[8][kGroupThreads]>(smem);
+  float2 (*part)[8][kGroupThreads] =
+      reinterpret_cast<float2 (*)[8][kGroupThreads]>(smem + kCutTablesBytes);
   const int g = threadIdx.x / kGroupThreads, lane = threadIdx.x % kGroupThreads;
   GroupTables& T = tables[g];
   const int64_t heavy = __ldg(heavy_count);
@@ -604,14 +647,10 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
     const BinRange br = {rg.x, rg.y, rg.z, rg.w};
     const int64_t total = s_total;
     if (slice < 0) {
-      float2 run[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) run[r] = make_float2(0.f, 0.f);
-      group_dispatch<4>(I, P, W, start, bx, by, 0, br, total, g, lane, T, run);
-      __syncthreads();  // every group is done with its tables
-#pragma unroll
-      for (int r = 0; r < 8; ++r) part[g][r][lane] = run[r];
-      __syncthreads();
+      for (int r = 0; r < 8; ++r) part[g][r][lane] = make_float2(0.f, 0.f);
+      group_dispatch<4>(I, P, W, start, bx, by, 0, br, total, g, lane, T, &part[g][0][lane]);
+      __syncthreads();  // every group's running sums are final
       // group g combines cell r = g of every thread's eight, over the groups in
       // order (the same order for every block and run)
       static_assert(kGroups == 8, "one cell of eight per group");
@@ -627,11 +666,10 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
       const int x = bx * kBin + cx + (r & 1), y = by * kBin + cy0 + (r >> 1);
       if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
     } else {
-      float2 run[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      group_dispatch<1>(I, P, W, start, bx, by, slice * kSliceRows, br, total, g, lane, T, run);
-      __syncthreads();
-      part[g][0][lane] = run[0];
-      part[g][1][lane] = run[1];
+      part[g][0][lane] = make_float2(0.f, 0.f);
+      part[g][1][lane] = make_float2(0.f, 0.f);
+      group_dispatch<1>(I, P, W, start, bx, by, slice * kSliceRows, br, total, g, lane, T,
+                        &part[g][0][lane]);
       __syncthreads();
       if (threadIdx.x < 2 * kGroupThreads) {  // 64 cells, one thread each
         const int l = threadIdx.x >> 1, r = threadIdx.x & 1;
@@ -709,13 +747,40 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
     k_radix_pass<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, pass, ghist,
                                                     chunk_ctr, status, ws.keys[cur ^ 1],
                                                     ws.vals[cur ^ 1], prepared, prepared_w, ws.spts,
-                                                    ws.sw, last, ws.err);
+                                                    ws.sw, last, ws.err, tc::kWaitLimitNs);
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cur ^= 1;
   }
   k_bin_bounds<<<(int)((total_bins + 1 + 255) / 256), 256, 0, s>>>(ws.keys[cur], m,
                                                                    (int)total_bins, ws.start);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+size_t lookback_probe_words() { return 4 * 4096 + 2 * 2 * 256 + 256 + kMaxPasses; }
+
+cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint64_t limit_ns,
+                                          cudaStream_t s) {
+  // 4096 zero keys in two chunks; the chunk counter starts at 1, so the one
+  // CTA takes chunk 1 and waits for a chunk 0 that never publishes
+  constexpr int64_t m = 2 * kSortChunk;
+  uint32_t* keys = buf;
+  uint32_t* vals = keys + m;
+  uint32_t* keys_out = vals + m;
+  uint32_t* vals_out = keys_out + m;
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(vals_out + m);
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(status + 2 * 256);
+  uint32_t* chunk_ctr = ghist + 256;
+  cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(uint32_t) * lookback_probe_words(), s);
+  if (e != cudaSuccess) return e;
+  const uint32_t one = 1;
+  // a kernel-parameter write keeps the probe free of host-to-device copies
+  e = launch_upload(&one, sizeof(one), chunk_ctr, s);
+  if (e != cudaSuccess) return e;
+  k_radix_pass<<<1, kSortThreads, 0, s>>>(keys, vals, m, 0, ghist, chunk_ctr, status, keys_out,
+                                          vals_out, nullptr, nullptr, nullptr, nullptr, 0, err,
+                                          limit_ns);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -735,7 +800,10 @@ cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins, 
   // slicing instance that may turn out heavy
   const int64_t ctas = (int64_t)nb + (int64_t)(kSlices - 1) * slice_bins;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
-  k_cutoff<<<(unsigned)ctas, kGroups * kGroupThreads, 0, s>>>(
+  if ((e = cudaFuncSetAttribute(k_cutoff, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kCutSmemBytes)) != cudaSuccess)
+    return e;
+  k_cutoff<<<(unsigned)ctas, kGroups * kGroupThreads, kCutSmemBytes, s>>>(
       tab, ninst, ws.spts, ws.sw, ws.start, ws.order, ws.totals, ws.ranges,
       ws.ocount + 2 * kCutOrderKeys, nb);
   note_launches(3);

@@ -345,6 +345,13 @@ CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
 cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t total_bins,
                             const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                             CutoffScratch ws, cudaStream_t s);
+// The bounded wait of the sort's look-back, made to run out: one radix pass
+// over 4096 zero keys runs as the second chunk while the first never
+// publishes, so it gives up after limit_ns and records a timeout (role 31) in
+// err.  buf: lookback_probe_words() words of device memory.
+size_t lookback_probe_words();
+cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint64_t limit_ns,
+                                          cudaStream_t s);
 // The cutoff evaluation of the first ninst instances (output blocks
 // 0..cut_bins-1, of which slice_bins belong to instances with CutInst::slice
 // set): one CTA per block, or per 4-row slice of a heavy block.
