@@ -40,7 +40,7 @@ int kde_diag_wait_timeout(int64_t limit_ns, void* stream);
  * kde_diag_sort_wait_timeout — exercises the bounded wait of the bin sort's
  * look-back (no counterpart in the paper; the sort orders the points of the
  * cutoff path, Sec. III-C with Eq. 8, and of the block-sparse path): one
- * radix pass over 4096 zero keys runs as the second of two chunks while the
+ * radix pass over two chunks of zero keys runs as the second while the
  * first never publishes its counts, so the pass gives up after limit_ns
  * nanoseconds, records the timeout (role 31), keeps every position it writes
  * inside its buffers and returns, leaving the context usable.  Returns

@@ -23,9 +23,9 @@ namespace {
 constexpr int kBin = kCutoffBin;    // cells per output block side
 constexpr int kGroupThreads = 32;   // a point group is one warp: 8 cells per thread
 constexpr int kGroups = 8;          // point groups per CTA (one output block)
-constexpr int kSortThreads = 256;   // 8 warps
+constexpr int kSortThreads = 512;   // 16 warps
 constexpr int kSortRounds = 8;      // 32-element rounds per warp
-constexpr int kSortChunk = kSortThreads * kSortRounds;  // 2048 keys per block
+constexpr int kSortChunk = kSortThreads * kSortRounds;  // 4096 keys per block
 constexpr int kMaxPasses = 4;     // 8-bit digits of 32-bit keys
 constexpr int kBatch = 32;          // points per shared-memory batch (one per lane)
 
@@ -135,7 +135,7 @@ __device__ __forceinline__ unsigned long long status_word(int pass, bool incl, u
 
 // One stable counting pass over 8 bits of the keys (Merrill and Garland's
 // single-pass prefix scan with decoupled look-back, applied per digit).  CTAs
-// take 2048-key chunks in the order they start (a counter), so every chunk a
+// take 4096-key chunks in the order they start (a counter), so every chunk a
 // CTA waits for belongs to a CTA that is already running.  Each CTA ranks its
 // keys per digit (stable: warps in order, lanes in order), publishes its
 // per-digit counts, then walks back over earlier chunks until it meets an
@@ -173,17 +173,21 @@ __global__ void __launch_bounds__(kSortThreads)
   uint32_t digit[kSortRounds], rank[kSortRounds];
   rank_digits(kv, m, (int64_t)chunk * kSortChunk, shift, cnt, digit, rank);
   __syncthreads();
-  const int d = threadIdx.x;  // 256 threads, one digit each
+  // the first 256 threads own one digit each
+  const int d = threadIdx.x & 255;
+  const bool dig = threadIdx.x < 256;
   uint32_t total = 0;
-  for (int w = 0; w < kSortThreads / 32; ++w) {
-    const uint32_t c = cnt[w][d];
-    cnt[w][d] = total;  // exclusive prefix over the warps
-    total += c;
+  if (dig) {
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      const uint32_t c = cnt[w][d];
+      cnt[w][d] = total;  // exclusive prefix over the warps
+      total += c;
+    }
   }
   volatile unsigned long long* st = status + (size_t)chunk * 256 + d;
-  *st = status_word(pass, chunk == 0, total);
+  if (dig) *st = status_word(pass, chunk == 0, total);
   uint64_t excl = 0;
-  if (chunk > 0) {
+  if (dig && chunk > 0) {
     // four earlier chunks per step, their words loaded together; the walk
     // ends at the first inclusive prefix (chunk 0 publishes one at once)
     constexpr int kLook = 4;
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads)
     *st = status_word(pass, true, excl + total);
   }
   // keys of smaller digits: exclusive scan of this pass's histogram
-  const uint32_t gh = ghist[pass * 256 + d];
+  const uint32_t gh = dig ? ghist[pass * 256 + d] : 0u;
   uint32_t inc = gh;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   uint32_t before = 0;
   for (int w = 0; w < warp; ++w) before += wsum[w];
-  base[d] = before + inc - gh + (uint32_t)excl;
+  if (dig) base[d] = before + inc - gh + (uint32_t)excl;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
@@ -758,11 +762,11 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
   return cudaGetLastError();
 }
 
-size_t lookback_probe_words() { return 4 * 4096 + 2 * 2 * 256 + 256 + kMaxPasses; }
+size_t lookback_probe_words() { return 4 * 2 * kSortChunk + 2 * 2 * 256 + 256 + kMaxPasses; }
 
 cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint64_t limit_ns,
                                           cudaStream_t s) {
-  // 4096 zero keys in two chunks; the chunk counter starts at 1, so the one
+  // zero keys in two chunks; the chunk counter starts at 1, so the one
   // CTA takes chunk 1 and waits for a chunk 0 that never publishes
   constexpr int64_t m = 2 * kSortChunk;
   uint32_t* keys = buf;

@@ -346,7 +346,7 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
                             const float4* prepared, const float* prepared_w, const CutoffSizes& z,
                             CutoffScratch ws, cudaStream_t s);
 // The bounded wait of the sort's look-back, made to run out: one radix pass
-// over 4096 zero keys runs as the second chunk while the first never
+// over two chunks of zero keys runs as the second chunk while the first never
 // publishes, so it gives up after limit_ns and records a timeout (role 31) in
 // err.  buf: lookback_probe_words() words of device memory.
 size_t lookback_probe_words();
