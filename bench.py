@@ -417,6 +417,7 @@ def run_ours(args):
         if sg != nx:
             simt_out = None
 
+    sparse_e2e = None  # the block-sparse step through the host-buffer call
     if not args.no_e2e:
         # End to end through the same call with host buffers: pinned (lon, lat)
         # and weights in, the pinned grid out; the library copies them on the
@@ -474,6 +475,42 @@ def run_ours(args):
                          "kernel_ms": statistics.mean(a.elapsed_time(b) for a, b in e2e_pairs),
                          "clocks": e2e_clocks.stop()}
         del ws
+        if rank == 0 and args.path in ("tc_split16", "tc_fp16") and not args.flags \
+                and not args.no_sparse:
+            # the block-sparse step through the same host-buffer call: its
+            # kernels take a hundredth of the dense step's, so the copies show
+            flags_sp = flags_e2e | kde.FLAG_SKIP_ZERO
+            wss = kde.workspace_size(lonlat_host, w_host, origin, wl.cell, nx, ny, wl.h,
+                                     args.kernel, outs_host[0], path=args.path, flags=flags_sp,
+                                     lat0_deg=lat0, **tiling)
+            ws_sp = [torch.empty(wss, dtype=torch.uint8, device=dev) for _ in range(2)]
+
+            def sp_step(k):
+                b = k % 2
+                kde.grid(lonlat_host, w_host, origin, wl.cell, nx, ny, wl.h, args.kernel,
+                         out=outs_host[b], path=args.path, flags=flags_sp, lat0_deg=lat0,
+                         stream=streams[b], workspace=ws_sp[b], **tiling)
+
+            for k in range(4):
+                sp_step(k)
+            torch.cuda.synchronize()
+            reps = 20
+            e0.record(streams[0])
+            streams[1].wait_event(e0)
+            for k in range(reps):
+                sp_step(k)
+            streams[0].wait_stream(streams[1])
+            e1.record(streams[0])
+            torch.cuda.synchronize()
+            sms_e2e = e0.elapsed_time(e1) / reps
+            sparse_e2e = {"value": evals / (sms_e2e * 1e-3) / 1e9, "unit": UNIT,
+                          "ms_per_step": sms_e2e, "h2d_bytes_per_step": h2d_bytes,
+                          "d2h_bytes_per_step": int(outs_host[0].numel() * 4),
+                          # input bytes per step over the step time: the copy rate the
+                          # step sustains while they overlap the other stream's kernels
+                          "h2d_gbs_at_step_rate": h2d_bytes / (sms_e2e * 1e-3) / 1e9,
+                          "copies": result["e2e"]["copies"]}
+            del ws_sp
 
     if rank == 0 and not args.no_peak_probe:
         # the tcgen05 FP16 and ex2 rates measured by the library's own probes,
@@ -505,6 +542,8 @@ def run_ours(args):
             and not args.no_sparse:
         result["block_sparse"] = sparse_leg(step, stream, out_dev, new_pair, kernel_ms, evals,
                                             sample)
+        if sparse_e2e is not None:
+            result["block_sparse"]["e2e"] = sparse_e2e
         products = 3 if args.path == "tc_split16" else 1
         pt = sparse_products(xy_dev.cpu().numpy().reshape(-1, 2), origin, wl.cell, nx, ny, wl.h)
         flops = 2.0 * products * 65536.0 * pt
