@@ -15,8 +15,8 @@ extern "C" {
  * kde_diag_exclusive_scan — the multi-block exclusive prefix sum of
  * arXiv 2004.13653, Sec. IV-A ("Scan Algorithm"): each block of `per_block`
  * elements is scanned, the block totals are scanned in turn (recursively) and
- * propagated to the following blocks.  The binned cutoff path uses it for
- * its radix-sort bucket offsets.  in, out: device, [n] uint32 (must not
+ * propagated to the following blocks.  The block-sparse work list and the
+ * Douglas-Peucker compaction use it.  in, out: device, [n] uint32 (must not
  * alias); per_block in [1, 2048] (small values reproduce the paper's worked
  * example with four-element blocks).  Synchronous; uses the library
  * workspace.  Errors: KDE_EINVAL (n < 0, per_block out of range, null or host

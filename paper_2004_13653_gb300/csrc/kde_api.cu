@@ -287,7 +287,7 @@ struct BatchPlan {
   CutoffSizes cz;
   bool host_pts = false, host_w = false, host_out = false;
   size_t off_scal, off_pts, off_wts, off_tab_prep, off_tab_tc, off_tab_cut, off_tab_red;
-  size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_hscan, off_co_stemp, off_co_start,
+  size_t off_co_keys[2], off_co_vals[2], off_co_hist, off_co_start,
       off_co_spts, off_co_sw, off_co_order, off_co_totals, off_co_ranges, off_co_ocount, off_hxy,
       off_hw,
       off_hout, total;
@@ -598,8 +598,6 @@ int make_plan(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
       P->off_co_vals[k] = take(u * (size_t)P->cut_m);
     }
     P->off_co_hist = take(u * P->cz.hist_words);
-    P->off_co_hscan = take(u);  // unused by the one-sweep sort
-    P->off_co_stemp = take(u * (P->cz.scan_words + 64));
     P->off_co_start = take(u * ((size_t)P->total_bins + 1));
     P->off_co_spts = take(sizeof(float4) * (size_t)P->cut_m);
     P->off_co_sw = take(sizeof(float) * (size_t)P->cut_m);
@@ -888,8 +886,6 @@ int run_batch(const kde_args* A, int count, const kde_opts* o, const kde_tiling*
       cs.vals[k] = reinterpret_cast<uint32_t*>(base + P.off_co_vals[k]);
     }
     cs.hist = reinterpret_cast<uint32_t*>(base + P.off_co_hist);
-    cs.hist_scan = reinterpret_cast<uint32_t*>(base + P.off_co_hscan);
-    cs.scan_temp = reinterpret_cast<uint32_t*>(base + P.off_co_stemp);
     cs.start = reinterpret_cast<uint32_t*>(base + P.off_co_start);
     cs.spts = reinterpret_cast<float4*>(base + P.off_co_spts);
     cs.sw = reinterpret_cast<float*>(base + P.off_co_sw);

@@ -727,7 +727,6 @@ CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {
   // look-back status (one 64-bit word per chunk and digit), the per-pass
   // digit histograms and the per-pass chunk counters, cleared together
   z.hist_words = (size_t)2 * 256 * z.nchunks + (size_t)kMaxPasses * 256 + kMaxPasses;
-  z.scan_words = 0;
   return z;
 }
 

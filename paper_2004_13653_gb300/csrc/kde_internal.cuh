@@ -312,9 +312,7 @@ int cutoff_sort_bin(int nx, int ny, double reach_cells);
 struct CutoffScratch {
   uint32_t* keys[2];
   uint32_t* vals[2];
-  uint32_t* hist;
-  uint32_t* hist_scan;
-  uint32_t* scan_temp;
+  uint32_t* hist;   // [hist_words] the sort's look-back status, digit histograms, counters
   uint32_t* start;  // [total bins + 1]
   float4* spts;     // points in bin order
   float* sw;
@@ -333,7 +331,7 @@ constexpr int kCutOrderKeys = 2 * kCutOrderClasses;
 constexpr int kCutOcountWords = 2 * kCutOrderKeys + 1;
 struct CutoffSizes {
   int nchunks, passes;
-  size_t hist_words, scan_words;
+  size_t hist_words;
 };
 CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins);
 // Keys, stable radix sort, bin starts and the permuted points for every
