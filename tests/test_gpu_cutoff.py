@@ -221,3 +221,23 @@ def test_heavy_blocks_reproducible_and_same_in_a_batch():
     outs = kde.grid_batched([inst(other, oracle.EPANECHNIKOV), inst(wl, kid)], flags=kde.FLAG_SYNC)
     assert np.array_equal(outs[1].cpu().numpy(), a)
     assert np.array_equal(outs[0].cpu().numpy(), run_gpu(other, oracle.EPANECHNIKOV))
+
+
+def test_four_radix_passes_on_a_16384_square_grid():
+    """16384^2 cells at h = 2 cells: 4096^2 = 2^24 sort bins of 4 cells, keys of 25 bits, so the
+    bin sort runs all four 8-bit passes (the last one writing the permuted points) and the
+    gather takes a million output blocks; sampled cells around the densest one and elsewhere
+    against the oracle."""
+    kid = oracle.EPANECHNIKOV
+    rng = np.random.default_rng(599)
+    cell, n_side = 10.0, 16384
+    wl = workloads.random_points(599, 60_000, 1.0, cell, n_side, n_side, 2.0 * cell, kid)
+    wl.local[:40_000] = rng.uniform(0.0, n_side * cell, size=(40_000, 2))
+    wl.local[40_000:] = rng.normal([0.7 * n_side * cell, 0.2 * n_side * cell], 30.0,
+                                   size=(20_000, 2))
+    F = run_gpu(wl, kid)
+    assert F.shape == (n_side, n_side)
+    cells = sample_cells(F, 512, seed=600)
+    ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
+    assert np.max(ref) > 0
+    assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
