@@ -113,6 +113,38 @@ def cutoff_pairs(xy, origin, cell, nx, ny, h):
     return int(B * B * reach_pts.sum())
 
 
+def support_pairs(xy, origin, cell, nx, ny, h):
+    """Point-cell pairs inside the square support |s| <= 1, |t| <= 1 of the
+    product kernels (offsets in bandwidths): the algorithmic work of the
+    cutoff path, sum over points of (cells per row) x (cells per column)."""
+    import numpy as np
+    X = (np.asarray(xy[:, 0], np.float64) - origin[0]) / cell
+    Y = (np.asarray(xy[:, 1], np.float64) - origin[1]) / cell
+    r = h / cell
+
+    def span(c, n):
+        # cell centres i + 1/2 within r of c, for i in [0, n)
+        lo = np.maximum(np.ceil(c - r - 0.5), 0.0)
+        hi = np.minimum(np.floor(c + r - 0.5), n - 1.0)
+        return np.maximum(hi - lo + 1.0, 0.0)
+    return int((span(X, nx) * span(Y, ny)).sum())
+
+
+def cutoff_roofline(pairs, support, kernel_ms, n, nx, ny, peaks, peak_pairs):
+    """The cutoff path's two rooflines: evaluated pairs against the FP32 ALU
+    peak (the binding one), and its algorithmic bytes (the points read by the
+    centring and by the sort's passes and the gather, about 60 B per point, and
+    the grid written once) against the measured HBM rate; plus the pairs inside
+    the supports, the work the method itself defines."""
+    sec = kernel_ms * 1e-3
+    gbs = (60.0 * n + 4.0 * nx * ny) / sec / 1e9
+    return {"bound": "alu", "achieved": pairs / sec / 1e12, "peak": peak_pairs / 1e12,
+            "unit": "Tpair/s", "frac": pairs / sec / peak_pairs, "traffic": None,
+            "support_pairs": support, "support_tpair_s": support / sec / 1e12,
+            "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                    "frac": gbs / peaks["hbm_gbs"]}}
+
+
 def measured_traffic(path, grid, points):
     import hashlib
     t = TRAFFIC.get((path, grid, points))
@@ -356,6 +388,11 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_pairs / 1e12,
                 "unit": "Tpair/s", "frac": achieved / peak_pairs, "traffic": None,
                 "peak_source": f"FP32 issue 128/clk/SM at {clk_hz/1e6:.0f} MHz"}
+        if args.path == "cutoff":
+            xy_np = xy_dev.cpu().numpy().reshape(-1, 2)
+            roof = dict(cutoff_roofline(pairs, support_pairs(xy_np, origin, wl.cell, nx, ny, wl.h),
+                                        kernel_ms, n, nx, ny, peaks, peak_pairs),
+                        peak_source=roof["peak_source"])
     else:
         products = 3 if args.path == "tc_split16" else 1
         flops = 2.0 * products * evals
@@ -715,11 +752,11 @@ def configs12_leg(dev, peaks, sms, local):
     cut = out["config2_epanechnikov_cutoff"]
     pairs = cutoff_pairs(c2.xy, c2.origin, c2.cell, c2.nx, c2.ny, c2.h)
     peak_a = alu_peak_pairs(peaks, sms)
-    cut["roofline"] = {"bound": "alu", "achieved": pairs / (cut["ms_per_call"] * 1e-3) / 1e12,
-                       "peak": peak_a / 1e12, "unit": "Tpair/s",
-                       "frac": pairs / (cut["ms_per_call"] * 1e-3) / peak_a,
-                       "note": "evaluated pairs (16x16-cell blocks x points of the sort bins "
-                               "within reach) over the whole call"}
+    cut["roofline"] = dict(cutoff_roofline(pairs, support_pairs(c2.xy, c2.origin, c2.cell, c2.nx,
+                                                                c2.ny, c2.h),
+                                           cut["ms_per_call"], c2.n, c2.nx, c2.ny, peaks, peak_a),
+                           note="evaluated pairs (16x16-cell blocks x points of the sort bins "
+                                "within reach) over the whole call")
     out["config2_points"] = c2.n
     out["clocks"] = clk
     del xy1, xy2

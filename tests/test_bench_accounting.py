@@ -155,3 +155,16 @@ def test_measured_traffic_follows_the_source_hash(monkeypatch):
     monkeypatch.setitem(bench.TRAFFIC, key, dict(entry, sha256=hsh.hexdigest()))
     assert bench.measured_traffic(*key) == entry["bytes"]
     assert bench.measured_traffic("tc_split16", 2048, 40_000) is None
+
+
+@pytest.mark.parametrize("nx,ny,h_cells,n", [(40, 40, 2.0, 300), (53, 37, 0.7, 500),
+                                              (96, 64, 9.0, 200), (70, 90, 20.0, 150)])
+def test_support_pairs_equal_brute_force(nx, ny, h_cells, n):
+    """The cutoff path's algorithmic work: every point against every cell,
+    counting the pairs with both offsets within a bandwidth."""
+    cell = 10.0
+    h = h_cells * cell
+    xy = _points(nx + ny + 7, n, nx, ny, cell)
+    cs = cell / h
+    want = _support_pairs(xy[:, 0] / h, xy[:, 1] / h, nx, ny, cs)
+    assert bench.support_pairs(xy, (0.0, 0.0), cell, nx, ny, h) == want
