@@ -149,8 +149,9 @@ void kde_default_opts(kde_opts* o);
 /*
  * kde_grid — the density of Sec. III-C (Eq. 7 read as a direct sum over
  * points, Table 1 kernels, Eq. 8 indicator) at the nx*ny cell centres.
- * points/weights/out may be device or host memory.  Runs on the legacy
- * default stream with the AUTO path and returns after completion.
+ * points/weights/out may be device or host memory.  Runs on the calling
+ * thread's kde_set_stream() stream (the legacy default stream unless set)
+ * with the AUTO path and returns after completion.
  * Errors: KDE_EINVAL (null points with n > 0, null out, n < 0, nx/ny <= 0,
  * nx*ny >= 2^31, cell or h not positive and finite, unknown kernel_id,
  * non-finite origin), KDE_EDATA (a non-finite coordinate or weight),
@@ -159,6 +160,14 @@ void kde_default_opts(kde_opts* o);
 int kde_grid(const double* points, const float* weights, int64_t n,
              const double grid_origin[2], double cell, int nx, int ny,
              double h, int kernel_id, float* out);
+
+/* kde_set_stream — the CUDA stream (a cudaStream_t; NULL = the legacy
+ * default stream, the initial setting) that kde_grid() runs on and waits for,
+ * for the calling host thread only (Sec. III-C's density computed by
+ * kde_grid as above; the stream is plumbing, without a counterpart in the
+ * paper).  The stream must stay valid while kde_grid() calls use it.
+ * kde_grid_ex and the other entry points take their stream from kde_opts. */
+void kde_set_stream(void* stream);
 
 /* kde_grid with explicit path, stream, workspace and tiling (Sec. III-C,
  * Eq. 7 / Table 1).  Asynchronous on opts->stream unless KDE_FLAG_SYNC.

@@ -64,7 +64,7 @@ EXPORTS = ("kde_default_opts", "kde_grid", "kde_grid_ex", "kde_workspace_size",
            "kde_last_error", "kde_release", "kde_version", "kde_launch_count",
            "kde_diag_exclusive_scan", "kde_grid_noalloc", "kde_diag_wait_timeout",
            "kde_grid_binned", "kde_dp_simplify", "kde_diag_peak_rates",
-           "kde_diag_sort_wait_timeout")
+           "kde_diag_sort_wait_timeout", "kde_set_stream")
 
 _lib = None
 
@@ -124,6 +124,8 @@ def load(build_if_stale: bool = False) -> ctypes.CDLL:
     lib.kde_diag_wait_timeout.restype = i32
     lib.kde_diag_sort_wait_timeout.argtypes = [i64, vp]
     lib.kde_diag_sort_wait_timeout.restype = i32
+    lib.kde_set_stream.argtypes = [vp]
+    lib.kde_set_stream.restype = None
     lib.kde_diag_peak_rates.argtypes = [P(ctypes.c_double * 3), vp]
     lib.kde_diag_peak_rates.restype = i32
     lib.kde_diag_exclusive_scan.argtypes = [vp, vp, i64, i32, vp]
@@ -249,12 +251,24 @@ def grid(points, weights, origin, cell, nx, ny, h, kernel="gaussian", out=None, 
 
 
 def grid_simple(points, weights, origin, cell, nx, ny, h, kernel, out):
-    """kde_grid: the plain entry point (legacy stream, AUTO path, synchronous)."""
+    """kde_grid: the plain entry point (the set_stream stream, legacy unless
+    set; AUTO path; synchronous)."""
     a = make_args(points, weights, origin, cell, nx, ny, h, kernel, out)
     org = (ctypes.c_double * 2)(float(origin[0]), float(origin[1]))
     check(load().kde_grid(a.points, a.weights, a.n, ctypes.byref(org), a.cell, a.nx, a.ny, a.h,
                           a.kernel_id, a.out))
     return out
+
+
+def set_stream(stream=None) -> None:
+    """kde_set_stream: the stream grid_simple (kde_grid) runs on and waits for,
+    for the calling thread; a torch.cuda.Stream, a raw cudaStream_t as int, or
+    None for the legacy default stream."""
+    if stream is None:
+        ptr = None
+    else:
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    load().kde_set_stream(ctypes.c_void_p(ptr))
 
 
 def workspace_size(points, weights, origin, cell, nx, ny, h, kernel, out, **opts) -> int:

@@ -22,6 +22,8 @@ void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); 
 namespace {
 
 thread_local char g_err[512] = "";
+// the stream kde_grid() runs on, per calling thread (kde_set_stream)
+thread_local void* g_plain_stream = nullptr;
 
 int fail(int code, const char* fmt, ...) {
   va_list ap;
@@ -1026,8 +1028,11 @@ int kde_grid(const double* points, const float* weights, int64_t n, const double
   a.out = out;
   kde_opts o;
   kde_default_opts(&o);
+  o.stream = g_plain_stream;
   return run_batch(&a, 1, &o, nullptr, true);
 }
+
+void kde_set_stream(void* stream) { g_plain_stream = stream; }
 
 int kde_grid_ex(const kde_args* a, const kde_opts* opts) {
   if (!a) return fail(KDE_EINVAL, "args is NULL");

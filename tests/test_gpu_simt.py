@@ -101,6 +101,53 @@ def test_host_buffers_through_plain_entry():
     assert rel_linf(out, ref) <= 1e-5  # AUTO path
 
 
+def test_plain_entry_runs_on_the_set_stream():
+    """kde_set_stream: the points reach their device buffer on a side stream
+    only after a ~0.1 s spin; kde_grid on that stream reads them in order and
+    matches the oracle (on the legacy stream it would race the spin, because
+    torch's streams do not synchronise with it).  Another thread, which has
+    set no stream, still runs on the legacy stream."""
+    import threading
+    wl = workloads.config1()
+    src = _dev(wl.xy, torch.float64)
+    pts = torch.zeros_like(src)
+    w = _dev(wl.w, torch.float32)
+    out = torch.full((wl.ny, wl.nx), 7.0, device="cuda")
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    try:
+        kde.set_stream(side)
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(200_000_000)
+            pts.copy_(src)
+        kde.grid_simple(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel, out)
+        assert side.query()  # kde_grid waited for its stream
+        assert rel_linf(out.cpu().numpy(), ref) <= 1e-5
+
+        other = torch.full_like(out, 7.0)
+        torch.cuda.synchronize()
+        errs = []
+
+        def worker():
+            try:
+                kde.grid_simple(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel,
+                                other)
+            except Exception as e:  # reported below, on the test's thread
+                errs.append(e)
+        t = threading.Thread(target=worker)
+        t.start()
+        t.join()
+        assert not errs
+        assert rel_linf(other.cpu().numpy(), ref) <= 1e-5
+    finally:
+        kde.set_stream(None)
+    torch.cuda.synchronize()
+    out.fill_(7.0)
+    kde.grid_simple(pts, w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel, out)
+    assert rel_linf(out.cpu().numpy(), ref) <= 1e-5
+
+
 def test_nonfinite_coordinate_reported():
     wl = workloads.config1()
     xy = wl.xy.copy()
