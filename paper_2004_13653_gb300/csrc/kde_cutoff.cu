@@ -39,19 +39,31 @@ __device__ __forceinline__ int find_by(const T* tab, int ninst, int64_t v, int64
   return lo;
 }
 
+// Radix buckets per pass: the 256 values of an 8-bit digit, then one bucket
+// for keys with a bit set at or above `top` = 8 x passes.  Only the key that
+// marks padding and unreachable points (total_bins) can have one, when it
+// needs a bit more than every valid key; it then sorts after every digit in
+// each pass, so the valid keys alone decide the number of passes.
+constexpr int kDigits = 257;
+static_assert(kSortThreads >= kDigits, "one thread per radix bucket in the look-back");
+
+__device__ __forceinline__ uint32_t radix_digit(uint32_t key, int shift, int top) {
+  return (top < 32 && (key >> top) != 0u) ? 256u : (key >> shift) & 255u;
+}
+
 // Bin key of each point of every instance (points centred and scaled):
 // key = bin_begin + by * nbx + bx, or total_bins for padding and for points
 // that cannot reach their grid.  vals = the point's index in the prepared
 // arrays.  Each CTA also counts the digits of every radix pass of its keys
 // (lanes that share a digit add once) and adds them to the per-pass
-// histograms ghist[pass][256].
+// histograms ghist[pass][kDigits].
 __global__ void __launch_bounds__(256)
     k_bin_keys(const CutInst* __restrict__ tab, int ninst, int64_t m,
                const float4* __restrict__ prepared, uint32_t total_bins, int passes,
                uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                uint32_t* __restrict__ ghist) {
-  __shared__ uint32_t h[kMaxPasses][256];
-  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __shared__ uint32_t h[kMaxPasses][kDigits];
+  for (int i = threadIdx.x; i < kMaxPasses * kDigits; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -80,13 +92,13 @@ __global__ void __launch_bounds__(256)
     }
     const unsigned act = __ballot_sync(0xffffffffu, valid);
     for (int pass = 0; pass < passes; ++pass) {
-      const uint32_t d = (key >> (8 * pass)) & 255u;
-      const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 256u) & act;
+      const uint32_t d = radix_digit(key, 8 * pass, 8 * passes);
+      const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & act;
       if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[pass][d], (uint32_t)__popc(peers));
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+  for (int i = threadIdx.x; i < passes * kDigits; i += blockDim.x) {
     const uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(&ghist[i], c);
   }
@@ -97,8 +109,8 @@ __global__ void __launch_bounds__(256)
 // found with match_any, per-warp digit counts kept in shared memory.
 // Deterministic.
 __device__ __forceinline__ void rank_digits(const uint32_t (&kv)[kSortRounds], int64_t m,
-                                            int64_t base, int shift,
-                                            uint32_t (*cnt)[256], uint32_t (&digit)[kSortRounds],
+                                            int64_t base, int shift, int top,
+                                            uint32_t (*cnt)[kDigits], uint32_t (&digit)[kSortRounds],
                                             uint32_t (&rank)[kSortRounds]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -106,7 +118,7 @@ __device__ __forceinline__ void rank_digits(const uint32_t (&kv)[kSortRounds], i
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t e = base + (int64_t)warp * 32 * kSortRounds + r * 32 + lane;
     const bool valid = e < m;
-    const uint32_t d = valid ? (kv[r] >> shift) & 255u : 0u;
+    const uint32_t d = valid ? radix_digit(kv[r], shift, top) : 0u;
     const uint32_t active = __ballot_sync(0xffffffffu, valid);
     uint32_t peers = 0, old = 0;
     if (valid) {
@@ -133,7 +145,8 @@ __device__ __forceinline__ unsigned long long status_word(int pass, bool incl, u
   return ((unsigned long long)(pass + 1) << 61) | (incl ? kStatusIncl : 0ull) | v;
 }
 
-// One stable counting pass over 8 bits of the keys (Merrill and Garland's
+// One stable counting pass over 8 bits of the keys and the bucket above them
+// (`top` = 8 x passes; Merrill and Garland's
 // single-pass prefix scan with decoupled look-back, applied per digit).  CTAs
 // take 4096-key chunks in the order they start (a counter), so every chunk a
 // CTA waits for belongs to a CTA that is already running.  Each CTA ranks its
@@ -146,17 +159,19 @@ __device__ __forceinline__ unsigned long long status_word(int pass, bool incl, u
 // positions are then bounded, not correct.
 __global__ void __launch_bounds__(kSortThreads)
     k_radix_pass(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
-                 int pass, const uint32_t* __restrict__ ghist, uint32_t* __restrict__ chunk_ctr,
+                 int pass, int top, const uint32_t* __restrict__ ghist,
+                 uint32_t* __restrict__ chunk_ctr,
                  unsigned long long* __restrict__ status, uint32_t* __restrict__ keys_out,
                  uint32_t* __restrict__ vals_out, const float4* __restrict__ prepared,
                  const float* __restrict__ wts, float4* __restrict__ spts, float* __restrict__ sw,
                  int last, CallScalars* __restrict__ err, uint64_t limit_ns) {
-  __shared__ uint32_t cnt[kSortThreads / 32][256];
-  __shared__ uint32_t base[256];
+  __shared__ uint32_t cnt[kSortThreads / 32][kDigits];
+  __shared__ uint32_t base[kDigits];
   __shared__ uint32_t wsum[kSortThreads / 32];
   __shared__ uint32_t chunk_s;
   if (threadIdx.x == 0) chunk_s = atomicAdd(&chunk_ctr[pass], 1u);
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < (kSortThreads / 32) * kDigits; i += kSortThreads)
+    (&cnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t chunk = chunk_s;
   const int shift = 8 * pass;
@@ -171,11 +186,11 @@ __global__ void __launch_bounds__(kSortThreads)
     vv[r] = e < m ? vals[e] : 0u;
   }
   uint32_t digit[kSortRounds], rank[kSortRounds];
-  rank_digits(kv, m, (int64_t)chunk * kSortChunk, shift, cnt, digit, rank);
+  rank_digits(kv, m, (int64_t)chunk * kSortChunk, shift, top, cnt, digit, rank);
   __syncthreads();
-  // the first 256 threads own one digit each
-  const int d = threadIdx.x & 255;
-  const bool dig = threadIdx.x < 256;
+  // the first kDigits threads own one bucket each
+  const bool dig = threadIdx.x < kDigits;
+  const int d = dig ? (int)threadIdx.x : 0;
   uint32_t total = 0;
   if (dig) {
     for (int w = 0; w < kSortThreads / 32; ++w) {
@@ -184,7 +199,7 @@ __global__ void __launch_bounds__(kSortThreads)
       total += c;
     }
   }
-  volatile unsigned long long* st = status + (size_t)chunk * 256 + d;
+  volatile unsigned long long* st = status + (size_t)chunk * kDigits + d;
   if (dig) *st = status_word(pass, chunk == 0, total);
   uint64_t excl = 0;
   if (dig && chunk > 0) {
@@ -197,8 +212,9 @@ __global__ void __launch_bounds__(kSortThreads)
       unsigned long long v[kLook];
 #pragma unroll
       for (int j = 0; j < kLook; ++j)
-        v[j] = c - j >= 0 ? *(volatile unsigned long long*)(status + (size_t)(c - j) * 256 + d)
-                          : 0ull;
+        v[j] = c - j >= 0
+                   ? *(volatile unsigned long long*)(status + (size_t)(c - j) * kDigits + d)
+                   : 0ull;
       bool done = false;
       int j = 0;
       for (; j < kLook; ++j) {
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(kSortThreads)
     *st = status_word(pass, true, excl + total);
   }
   // keys of smaller digits: exclusive scan of this pass's histogram
-  const uint32_t gh = dig ? ghist[pass * 256 + d] : 0u;
+  const uint32_t gh = dig ? ghist[pass * kDigits + d] : 0u;
   uint32_t inc = gh;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -721,12 +737,14 @@ int cutoff_sort_bin(int nx, int ny, double reach_cells) {
 CutoffSizes cutoff_sizes(int64_t m, int64_t total_bins) {
   CutoffSizes z;
   z.nchunks = (int)((m + kSortChunk - 1) / kSortChunk);
+  // the valid keys 0..total_bins - 1 set the passes; the marker total_bins
+  // takes the bucket above the digits where it needs one more bit
   int bits = 1;
-  while ((1ll << bits) <= (long long)total_bins) ++bits;  // keys 0..total_bins
+  while ((1ll << bits) < (long long)total_bins) ++bits;
   z.passes = (bits + 7) / 8;
-  // look-back status (one 64-bit word per chunk and digit), the per-pass
-  // digit histograms and the per-pass chunk counters, cleared together
-  z.hist_words = (size_t)2 * 256 * z.nchunks + (size_t)kMaxPasses * 256 + kMaxPasses;
+  // look-back status (one 64-bit word per chunk and bucket), the per-pass
+  // bucket histograms and the per-pass chunk counters, cleared together
+  z.hist_words = (size_t)2 * kDigits * z.nchunks + (size_t)kMaxPasses * kDigits + kMaxPasses;
   return z;
 }
 
@@ -736,8 +754,8 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
   if (ninst <= 0 || m <= 0) return cudaSuccess;
   if (z.passes < 1 || z.passes > kMaxPasses) return cudaErrorInvalidValue;
   unsigned long long* status = reinterpret_cast<unsigned long long*>(ws.hist);
-  uint32_t* ghist = ws.hist + (size_t)2 * 256 * z.nchunks;
-  uint32_t* chunk_ctr = ghist + kMaxPasses * 256;
+  uint32_t* ghist = ws.hist + (size_t)2 * kDigits * z.nchunks;
+  uint32_t* chunk_ctr = ghist + kMaxPasses * kDigits;
   cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * z.hist_words, s);
   if (e != cudaSuccess) return e;
   k_bin_keys<<<grid_for(m), 256, 0, s>>>(tab, ninst, m, prepared, (uint32_t)total_bins, z.passes,
@@ -747,8 +765,9 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
   int cur = 0;
   for (int pass = 0; pass < z.passes; ++pass) {
     const int last = pass == z.passes - 1;
-    k_radix_pass<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, pass, ghist,
-                                                    chunk_ctr, status, ws.keys[cur ^ 1],
+    k_radix_pass<<<z.nchunks, kSortThreads, 0, s>>>(ws.keys[cur], ws.vals[cur], m, pass,
+                                                    8 * z.passes, ghist, chunk_ctr, status,
+                                                    ws.keys[cur ^ 1],
                                                     ws.vals[cur ^ 1], prepared, prepared_w, ws.spts,
                                                     ws.sw, last, ws.err, tc::kWaitLimitNs);
     note_launches(1);
@@ -761,7 +780,9 @@ cudaError_t launch_bin_sort(const CutInst* tab, int ninst, int64_t m, int64_t to
   return cudaGetLastError();
 }
 
-size_t lookback_probe_words() { return 4 * 2 * kSortChunk + 2 * 2 * 256 + 256 + kMaxPasses; }
+size_t lookback_probe_words() {
+  return 4 * 2 * kSortChunk + 2 * 2 * kDigits + kDigits + kMaxPasses;
+}
 
 cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint64_t limit_ns,
                                           cudaStream_t s) {
@@ -773,15 +794,15 @@ cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint6
   uint32_t* keys_out = vals + m;
   uint32_t* vals_out = keys_out + m;
   unsigned long long* status = reinterpret_cast<unsigned long long*>(vals_out + m);
-  uint32_t* ghist = reinterpret_cast<uint32_t*>(status + 2 * 256);
-  uint32_t* chunk_ctr = ghist + 256;
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(status + 2 * kDigits);
+  uint32_t* chunk_ctr = ghist + kDigits;
   cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(uint32_t) * lookback_probe_words(), s);
   if (e != cudaSuccess) return e;
   const uint32_t one = 1;
   // a kernel-parameter write keeps the probe free of host-to-device copies
   e = launch_upload(&one, sizeof(one), chunk_ctr, s);
   if (e != cudaSuccess) return e;
-  k_radix_pass<<<1, kSortThreads, 0, s>>>(keys, vals, m, 0, ghist, chunk_ctr, status, keys_out,
+  k_radix_pass<<<1, kSortThreads, 0, s>>>(keys, vals, m, 0, 8, ghist, chunk_ctr, status, keys_out,
                                           vals_out, nullptr, nullptr, nullptr, nullptr, 0, err,
                                           limit_ns);
   note_launches(1);

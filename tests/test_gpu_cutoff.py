@@ -223,21 +223,54 @@ def test_heavy_blocks_reproducible_and_same_in_a_batch():
     assert np.array_equal(outs[0].cpu().numpy(), run_gpu(other, oracle.EPANECHNIKOV))
 
 
-def test_four_radix_passes_on_a_16384_square_grid():
-    """16384^2 cells at h = 2 cells: 4096^2 = 2^24 sort bins of 4 cells, keys of 25 bits, so the
-    bin sort runs all four 8-bit passes (the last one writing the permuted points) and the
-    gather takes a million output blocks; sampled cells around the densest one and elsewhere
-    against the oracle."""
+def _wide_grid(seed, n_side, cell, centre):
+    """60,000 points: two thirds uniform over an n_side^2 grid, one third in
+    a cluster of sigma 30 m, at h = 2 cells (4-cell sort bins)."""
+    rng = np.random.default_rng(seed)
     kid = oracle.EPANECHNIKOV
-    rng = np.random.default_rng(599)
-    cell, n_side = 10.0, 16384
-    wl = workloads.random_points(599, 60_000, 1.0, cell, n_side, n_side, 2.0 * cell, kid)
+    wl = workloads.random_points(seed, 60_000, 1.0, cell, n_side, n_side, 2.0 * cell, kid)
     wl.local[:40_000] = rng.uniform(0.0, n_side * cell, size=(40_000, 2))
-    wl.local[40_000:] = rng.normal([0.7 * n_side * cell, 0.2 * n_side * cell], 30.0,
-                                   size=(20_000, 2))
+    wl.local[40_000:] = rng.normal(np.asarray(centre) * n_side * cell, 30.0, size=(20_000, 2))
+    return wl
+
+
+def test_three_radix_passes_and_the_marker_bucket_on_a_16384_square_grid():
+    """16384^2 cells at h = 2 cells: 4096^2 = 2^24 sort bins of 4 cells.  The
+    valid keys take 24 bits (three 8-bit passes, the last writing the
+    permuted points); the key of padding, total_bins = 2^24, has the 25th bit
+    and sorts in the bucket above the digits in every pass.  The gather takes
+    a million output blocks; sampled cells around the densest one and
+    elsewhere against the oracle."""
+    kid = oracle.EPANECHNIKOV
+    wl = _wide_grid(599, 16384, 10.0, (0.7, 0.2))
     F = run_gpu(wl, kid)
-    assert F.shape == (n_side, n_side)
+    assert F.shape == (16384, 16384)
     cells = sample_cells(F, 512, seed=600)
     ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
     assert np.max(ref) > 0
     assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
+
+
+def test_four_radix_passes_on_a_batch_of_two_16384_square_grids():
+    """Two 16384^2 instances in one batch share one sort over 2^25 bins: keys
+    of 25 bits run all four passes (the padding key 2^25 then fits the top
+    digit).  Each instance is checked at sampled cells against the oracle and
+    equals its own single call bit for bit."""
+    kid = oracle.EPANECHNIKOV
+    wls = [_wide_grid(601, 16384, 10.0, (0.3, 0.8)), _wide_grid(602, 16384, 10.0, (0.5, 0.5))]
+    insts = []
+    for wl in wls:
+        insts.append(dict(points=torch.as_tensor(wl.xy, dtype=torch.float64, device="cuda"),
+                          weights=torch.as_tensor(wl.w, dtype=torch.float32, device="cuda"),
+                          origin=wl.origin, cell=wl.cell, nx=wl.nx, ny=wl.ny, h=wl.h,
+                          kernel=kid))
+    outs = kde.grid_batched(insts, flags=kde.FLAG_SYNC)
+    for k, (wl, F) in enumerate(zip(wls, outs)):
+        Fh = F.cpu().numpy()
+        cells = sample_cells(Fh, 256, seed=603 + k)
+        ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
+        assert np.max(ref) > 0
+        assert rel_linf(Fh.reshape(-1)[cells], ref) <= TOL_FP32
+        del Fh
+    alone = run_gpu(wls[1], kid)
+    assert np.array_equal(outs[1].cpu().numpy(), alone)
