@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(kSortThreads)
       c -= j;
       if (j == 0 && (it & 63) == 0 &&
           (tc::globaltimer_ns() - t0 > limit_ns || it > (1u << 30))) {
-        if (atomicOr(&err->err, kErrTimeout) == 0) atomicExch(&err->timeout_where, kRoleLookback);
+        if (atomicOr(&err->err, kErrTimeout | kErrSortTimeout) == 0)
+          atomicExch(&err->timeout_where, kRoleLookback);
         break;
       }
     }
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
              const float* __restrict__ W, const uint32_t* __restrict__ start,
              const uint32_t* __restrict__ order, const uint32_t* __restrict__ totals,
              const int4* __restrict__ ranges, const uint32_t* __restrict__ heavy_count,
-             int nblocks) {
+             int nblocks, const CallScalars* __restrict__ err) {
   // the groups' tables, then their running sums (cell r of lane l of group g
   // at part[g][r][l])
   extern __shared__ __align__(16) unsigned char smem[];
@@ -634,6 +635,10 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
       reinterpret_cast<float2 (*)[8][kGroupThreads]>(smem + kCutTablesBytes);
   const int g = threadIdx.x / kGroupThreads, lane = threadIdx.x % kGroupThreads;
   GroupTables& T = tables[g];
+  // after a timed-out sort the bin starts may not rise, and positions taken
+  // from them could leave the sorted points: compute nothing (the call
+  // reports the timeout)
+  if (*reinterpret_cast<const volatile int*>(&err->err) & kErrSortTimeout) return;
   const int64_t heavy = __ldg(heavy_count);
   const int64_t item = blockIdx.x;
   if (item >= (int64_t)nblocks + (int64_t)(kSlices - 1) * heavy) return;
@@ -812,7 +817,7 @@ cudaError_t launch_lookback_timeout_probe(uint32_t* buf, CallScalars* err, uint6
 cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins, int64_t slice_bins,
                                const CutoffScratch& ws, cudaStream_t s) {
   if (ninst <= 0 || cut_bins <= 0) return cudaSuccess;
-  if (cut_bins > 0x7fffffff) return cudaErrorInvalidValue;
+  if (cut_bins > 0x7fffffff || !ws.err) return cudaErrorInvalidValue;
   const int nb = (int)cut_bins, grid = (nb + 255) / 256;
   // per-key counts and cursors of the order, then the gather's item counter
   cudaError_t e = cudaMemsetAsync(ws.ocount, 0, sizeof(uint32_t) * kCutOcountWords, s);
@@ -829,7 +834,7 @@ cudaError_t launch_cutoff_eval(const CutInst* tab, int ninst, int64_t cut_bins, 
     return e;
   k_cutoff<<<(unsigned)ctas, kGroups * kGroupThreads, kCutSmemBytes, s>>>(
       tab, ninst, ws.spts, ws.sw, ws.start, ws.order, ws.totals, ws.ranges,
-      ws.ocount + 2 * kCutOrderKeys, nb);
+      ws.ocount + 2 * kCutOrderKeys, nb, ws.err);
   note_launches(3);
   return cudaGetLastError();
 }

@@ -22,6 +22,12 @@ namespace kde {
 constexpr int kErrTimeout = 1;    // a bounded device-side wait gave up
 constexpr int kErrNonFinite = 2;  // non-finite coordinate or weight
 constexpr int kErrBadArg = 4;     // a kernel saw an impossible argument
+// the bin sort's look-back gave up (set with kErrTimeout): the sorted order and
+// the bin starts are then not trusted, and the kernels that walk the sorted
+// points (the cutoff gather, the block-sparse contraction) skip their work;
+// only the sort sets it, in a launch before theirs, so every CTA of theirs
+// reads the same value
+constexpr int kErrSortTimeout = 8;
 
 struct CallScalars {
   int err;            // OR of kErr* bits

@@ -210,8 +210,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   int n_items = n_items_arg;
   if (SPARSE) {  // the work list was built on the device by the preceding launches
     const int listed = (int)__ldg(sp.piece_begin + sp.tiles_total);
-    // a list longer than the partial buffer is an error: no piece is computed
-    n_items = listed > sp.max_pieces ? 0 : listed;
+    // a list longer than the partial buffer is an error: no piece is computed.
+    // So is a timed-out bin sort (the pieces' positions come from its bin
+    // starts); only the sort, an earlier launch, sets that bit, so both CTAs
+    // of a pair read the same value and agree on their (empty) list
+    const bool sort_failed =
+        *reinterpret_cast<const volatile int*>(&scal->err) & kErrSortTimeout;
+    n_items = listed > sp.max_pieces || sort_failed ? 0 : listed;
     if (listed > sp.max_pieces && blockIdx.x == 0 && threadIdx.x == 0)
       atomicOr(&scal->err, kErrBadArg);
   }
