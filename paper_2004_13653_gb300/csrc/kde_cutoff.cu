@@ -381,6 +381,11 @@ __device__ __forceinline__ int weight_key(uint32_t total) {
 // and its instance, so a block is computed the same way in every run and in a
 // batch as on its own.
 constexpr int kHeavyKey = 25;  // weight_key(4096)
+// Blocks with fewer than 192 points within reach (weight class 15 and below,
+// empty blocks included) are computed two to a CTA, four point groups each:
+// eight groups would leave most of their warps without a batch.  Like the
+// split of heavy blocks, this depends only on the block's own count.
+constexpr int kLightKey = 15;  // weight_key(191)
 __device__ __forceinline__ int order_key(const CutInst& I, uint32_t total) {
   const int k = weight_key(total);
   return I.slice && k >= kHeavyKey ? kCutOrderClasses + k : k;
@@ -434,8 +439,12 @@ __global__ void k_cut_order_scatter(const CutInst* __restrict__ tab, int ninst,
       first[k] = acc;
       acc += ocount[k];
     }
-    // the blocks to be split into slices come first; the gather needs their count
-    if (blockIdx.x == 0) ocount[2 * kCutOrderKeys] = first[kCutOrderClasses - 1];
+    // the blocks to be split into slices come first and the light ones last;
+    // the gather needs the count of the first and the position of the second
+    if (blockIdx.x == 0) {
+      ocount[2 * kCutOrderKeys] = first[kCutOrderClasses - 1];
+      ocount[2 * kCutOrderKeys + 1] = first[kLightKey];
+    }
   }
   __syncthreads();
   const int blk = blockIdx.x * blockDim.x + threadIdx.x;
@@ -496,13 +505,13 @@ constexpr int kSlices = kBin / kSliceRows;  // items per heavy block
 // The work of one item, for one kernel: rows y_off..y_off + 4 RPL - 1 of the
 // block (RPL = 4: all 16 rows; RPL = 1: a 4-row slice).  The points that can
 // reach those rows are the runs of the sort bins in range br, one run per bin
-// row; their concatenation is cut into kBatch-point batches, and warp g of
-// the CTA takes batches g, g+G, g+2G, ... (fetching the next while computing
+// row; their concatenation is cut into kBatch-point batches, and group g of
+// the block's NG takes batches g, g+NG, g+2NG, ... (fetching the next while computing
 // the current; the warp synchronises only itself) and adds each batch into
 // the (hi, lo) running sums of its cells with a two-sum; the running sums
 // live in shared memory (run[r * 32] for cell r of this lane), which keeps
 // the kernel at 64 registers and four CTAs per SM.
-template <int KID, bool RADIAL, int RPL>
+template <int KID, bool RADIAL, int RPL, int NG>
 __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __restrict__ P,
                                              const float* __restrict__ W,
                                              const uint32_t* __restrict__ start, int bx, int by,
@@ -520,7 +529,7 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   if (total == 0) return;
   RunCursor32 cur;
   cur.init(start, I.bin_begin, I.nbx, br);
-  constexpr uint32_t kStride = kGroups * kBatch;
+  constexpr uint32_t kStride = NG * kBatch;
   const uint32_t total32 = (uint32_t)total;
   uint32_t v = g * kBatch + lane;  // this lane's point of the warp's current batch
   float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -585,7 +594,7 @@ __device__ __forceinline__ uint32_t range_total(const uint32_t* __restrict__ sta
   return total;
 }
 
-template <int RPL>
+template <int RPL, int NG>
 __device__ __forceinline__ void group_dispatch(const CutInst& I, const float4* __restrict__ P,
                                                const float* __restrict__ W,
                                                const uint32_t* __restrict__ start, int bx, int by,
@@ -594,10 +603,10 @@ __device__ __forceinline__ void group_dispatch(const CutInst& I, const float4* _
   switch (I.kid) {
 #define KDE_CUT(K)                                                                       \
   case K:                                                                                \
-    cutoff_group<K, false, RPL>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run); \
+    cutoff_group<K, false, RPL, NG>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run); \
     break;                                                                               \
   case kRadial + K:                                                                      \
-    cutoff_group<K, true, RPL>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run);  \
+    cutoff_group<K, true, RPL, NG>(I, P, W, start, bx, by, y_off, br, total, g, lane, T, run); \
     break;
     KDE_CUT(KDE_UNIFORM)
     KDE_CUT(KDE_TRIANGULAR)
@@ -613,7 +622,8 @@ __device__ __forceinline__ void group_dispatch(const CutInst& I, const float4* _
 
 // One CTA of kGroups one-warp point groups per item: first the four slices of
 // every heavy block, then the other blocks, each in the order list's
-// heaviest-first order (CTAs past the last item return at once).  A whole
+// heaviest-first order, and last the light blocks two at a time, groups 0-3
+// on the first and 4-7 on the second (CTAs past the last item return at once).  A whole
 // block's eight cells per thread, or a slice's two, are summed over the groups
 // in group order at the end, so every cell is computed by one CTA in a fixed
 // order and results are reproducible bit for bit.  Blocks of 16 cells spread a
@@ -628,8 +638,9 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
   // the groups' tables, then their running sums (cell r of lane l of group g
   // at part[g][r][l])
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int4 s_rg;
-  __shared__ uint32_t s_total;
+  __shared__ int4 s_rg[2];
+  __shared__ uint32_t s_total[2];
+  __shared__ int s_blk[2];
   GroupTables* tables = reinterpret_cast<GroupTables*>(smem);
   float2 (*part)[8][kGroupThreads] =
       reinterpret_cast<float2 (*)[8][kGroupThreads]>(smem + kCutTablesBytes);
@@ -640,8 +651,56 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
   // reports the timeout)
   if (*reinterpret_cast<const volatile int*>(&err->err) & kErrSortTimeout) return;
   const int64_t heavy = __ldg(heavy_count);
+  const int64_t light = __ldg(heavy_count + 1);  // order position of the first light block
+  const int64_t singles = kSlices * heavy + (light - heavy);
   const int64_t item = blockIdx.x;
-  if (item >= (int64_t)nblocks + (int64_t)(kSlices - 1) * heavy) return;
+  if (item >= singles + ((int64_t)nblocks - light + 1) / 2) return;
+  if (item >= singles) {
+    // two light blocks: half h = g / 4 takes the block at order position
+    // light + 2 (item - singles) + h with its four groups
+    const int half = g >> 2, gh = g & 3;
+    const int64_t pos = light + 2 * (item - singles) + half;
+    const bool has = pos < nblocks;
+    if (has && gh == 0 && lane == 0) {
+      const int blk = (int)__ldg(order + pos);
+      s_blk[half] = blk;
+      s_rg[half] = __ldg(ranges + blk);
+      s_total[half] = __ldg(totals + blk);
+    }
+    __syncthreads();
+    if (has) {
+      int bx, by;
+      const CutInst& I = output_block(tab, ninst, s_blk[half], bx, by);
+      const int4 rg = s_rg[half];
+      const BinRange br = {rg.x, rg.y, rg.z, rg.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r) part[g][r][lane] = make_float2(0.f, 0.f);
+      group_dispatch<4, 4>(I, P, W, start, bx, by, 0, br, s_total[half], gh, lane, T,
+                           &part[g][0][lane]);
+    }
+    __syncthreads();  // every group's running sums are final
+    if (has) {
+      // group gh of the half combines cells 2 gh and 2 gh + 1 of every
+      // thread's eight over the half's four groups, in order
+      int bx, by;
+      const CutInst& I = output_block(tab, ninst, s_blk[half], bx, by);
+      const int cx = 2 * (lane & 7), cy0 = 4 * (lane >> 3);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int r = 2 * gh + rr;
+        float2 sum = part[4 * half][r][lane];
+#pragma unroll
+        for (int h = 1; h < 4; ++h) {
+          const float2 o = part[4 * half + h][r][lane];
+          two_sum_acc(sum, o.x);
+          sum.y += o.y;
+        }
+        const int x = bx * kBin + cx + (r & 1), y = by * kBin + cy0 + (r >> 1);
+        if (x < I.nx && y < I.ny) I.out[(int64_t)y * I.nx + x] = (sum.x + sum.y) * I.scale;
+      }
+    }
+    return;
+  }
   {
     int64_t pos;
     int slice;
@@ -657,24 +716,25 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
     const CutInst& I = output_block(tab, ninst, blk, bx, by);
     if (threadIdx.x == 0) {
       if (slice < 0) {
-        s_rg = __ldg(ranges + blk);
-        s_total = __ldg(totals + blk);
+        s_rg[0] = __ldg(ranges + blk);
+        s_total[0] = __ldg(totals + blk);
       } else {  // the slice's own bin range and point count
         const BinRange b = block_bins_rect(I.cs, I.range_reach, I.inv_binw, I.nbx, I.nby,
                                            bx * kBin, by * kBin + slice * kSliceRows, kBin,
                                            kSliceRows);
-        s_rg = make_int4(b.lo_bx, b.hi_bx, b.lo_by, b.hi_by);
-        s_total = range_total(start, I.bin_begin, I.nbx, b);
+        s_rg[0] = make_int4(b.lo_bx, b.hi_bx, b.lo_by, b.hi_by);
+        s_total[0] = range_total(start, I.bin_begin, I.nbx, b);
       }
     }
     __syncthreads();
-    const int4 rg = s_rg;
+    const int4 rg = s_rg[0];
     const BinRange br = {rg.x, rg.y, rg.z, rg.w};
-    const int64_t total = s_total;
+    const int64_t total = s_total[0];
     if (slice < 0) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) part[g][r][lane] = make_float2(0.f, 0.f);
-      group_dispatch<4>(I, P, W, start, bx, by, 0, br, total, g, lane, T, &part[g][0][lane]);
+      group_dispatch<4, kGroups>(I, P, W, start, bx, by, 0, br, total, g, lane, T,
+                                 &part[g][0][lane]);
       __syncthreads();  // every group's running sums are final
       // group g combines cell r = g of every thread's eight, over the groups in
       // order (the same order for every block and run)
@@ -693,7 +753,7 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads)
     } else {
       part[g][0][lane] = make_float2(0.f, 0.f);
       part[g][1][lane] = make_float2(0.f, 0.f);
-      group_dispatch<1>(I, P, W, start, bx, by, slice * kSliceRows, br, total, g, lane, T,
+      group_dispatch<1, kGroups>(I, P, W, start, bx, by, slice * kSliceRows, br, total, g, lane, T,
                         &part[g][0][lane]);
       __syncthreads();
       if (threadIdx.x < 2 * kGroupThreads) {  // 64 cells, one thread each

@@ -325,7 +325,8 @@ struct CutoffScratch {
   uint32_t* order;  // [cutoff output blocks] the blocks, heaviest first
   uint32_t* totals; // [cutoff output blocks] points within reach of each block
   int4* ranges;     // [cutoff output blocks] each block's sort-bin range (BinRange)
-  uint32_t* ocount; // [kCutOcountWords] per-key block counts and cursors, blocks to split
+  uint32_t* ocount; // [kCutOcountWords] per-key block counts and cursors, blocks to split,
+                    // position of the first light block
   CallScalars* err; // where a timed-out wait of the sort's look-back is recorded
 };
 // Weight classes of the cutoff path's output blocks (by points within reach:
@@ -334,7 +335,7 @@ struct CutoffScratch {
 // cursors and the number of blocks to be split.
 constexpr int kCutOrderClasses = 66;
 constexpr int kCutOrderKeys = 2 * kCutOrderClasses;
-constexpr int kCutOcountWords = 2 * kCutOrderKeys + 1;
+constexpr int kCutOcountWords = 2 * kCutOrderKeys + 2;
 struct CutoffSizes {
   int nchunks, passes;
   size_t hist_words;
