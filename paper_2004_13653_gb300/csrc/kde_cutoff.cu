@@ -9,7 +9,9 @@
 // in sorted order: its eight warps take 32-point batches in turn, tabulate
 // the x and y kernel factors of the block's 16 columns and 16 rows in shared
 // memory, and each thread adds the outer products into its eight cells.  The
-// blocks run heaviest first.  Nothing is accumulated with atomics, and the
+// blocks run heaviest first; a block with thousands of points within reach is
+// split into four row slices, one CTA each, and light blocks share a CTA two
+// at a time, four warps each.  Nothing is accumulated with atomics, and the
 // order of every sum is fixed, so results are reproducible bit for bit.  The
 // same sort, with 32-cell bins and a wider reach, orders the points of the
 // block-sparse tensor-core path.
