@@ -456,6 +456,40 @@ __global__ void k_cut_order_scatter(const CutInst* __restrict__ tab, int ninst,
   order[first[key] + atomicAdd(&ocount[kCutOrderKeys + key], 1u)] = (uint32_t)blk;
 }
 
+// The RunCursor walk with 32-bit positions (a block's or slice's reach list
+// and the sorted points number fewer than 2^32): fewer registers in the
+// gather, whose occupancy its register count sets.
+struct RunCursor32 {
+  const uint32_t* row;  // start + row0 + by * nbx
+  int nbx, lo_bx, hi_bx, by, hi_by;
+  uint32_t vr, ra, rb;
+  __device__ __forceinline__ void load_run() {
+    ra = __ldg(row + lo_bx);
+    rb = __ldg(row + hi_bx + 1);
+  }
+  __device__ __forceinline__ void init(const uint32_t* start, int row0, int nbx_,
+                                       const BinRange& br) {
+    nbx = nbx_;
+    lo_bx = br.lo_bx;
+    hi_bx = br.hi_bx;
+    by = br.lo_by;
+    hi_by = br.hi_by;
+    row = start + row0 + by * nbx;
+    vr = 0;
+    load_run();
+  }
+  // index of position v (v below the range's total, not decreasing)
+  __device__ __forceinline__ uint32_t map(uint32_t v) {
+    while (v >= vr + (rb - ra) && by < hi_by) {
+      vr += rb - ra;
+      ++by;
+      row += nbx;
+      load_run();
+    }
+    return ra + (v - vr);
+  }
+};
+
 // Shared-memory tables of one point group.
 struct GroupTables {
   float4 P[kBatch];
@@ -495,7 +529,7 @@ __device__ __forceinline__ void cutoff_group(const CutInst& I, const float4* __r
   const float2 gxe = I.gxt[min(x0 + ej, nx - 1)];
   const float2 gye = I.gyt[min(y0 + ej, ny - 1)];
   if (total == 0) return;
-  RunCursor cur;
+  RunCursor32 cur;
   cur.init(start, I.bin_begin, I.nbx, br);
   constexpr uint32_t kStride = NG * kBatch;
   const uint32_t total32 = (uint32_t)total;

@@ -159,40 +159,42 @@ __host__ __device__ inline BinRange tile_bins(double cs, double reach, double in
   return block_bins(cs, reach, inv_binw, nbx, nby, tm * 256, tn * 256, 256);
 }
 
-// Walks the runs of a range of sort bins (one run per bin row, concatenated)
-// and maps a position of the concatenation to the point's index in the sorted
-// points.  Positions are 32-bit: a range and the sorted points of a call hold
-// fewer than 2^32 points.
+// Walks the bin-row runs of a block's range (the points of bins lo_bx..hi_bx
+// of each row, contiguous in the sorted order) in increasing position order
+// and maps a position of their concatenation to an index of the sorted
+// points.  Positions must not decrease from call to call.
 struct RunCursor {
-  const uint32_t* row;  // start + row0 + by * nbx
-  int nbx, lo_bx, hi_bx, by, hi_by;
-  uint32_t vr, ra, rb;  // position of the current run's first point; the run
+  const uint32_t* start;
+  int row0, nbx, lo_bx, hi_bx, by, hi_by;
+  int64_t vr;         // position of the current run's first point
+  uint32_t ra, rb;    // the current run in the sorted points
   __device__ __forceinline__ void load_run() {
-    ra = __ldg(row + lo_bx);
-    rb = __ldg(row + hi_bx + 1);
+    const int row = row0 + by * nbx;
+    ra = __ldg(start + row + lo_bx);
+    rb = __ldg(start + row + hi_bx + 1);
   }
   // start: bin starts of the sort; row0: first bin of the instance; the range
   // must not be empty
-  __device__ __forceinline__ void init(const uint32_t* start, int row0, int nbx_,
+  __device__ __forceinline__ void init(const uint32_t* start_, int row0_, int nbx_,
                                        const BinRange& br) {
+    start = start_;
+    row0 = row0_;
     nbx = nbx_;
     lo_bx = br.lo_bx;
     hi_bx = br.hi_bx;
     by = br.lo_by;
     hi_by = br.hi_by;
-    row = start + row0 + by * nbx;
     vr = 0;
     load_run();
   }
-  // index of position v (v below the range's total, not decreasing)
-  __device__ __forceinline__ uint32_t map(uint32_t v) {
-    while (v >= vr + (rb - ra) && by < hi_by) {
+  // index of position v (v below the range's total)
+  __device__ __forceinline__ int64_t map(int64_t v) {
+    while (v >= vr + (int64_t)(rb - ra) && by < hi_by) {
       vr += rb - ra;
       ++by;
-      row += nbx;
       load_run();
     }
-    return ra + (v - vr);
+    return (int64_t)ra + (v - vr);
   }
 };
 __host__ __device__ inline bool range_empty(const BinRange& br) {

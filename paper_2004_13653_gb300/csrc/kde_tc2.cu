@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   P[u][hh] = __ldg(I.pts + v);
                   W[u][hh] = __ldg(I.wts + v);
                 } else if (v < itm.vend) {
-                  const uint32_t p = cur.map((uint32_t)v);
+                  const int64_t p = cur.map(v);
                   P[u][hh] = __ldg(I.pts + p);
                   W[u][hh] = __ldg(I.wts + p);
                 } else {  // past the piece: a zero-weight point (B = 0)
