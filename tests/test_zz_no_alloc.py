@@ -72,6 +72,38 @@ def test_noalloc_takes_no_device_memory(lib):
     assert free1 == free0
 
 
+def test_noalloc_in_a_captured_graph_matches_the_oracle(lib):
+    """Captured into a CUDA graph in global capture mode (an allocation by any
+    thread fails the capture), after one plain call that looks up the scratch:
+    every replay gives the plain call's values bit for bit, within FP32 of the
+    oracle."""
+    wl = workloads.config1()
+    pts = torch.as_tensor(np.ascontiguousarray(wl.xy), dtype=torch.float64, device="cuda")
+    w = torch.as_tensor(wl.w, dtype=torch.float32, device="cuda")
+    org = (ctypes.c_double * 2)(*wl.origin)
+
+    def call(out):
+        rc = lib.kde_grid_noalloc(pts.data_ptr(), w.data_ptr(), wl.n, ctypes.byref(org), wl.cell,
+                                  wl.nx, wl.ny, wl.h, oracle.GAUSSIAN, out.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+        assert rc == kde.KDE_OK, lib.kde_last_error().decode()
+
+    plain = torch.full((wl.ny, wl.nx), np.nan, dtype=torch.float32, device="cuda")
+    call(plain)
+    torch.cuda.synchronize()
+    out = torch.full_like(plain, np.nan)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        call(out)
+    for _ in range(2):
+        out.fill_(np.nan)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, plain)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, oracle.GAUSSIAN)
+    assert rel_linf(out.cpu().numpy(), ref) <= TOL_FP32
+
+
 def test_noalloc_rejects_inputs_beyond_its_scratch(lib):
     wl = workloads.random_points(801, 1_000_000, 5000.0, 10.0, 64, 64, 30.0, oracle.GAUSSIAN)
     out = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
