@@ -234,6 +234,34 @@ def _wide_grid(seed, n_side, cell, centre):
     return wl
 
 
+@pytest.mark.parametrize("nx,ny", [(68, 60), (64, 64), (1028, 4), (1020, 1028), (262148, 4)],
+                         ids=["255-bins", "256-bins", "257-bins", "65535-bins", "65537-bins"])
+def test_sort_pass_count_boundaries(nx, ny):
+    """Grids whose 4-cell sort bins number 255, 256, 257, 65535 and 65537
+    (1024^2's 65536 is covered elsewhere): valid keys of 8, 8, 9, 16 and 17
+    bits, the padding key fitting the top digit or taking the bucket above
+    the digits, on either side of every change in the number of passes.
+    Points over and around the grid, a share beyond reach; n not a multiple
+    of the sort's chunk.  Against the oracle on every cell of the small grids
+    and on sampled cells of the large ones."""
+    kid = oracle.EPANECHNIKOV
+    cell = 10.0
+    rng = np.random.default_rng(nx + 7 * ny)
+    wl = workloads.random_points(nx + ny, 20_003, 1.0, cell, nx, ny, 2.0 * cell, kid)
+    W, H = nx * cell, ny * cell
+    wl.local[:] = np.stack([rng.uniform(-0.2 * W, 1.2 * W, wl.n),
+                            rng.uniform(-0.2 * H - 50.0, 1.2 * H + 50.0, wl.n)], 1)
+    F = run_gpu(wl, kid)
+    if nx * ny <= 5000:
+        ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid)
+        assert rel_linf(F, ref) <= TOL_FP32
+    else:
+        cells = sample_cells(F, 512, seed=nx)
+        ref = oracle.kde_cells(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, kid, cells)
+        assert np.max(ref) > 0
+        assert rel_linf(F.reshape(-1)[cells], ref) <= TOL_FP32
+
+
 def test_three_radix_passes_and_the_marker_bucket_on_a_16384_square_grid():
     """16384^2 cells at h = 2 cells: 4096^2 = 2^24 sort bins of 4 cells.  The
     valid keys take 24 bits (three 8-bit passes, the last writing the
