@@ -148,6 +148,24 @@ def test_plain_entry_runs_on_the_set_stream():
     assert rel_linf(out.cpu().numpy(), ref) <= 1e-5
 
 
+def test_plain_entry_with_host_buffers_on_a_set_stream():
+    """Host (numpy) points, weights and output through kde_grid while a side
+    stream is set: the copies go through the workspace on that stream and the
+    call still returns the finished density, equal to the oracle's."""
+    wl = workloads.config1()
+    side = torch.cuda.Stream()
+    out = np.full((wl.ny, wl.nx), np.nan, dtype=np.float32)
+    try:
+        kde.set_stream(side)
+        kde.grid_simple(np.ascontiguousarray(wl.xy), np.ascontiguousarray(wl.w), wl.origin,
+                        wl.cell, wl.nx, wl.ny, wl.h, wl.kernel, out)
+    finally:
+        kde.set_stream(None)
+    ref = oracle.kde_grid(wl.xy, wl.w, wl.origin, wl.cell, wl.nx, wl.ny, wl.h, wl.kernel)
+    assert np.isfinite(out).all()
+    assert rel_linf(out, ref) <= 1e-5  # AUTO path
+
+
 def test_nonfinite_coordinate_reported():
     wl = workloads.config1()
     xy = wl.xy.copy()
